@@ -1,0 +1,163 @@
+/*
+ * mpjacobi.h -- C ABI of libmpjacobi, a GB300 (sm_103a) implementation of the
+ * mixed precision Jacobi eigensolver for real symmetric matrices of
+ * Zhou, "A Mixed Precision Eigensolver Based on the Jacobi Algorithm"
+ * (arXiv 2509.00495).
+ *
+ * Problem (Sec. 5.1, Algorithm 9): given a symmetric A in R^{n x n}, return an
+ * orthogonal Q and a diagonal Lambda = diag(W) with A = Q Lambda Q^T, plus the
+ * number of Jacobi sweeps used.  The mixed method computes
+ *   1. Q_l: approximate eigenvectors from an FP32 Jacobi (the paper's stage 1
+ *      is eig(single(A)); here an FP32 block round-robin Jacobi),
+ *   2. Q_d: Newton-Schulz X <- X (3I - X^T X) / 2 in FP64 (Sec. 4.3.4, Alg. 8),
+ *   3. A_cond = Q_d^T A Q_d in FP64 (Alg. 9 step 3),
+ *   4. FP64 Jacobi sweeps on A_cond from V = I until off(A_cond) <= tol
+ *      (Alg. 4, with the round-robin or the cyclic-by-row ordering),
+ *   5. W = diag(A_cond), Q = Q_d V.
+ * The plain method is step 4 applied to A itself (the paper's jacobi_eig).
+ *
+ * Conventions for every entry point:
+ *   - matrices are column-major FP64 with a leading dimension (ld >= n);
+ *     A(i,j) = A[i + j*lda];  Q(:,j) is the eigenvector of W[j];
+ *   - pointers named *_dev are CUDA device pointers owned by the caller; the
+ *     library never frees or keeps them past the call;
+ *   - `stream` is a cudaStream_t passed as void* (0 = legacy default stream);
+ *     all work is enqueued on it;
+ *   - errors are returned as mpj_status, never raised; argument errors are
+ *     found on the host before anything is enqueued; conditions found on the
+ *     device (non-finite input, sweep cap) are reported through mpj_info after
+ *     the call returns (the solve entry points synchronize `stream`);
+ *   - no entry point traps or asserts on the device; every device-side wait
+ *     has an iteration limit.
+ */
+#ifndef MPJACOBI_H
+#define MPJACOBI_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  MPJ_OK = 0,
+  MPJ_NOT_CONVERGED = 1,  /* results written, but off(A) > tol at the sweep cap */
+  MPJ_EINVAL = -1,        /* bad size, leading dimension, null pointer or option */
+  MPJ_ENOTSYM = -2,       /* opts.check_symmetry set and A(i,j) != A(j,i) somewhere */
+  MPJ_ENONFINITE = -3,    /* A holds a NaN or an infinity */
+  MPJ_ECUDA = -4,         /* a CUDA runtime call failed (see mpj_last_cuda_error) */
+  MPJ_ENOMEM = -5,        /* workspace allocation failed */
+  MPJ_EDEGENERATE = -6,   /* backward: w_i == w_j for i != j with a nonzero coupling */
+  MPJ_EWORKSPACE = -7,    /* caller workspace too small (see mpj_syev_workspace) */
+  MPJ_ETIMEOUT = -8       /* a device-side barrier gave up after its iteration limit */
+} mpj_status;
+
+enum { MPJ_ORDER_CYCLIC = 0, MPJ_ORDER_ROUND_ROBIN = 1 };
+enum { MPJ_METHOD_MIXED = 0, MPJ_METHOD_PLAIN = 1 };
+
+typedef struct {
+  double tol;        /* FP64 stop: off(A) <= tol; <= 0 selects n * 2^-53 * ||A||_F              */
+  double tol32;      /* stage-1 stop: off(A32) <= tol32; <= 0 selects n * 2^-24 * ||A||_F       */
+  int max_sweeps64;  /* FP64 sweep cap; <= 0 selects 30 (the paper's default is 10)           */
+  int max_sweeps32;  /* stage-1 sweep cap; <= 0 selects 15                                    */
+  int ns_steps;      /* Newton-Schulz steps; <= 0 selects 2 for n < 52000, else 3 (Alg. 8)     */
+  int ordering;      /* FP64 sweep ordering: MPJ_ORDER_ROUND_ROBIN (default) or _CYCLIC      */
+  int method;        /* MPJ_METHOD_MIXED (default) or MPJ_METHOD_PLAIN                        */
+  int polish;        /* 1: one more FP64 Newton-Schulz step on the final Q (not in the paper) */
+  int sort;          /* 1 (default): W ascending, Q's columns permuted to match              */
+  int check_symmetry;/* 1: fail with MPJ_ENOTSYM unless A is exactly symmetric               */
+} mpj_opts;
+
+typedef struct {
+  int status;        /* mpj_status of the solve                                               */
+  int sweeps32;      /* stage-1 (FP32) sweeps                                                 */
+  int sweeps64;      /* FP64 sweeps (the quantity the paper reports as "iterations")          */
+  int ns_steps;      /* Newton-Schulz steps applied                                           */
+  double norm_fro;   /* ||A||_F                                                               */
+  double tol;        /* FP64 tolerance used                                                   */
+  double off32;      /* off(A32) at the end of stage 1                                        */
+  double off_cond;   /* off(A_cond) before the FP64 sweeps                                    */
+  double off_final;  /* off(A) after the last FP64 sweep                                      */
+  float ms_stage[6]; /* device time per stage: stage1, NS, transform, sweeps, final, total   */
+} mpj_info;
+
+/* Fills `o` with the defaults described in mpj_opts. */
+void mpj_opts_default(mpj_opts* o);
+
+/* Human-readable name of a status code (static storage). */
+const char* mpj_status_str(int status);
+
+/* Text of the last CUDA error seen by this thread inside the library. */
+const char* mpj_last_cuda_error(void);
+
+/* Bytes of device workspace mpj_syev_ex needs for size n under `o` (NULL: defaults). */
+size_t mpj_syev_workspace(int n, const mpj_opts* o);
+
+/* Mixed precision symmetric eigensolver (Alg. 9), default options.
+ * A_dev: n x n input, read only.  W_dev: n eigenvalues (ascending).
+ * Q_dev: n x n eigenvectors, ldq = n.  tol <= 0 selects n 2^-53 ||A||_F.
+ * Allocates its workspace with cudaMallocAsync on `stream` and frees it before
+ * returning; synchronizes `stream`.  Returns MPJ_OK, MPJ_NOT_CONVERGED, or an
+ * error code. */
+int mpj_syev(int n, const double* A_dev, int lda, double* W_dev, double* Q_dev, double tol, void* stream);
+
+/* Same with explicit options, output leading dimension, optional host `info`
+ * (may be NULL) and optional caller workspace (work_dev may be NULL: then the
+ * library allocates; else work_bytes >= mpj_syev_workspace(n, o)). */
+int mpj_syev_ex(int n, const double* A_dev, int lda, double* W_dev, double* Q_dev, int ldq, const mpj_opts* o,
+                mpj_info* info, void* work_dev, size_t work_bytes, void* stream);
+
+/* Batched solve of `batch` independent matrices (sizes 1 <= n_i <= 256) in one
+ * persistent launch: one CTA per matrix from a size-sorted work queue.
+ * n_host: host array of sizes.  A_dev, W_dev, Q_dev: device arrays of `batch`
+ * device pointers (A read only, lda_i = n_i; Q_i is n_i x n_i, ld n_i).
+ * sweeps_host (may be NULL): receives the FP64 sweep count per matrix.
+ * Synchronizes `stream`.  Returns MPJ_NOT_CONVERGED if any matrix hit the cap. */
+int mpj_syev_batched(int batch, const int* n_host, const double* const* A_dev, double* const* W_dev,
+                     double* const* Q_dev, double tol, int* sweeps_host, void* stream);
+
+/* Eigen-adjoint (not in the paper): with W, Q from a solve (Q n x n, ld ldq),
+ * upstream gradients dW (n, may be NULL = 0) and dQ (n x n, ld lddq, may be
+ * NULL = 0), writes dA = sym(Q (diag(dW) + F o (Q^T dQ)) Q^T), F_ij = 1/(w_j - w_i)
+ * for i != j, F_ii = 0, sym(X) = (X + X^T)/2, into dA (ld ldda).
+ * `batch` matrices of the same n are processed at once; matrix b starts at
+ * offset b*n (W, dW) and b*ld*n (Q, dQ, dA).  Returns MPJ_EDEGENERATE if some
+ * w_i == w_j (i != j) meets a nonzero (Q^T dQ)_ij (dA is then undefined). */
+int mpj_syev_backward(int batch, int n, const double* W_dev, const double* Q_dev, int ldq, const double* dW_dev,
+                      const double* dQ_dev, int lddq, double* dA_dev, int ldda, void* stream);
+
+/* ---- stage entry points (each one step of Alg. 9, for stage-wise checks) ---- */
+
+/* Stage 1: FP32 block round-robin Jacobi on fl32(A) from V32 = I; writes
+ * Ql = double(V32) (n x n, ld ldq).  Stops at off(A32) <= tol32 (<= 0: default)
+ * or after max_sweeps (<= 0: 15).  sweeps / off32 (host, may be NULL). */
+int mpj_stage1(int n, const double* A_dev, int lda, double* Ql_dev, int ldq, double tol32, int max_sweeps,
+               int* sweeps, double* off32, void* stream);
+
+/* Newton-Schulz in place: X <- X (3I - X^T X)/2, `steps` times (Sec. 4.3.4). */
+int mpj_newton_schulz(int n, double* X_dev, int ldx, int steps, void* stream);
+
+/* Preconditioning: Ac = Qd^T A Qd (Alg. 9 step 3); Ac is written symmetric. */
+int mpj_precondition(int n, const double* A_dev, int lda, const double* Qd_dev, int ldq, double* Ac_dev, int ldc,
+                     void* stream);
+
+/* FP64 Jacobi sweeps in place on the symmetric A (full storage, both triangles
+ * kept equal) accumulating V <- V J (V holds the start matrix, e.g. I), with
+ * ordering MPJ_ORDER_ROUND_ROBIN or MPJ_ORDER_CYCLIC, per-pair skip rule
+ * |a_pq| > 2^-53 sqrt(|a_pp a_qq|), stop at off(A) <= tol (tol <= 0: n 2^-53 ||A||_F)
+ * or max_sweeps (<= 0: 30).  sweeps / off_final (host, may be NULL).
+ * Returns MPJ_NOT_CONVERGED at the cap. */
+int mpj_jacobi64(int n, double* A_dev, int lda, double* V_dev, int ldv, double tol, int ordering, int max_sweeps,
+                 int* sweeps, double* off_final, void* stream);
+
+/* FP64 matrix product on the library's DMMA kernel:
+ * C = alpha op(A) op(B) + beta C, op(X) = X or X^T (trans = 'N' or 'T'),
+ * op(A) m x k, op(B) k x n.  No symmetric shortcuts. */
+int mpj_dgemm(char transa, char transb, int m, int n, int k, double alpha, const double* A_dev, int lda,
+              const double* B_dev, int ldb, double beta, double* C_dev, int ldc, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MPJACOBI_H */

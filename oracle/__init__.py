@@ -26,6 +26,8 @@ _LIB = os.path.join(_HERE, "libmpj_oracle.so")
 
 CYCLIC = 0
 ROUND_ROBIN = 1
+BLOCK_ROUND_ROBIN = 2  # the FP32 stage's block ordering (blocks of 16)
+BLOCK = 16
 
 U_D = 2.0 ** -53  # unit roundoff, double (paper Sec. 1.2, unit roundoff table)
 U_L = 2.0 ** -24  # unit roundoff, single
@@ -86,6 +88,8 @@ def _declare(L):
     L.orc_fro_d.argtypes = [_i, _dp, _i]
     L.orc_fro_d.restype = _d
     L.orc_round_robin_pair.argtypes = [_i, _i, _i, _ip, _ip, _ip]
+    L.orc_block_pair.argtypes = [_i, _i, _i, _i, _i, _ip, _ip]
+    L.orc_block_pair.restype = _i
     L.orc_jacobi_d.argtypes = [_i, _dp, _i, _dp, _i, _i, _d, _d, _i, _i, _ip, _llp, _dp]
     L.orc_jacobi_d.restype = _i
     L.orc_jacobi_f.argtypes = [_i, _fp, _i, _fp, _i, _i, _d, ctypes.c_float, _i, _ip, _llp, _dp]
@@ -183,6 +187,29 @@ def round_robin_pairs(n: int):
                 pairs.append((p.value, q.value))
         rounds.append(pairs)
     return rounds
+
+
+def block_schedule(n: int):
+    """The block round-robin schedule: list over outer rounds of lists (per block
+    pair) of lists (per inner round) of the valid global pairs (p, q)."""
+    L = _load()
+    N = ((n + 2 * BLOCK - 1) // (2 * BLOCK)) * 2 * BLOCK
+    nb = N // BLOCK
+    p, q = ctypes.c_int(), ctypes.c_int()
+    out = []
+    for R in range(nb - 1):
+        rnd = []
+        for P in range(nb // 2):
+            inner = []
+            for rho in range(2 * BLOCK - 1):
+                pairs = []
+                for i in range(BLOCK):
+                    if L.orc_block_pair(n, R, P, rho, i, ctypes.byref(p), ctypes.byref(q)):
+                        pairs.append((p.value, q.value))
+                inner.append(pairs)
+            rnd.append(inner)
+        out.append(rnd)
+    return out
 
 
 def jacobi(A, V=None, *, ordering=CYCLIC, tol=0.0, skip_tol=U_D, max_sweeps=30, paper_mode=False,

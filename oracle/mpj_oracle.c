@@ -23,6 +23,8 @@
 
 #define ORC_CYCLIC 0      /* cyclic-by-row ordering, Sec. 3.3 (Algorithm 4)     */
 #define ORC_ROUND_ROBIN 1 /* circle-method tournament ordering (not in the paper) */
+#define ORC_BLOCK_RR 2    /* block round-robin ordering of the FP32 stage (not in the paper) */
+#define ORC_BLK 16        /* block size of ORC_BLOCK_RR */
 
 #define AT(M, ld, i, j) ((M)[(size_t)(i) + (size_t)(j) * (size_t)(ld)])
 
@@ -162,6 +164,29 @@ static int rr_pair(int n, int r, int i, int* p, int* q) {
 
 void orc_round_robin_pair(int n, int r, int i, int* p, int* q, int* valid) { *valid = rr_pair(n, r, i, p, q); }
 
+/* Block round-robin ordering (the FP32 stage's ordering): indices padded to
+ * N = n rounded up to a multiple of 2*ORC_BLK are cut into nb = N/ORC_BLK
+ * blocks.  A sweep is nb-1 outer rounds of the circle method on blocks; in
+ * outer round R, block pair P = (I, J), I < J, runs one inner circle-method
+ * sweep (2*ORC_BLK - 1 inner rounds of ORC_BLK pairs) over the 2*ORC_BLK
+ * indices of I u J, local index l < ORC_BLK meaning I*ORC_BLK + l and
+ * l >= ORC_BLK meaning J*ORC_BLK + l - ORC_BLK.  This returns the global pair
+ * (p < q) of inner pair i of inner round rho; 0 when q is a padding index.  */
+int orc_block_pair(int n, int R, int P, int rho, int i, int* p, int* q) {
+  int N = ((n + 2 * ORC_BLK - 1) / (2 * ORC_BLK)) * (2 * ORC_BLK);
+  int nb = N / ORC_BLK;
+  int I, J, lx, ly;
+  rr_pair(nb, R, P, &I, &J);
+  rr_pair(2 * ORC_BLK, rho, i, &lx, &ly);
+  int gx = lx < ORC_BLK ? I * ORC_BLK + lx : J * ORC_BLK + (lx - ORC_BLK);
+  int gy = ly < ORC_BLK ? I * ORC_BLK + ly : J * ORC_BLK + (ly - ORC_BLK);
+  *p = gx < gy ? gx : gy;
+  *q = gx < gy ? gy : gx;
+  return *q < n;
+}
+
+static int block_nb(int n) { return ((n + 2 * ORC_BLK - 1) / (2 * ORC_BLK)) * 2; }
+
 /* Symmetrize A = (A + A^T)/2, as the paper's cyclic listing does after every
  * sweep in which a rotation happened (Appendix B, jacobi_cyclic).           */
 static void symmetrize_d(int n, double* A, int lda) {
@@ -217,6 +242,23 @@ int orc_jacobi_d(int n, double* A, int lda, double* V, int ldv, int ordering, do
             ++rot;
           }
         }
+    } else if (ordering == ORC_BLOCK_RR) {
+      int nb = block_nb(n);
+      for (int R = 0; R < nb - 1; ++R)
+        for (int P = 0; P < nb / 2; ++P)
+          for (int rho = 0; rho < 2 * ORC_BLK - 1; ++rho)
+            for (int i = 0; i < ORC_BLK; ++i) {
+              int p, q;
+              if (!orc_block_pair(n, R, P, rho, i, &p, &q)) continue;
+              double apq = AT(A, lda, p, q);
+              if (fabs(apq) > skip_tol * sqrt(fabs(AT(A, lda, p, p) * AT(A, lda, q, q)))) {
+                double c, s;
+                orc_jacobi_pair_d(AT(A, lda, p, p), AT(A, lda, q, q), apq, &c, &s);
+                rotate_d(n, A, lda, V, ldv, p, q, c, s);
+                done_rot = 1;
+                ++rot;
+              }
+            }
     } else {
       for (int r = 0; r < m - 1; ++r)
         for (int i = 0; i < m / 2; ++i) {
@@ -280,6 +322,23 @@ int orc_jacobi_f(int n, float* A, int lda, float* V, int ldv, int ordering, doub
             ++rot;
           }
         }
+    } else if (ordering == ORC_BLOCK_RR) {
+      int nb = block_nb(n);
+      for (int R = 0; R < nb - 1; ++R)
+        for (int P = 0; P < nb / 2; ++P)
+          for (int rho = 0; rho < 2 * ORC_BLK - 1; ++rho)
+            for (int i = 0; i < ORC_BLK; ++i) {
+              int p, q;
+              if (!orc_block_pair(n, R, P, rho, i, &p, &q)) continue;
+              float apq = AT(A, lda, p, q);
+              if (fabsf(apq) > skip_tol * sqrtf(fabsf(AT(A, lda, p, p) * AT(A, lda, q, q)))) {
+                float c, s;
+                orc_jacobi_pair_f(AT(A, lda, p, p), AT(A, lda, q, q), apq, &c, &s);
+                rotate_f(n, A, lda, V, ldv, p, q, c, s);
+                done_rot = 1;
+                ++rot;
+              }
+            }
     } else {
       for (int r = 0; r < m - 1; ++r)
         for (int i = 0; i < m / 2; ++i) {

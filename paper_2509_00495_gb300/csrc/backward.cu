@@ -1,0 +1,94 @@
+// backward.cu -- eigen-adjoint of the symmetric eigensolver (not in the paper;
+// the standard first-order perturbation result, e.g. Giles 2008, "Collected
+// matrix derivative results"):
+//   M = Q^T dQ,  G_ii = dW_i,  G_ij = M_ij / (w_j - w_i) (i != j),
+//   dA = sym(Q G Q^T) = Q sym(G) Q^T,  sym(X) = (X + X^T)/2.
+// Symmetrizing G first makes the last product symmetric in exact arithmetic,
+// so it runs as a lower-tile product with mirrored writes (exactly symmetric
+// dA, half the flops): 2n^3 + 2n^3 + n^3 FP64 flops per matrix on the DMMA
+// kernel, batched over blockIdx.z.
+#include "common.cuh"
+#include "gemm64.cuh"
+
+namespace {
+
+// Gs = sym(G) from M (may be null: M = 0), w, dW (may be null: dW = 0).
+__global__ void adjoint_core(const double* __restrict__ M, const double* __restrict__ W,
+                             const double* __restrict__ dW, int n, double* __restrict__ Gs,
+                             unsigned* __restrict__ flags) {
+  const int b = blockIdx.z;
+  const double* w = W + (size_t)b * n;
+  const double* Mb = M ? M + (size_t)b * n * n : nullptr;
+  double* G = Gs + (size_t)b * n * n;
+  int j = blockIdx.y;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    double g;
+    if (i == j) {
+      g = dW ? dW[(size_t)b * n + i] : 0.0;
+    } else {
+      double mij = Mb ? Mb[(size_t)j * n + i] : 0.0;  // M(i,j)
+      double mji = Mb ? Mb[(size_t)i * n + j] : 0.0;  // M(j,i)
+      double gap = w[j] - w[i];
+      double gij = 0.0, gji = 0.0;
+      if (gap == 0.0) {
+        if (mij != 0.0 || mji != 0.0) atomicOr(flags, MPJ_FLAG_DEGENERATE);
+      } else {
+        gij = mij / gap;   // F_ij M_ij, F_ij = 1/(w_j - w_i)
+        gji = mji / -gap;  // F_ji M_ji
+      }
+      g = 0.5 * (gij + gji);
+    }
+    G[(size_t)j * n + i] = g;
+  }
+}
+
+}  // namespace
+
+extern "C" int mpj_syev_backward(int batch, int n, const double* W, const double* Q, int ldq, const double* dW,
+                                 const double* dQ, int lddq, double* dA, int ldda, void* stream) {
+  cudaStream_t s = (cudaStream_t)stream;
+  if (batch < 0 || n < 0 || ldq < n || lddq < n || ldda < n || ldq < 1 || lddq < 1 || ldda < 1) return MPJ_EINVAL;
+  if (batch == 0 || n == 0) return MPJ_OK;
+  if (!W || !Q || !dA) return MPJ_EINVAL;
+  size_t sq = (size_t)n * n;
+  void* w = nullptr;
+  size_t bytes = 2 * (size_t)batch * sq * sizeof(double) + 256;
+  if (cudaMallocAsync(&w, bytes, s) != cudaSuccess) return MPJ_ENOMEM;
+  double* M = (double*)w;
+  double* T = M + (size_t)batch * sq;
+  unsigned* flags = (unsigned*)(T + (size_t)batch * sq);
+  int st = MPJ_OK;
+  unsigned hflags = 0;
+  cudaError_t e = cudaMemsetAsync(flags, 0, sizeof(unsigned), s);
+  long long sQ = (long long)ldq * n, sdQ = (long long)lddq * n, sA = (long long)ldda * n, sN = (long long)sq;
+  if (e == cudaSuccess && dQ) {  // M = Q^T dQ
+    GemmArgs g{n, n, n, 1.0, 0.0, Q, ldq, sQ, dQ, lddq, sdQ, nullptr, n, 0, M, n, sN, 0};
+    e = mpj_gemm64_launch(g, true, false, batch, s);
+  }
+  if (e == cudaSuccess) {  // T = sym(G) (into T), then M = Q T, then dA = M Q^T (symmetric)
+    dim3 grid((n + 255) / 256 > 8 ? 8 : (n + 255) / 256, n, batch);
+    adjoint_core<<<grid, 256, 0, s>>>(dQ ? M : nullptr, W, dW, n, T, flags);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) {
+    GemmArgs g{n, n, n, 1.0, 0.0, Q, ldq, sQ, T, n, sN, nullptr, n, 0, M, n, sN, 0};
+    e = mpj_gemm64_launch(g, false, false, batch, s);
+  }
+  if (e == cudaSuccess) {
+    GemmArgs g{n, n, n, 1.0, 0.0, M, n, sN, Q, ldq, sQ, nullptr, n, 0, dA, ldda, sA, 1};
+    e = mpj_gemm64_launch(g, false, true, batch, s);
+  }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&hflags, flags, sizeof(unsigned), cudaMemcpyDeviceToHost, s);
+  if (e != cudaSuccess) {
+    mpj_set_cuda_error(e, "mpj_syev_backward", __LINE__);
+    st = MPJ_ECUDA;
+  }
+  cudaFreeAsync(w, s);
+  e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess && st >= 0) {
+    mpj_set_cuda_error(e, "mpj_syev_backward sync", __LINE__);
+    st = MPJ_ECUDA;
+  }
+  if (st == MPJ_OK && (hflags & MPJ_FLAG_DEGENERATE)) st = MPJ_EDEGENERATE;
+  return st;
+}

@@ -1,0 +1,20 @@
+// jacobi64.cuh -- FP64 Jacobi sweep driver and reductions (jacobi64.cu).
+#pragma once
+#include <cuda_runtime.h>
+#include <stddef.h>
+
+// Scratch (records, reduction partials, scalars) for mpj_jacobi64_run.
+size_t mpj_jacobi64_scratch_bytes(int n);
+
+// FP64 sweeps in place (see mpjacobi.h, mpj_jacobi64).  Synchronizes `s` once
+// per sweep to read off(A).  Returns MPJ_OK / MPJ_NOT_CONVERGED / MPJ_ECUDA.
+int mpj_jacobi64_run(int n, double* A, int lda, double* V, int ldv, double tol, int ordering, int max_sweeps,
+                     int* sweeps_out, double* off_out, double* off_initial, void* scratch, cudaStream_t s);
+
+// Sum of squares of A's entries (off_only: off-diagonal entries) into *out,
+// through 256 per-CTA partials summed in a fixed order; sets
+// MPJ_FLAG_NONFINITE in *flags (if not null) when an entry is NaN or Inf.
+cudaError_t mpj_sumsq(const double* A, int lda, int n, bool off_only, double* partial, double* out, unsigned* flags,
+                      cudaStream_t s);
+cudaError_t mpj_sumsq32(const float* A, int lda, int n, double* partial, double* out, cudaStream_t s);
+cudaError_t mpj_check_symmetric(const double* A, int lda, int n, unsigned* flags, cudaStream_t s);

@@ -1,0 +1,308 @@
+// stage1.cu -- stage 1 of the mixed algorithm: approximate eigenvectors Q_l
+// from an FP32 Jacobi (the paper's stage 1 is eig(single(A)), Sec. 4.1 and
+// Algorithm 9; only an approximate Q_l with ||A Q_l - Q_l D_l|| <~ n u_l ||A||
+// is needed, so the FP32 stage may use any convergent Jacobi ordering).
+//
+// Ordering: block round-robin.  The padded index range [0, N) (N a multiple
+// of 32, pads inert: zero rows/columns never rotate) is cut into nb = N/16
+// blocks of 16.  A sweep is nb-1 outer rounds of the circle method on blocks;
+// in each round the nb/2 disjoint block pairs (I, J) each run one inner
+// round-robin sweep over the 32 indices of I u J (31 inner rounds of 16
+// disjoint pairs, Algorithm 2 with the skip test of Algorithm 4 at u_l = 2^-24)
+// on their 32 x 32 diagonal subproblem, held in shared memory, accumulating the
+// 32 x 32 orthogonal U_IJ.  The rotations of one round touch disjoint index
+// sets, so applying them to the rest of the matrix afterwards as products
+//   A[P,Q] <- U_P^T A[P,Q] U_Q,   V[:,Q] <- V[:,Q] U_Q
+// (P, Q = index sets of block pairs) gives the same iterates as applying them
+// one by one.  Each round is two launches: the subproblem solves and the
+// blocked update (FP32 FMA), which touch A32 and V32 once per round instead of
+// once per pair step.  off(A32) is reduced after each sweep; stop at
+// off(A32) <= tol32 or the sweep cap.
+#include "common.cuh"
+#include "stage1.cuh"
+
+namespace {
+
+constexpr int BS = 16;  // block size
+constexpr int W2 = 32;  // indices per block pair
+constexpr int LD = 33;  // padded shared-memory leading dimension
+
+// global index of local index l in block pair (I, J)
+MPJ_DEV int gidx(int I, int J, int l) { return l < BS ? I * BS + l : J * BS + (l - BS); }
+
+MPJ_DEV void block_pair(int nb, int R, int slot, int& I, int& J) {
+  int x, y;
+  rr_slot(nb, R, slot, x, y);
+  I = x < y ? x : y;
+  J = x < y ? y : x;
+}
+
+__global__ void init32(const double* __restrict__ A, int lda, int n, int N, float* __restrict__ A32,
+                       float* __restrict__ V32) {
+  size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  size_t total = (size_t)N * N;
+  for (; idx < total; idx += (size_t)gridDim.x * blockDim.x) {
+    int i = (int)(idx % N), j = (int)(idx / N);
+    A32[idx] = (i < n && j < n) ? (float)A[(size_t)j * lda + i] : 0.0f;
+    V32[idx] = (i == j) ? 1.0f : 0.0f;
+  }
+}
+
+__global__ void widen(const float* __restrict__ V32, int N, int n, double* __restrict__ Q, int ldq) {
+  size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  size_t total = (size_t)n * n;
+  for (; idx < total; idx += (size_t)gridDim.x * blockDim.x) {
+    int i = (int)(idx % n), j = (int)(idx / n);
+    Q[(size_t)j * ldq + i] = (double)V32[(size_t)j * N + i];
+  }
+}
+
+// One CTA per block pair of outer round R: inner round-robin sweep on the
+// 32 x 32 subproblem; writes the rotated subproblem S and the accumulated U.
+__global__ void __launch_bounds__(256) solve32(const float* __restrict__ A32, int N, int nb, int R,
+                                               float* __restrict__ Sbuf, float* __restrict__ Ubuf) {
+  __shared__ float S[W2][LD];
+  __shared__ float U[W2][LD];
+  __shared__ RotRec<float> rec[W2 / 2];
+  const int slot = blockIdx.x;
+  int I, J;
+  block_pair(nb, R, slot, I, J);
+  const int tid = threadIdx.x;
+  for (int e = tid; e < W2 * W2; e += 256) {
+    int li = e % W2, lj = e / W2;
+    S[li][lj] = A32[(size_t)gidx(I, J, lj) * N + gidx(I, J, li)];
+    U[li][lj] = (li == lj) ? 1.0f : 0.0f;
+  }
+  __syncthreads();
+  const float skip = 0x1p-24f;
+  for (int rho = 0; rho < W2 - 1; ++rho) {
+    if (tid < W2 / 2) {
+      int x, y;
+      rr_slot(W2, rho, tid, x, y);
+      RotRec<float> rr;
+      rr_make_rec<float>(W2, W2, rho, x, y, S[x][x], S[y][y], S[y][x], skip, rr);
+      rec[tid] = rr;
+    }
+    __syncthreads();
+    {
+      int a = tid % 16, b = tid / 16;
+      if (a >= b) {
+        int xa, ya, xb, yb;
+        rr_slot(W2, rho, a, xa, ya);
+        rr_slot(W2, rho, b, xb, yb);
+        RotRec<float> ra = rec[a], rb = rec[b];
+        bool rota = rec_rotated(ra.cm1, ra.sig), rotb = rec_rotated(rb.cm1, rb.sig);
+        if (a == b) {
+          if (rota) {
+            S[xa][xa] = ra.dx;
+            S[ya][ya] = ra.dy;
+            S[xa][ya] = 0.0f;
+            S[ya][xa] = 0.0f;
+          }
+        } else if (rota || rotb) {
+          float vxx = S[xa][xb], vxy = S[xa][yb], vyx = S[ya][xb], vyy = S[ya][yb];
+          if (rota) {
+            rot_apply(ra.cm1, ra.sig, vxx, vyx);
+            rot_apply(ra.cm1, ra.sig, vxy, vyy);
+          }
+          if (rotb) {
+            rot_apply(rb.cm1, rb.sig, vxx, vxy);
+            rot_apply(rb.cm1, rb.sig, vyx, vyy);
+          }
+          S[xa][xb] = vxx;
+          S[xb][xa] = vxx;
+          S[xa][yb] = vxy;
+          S[yb][xa] = vxy;
+          S[ya][xb] = vyx;
+          S[xb][ya] = vyx;
+          S[ya][yb] = vyy;
+          S[yb][ya] = vyy;
+        }
+      }
+      // U <- U J: rows of U are independent; columns x_b, y_b
+      for (int e = tid; e < W2 * (W2 / 2); e += 256) {
+        int row = e % W2, sb = e / W2;
+        RotRec<float> rb = rec[sb];
+        if (!rec_rotated(rb.cm1, rb.sig)) continue;
+        int xb, yb;
+        rr_slot(W2, rho, sb, xb, yb);
+        float ux = U[row][xb], uy = U[row][yb];
+        rot_apply(rb.cm1, rb.sig, ux, uy);
+        U[row][xb] = ux;
+        U[row][yb] = uy;
+      }
+    }
+    __syncthreads();
+  }
+  float* So = Sbuf + (size_t)slot * W2 * W2;
+  float* Uo = Ubuf + (size_t)slot * W2 * W2;
+  for (int e = tid; e < W2 * W2; e += 256) {
+    int li = e % W2, lj = e / W2;
+    So[e] = S[li][lj];
+    Uo[e] = U[li][lj];
+  }
+}
+
+__device__ __forceinline__ void tri_tile(int t, int nt, int& ti, int& tj) {
+  tj = 0;
+  while (t >= nt - tj) {
+    t -= nt - tj;
+    ++tj;
+  }
+  ti = tj + t;
+}
+
+// Blocked application of the round's U's: lower tiles of A32 (with mirror)
+// and 32-row tiles of V32.
+__global__ void __launch_bounds__(256) update32(float* __restrict__ A32, float* __restrict__ V32, int N, int nb,
+                                                int R, const float* __restrict__ Sbuf,
+                                                const float* __restrict__ Ubuf, int n_atiles) {
+  __shared__ float T[W2][LD];
+  __shared__ float X[W2][LD];
+  __shared__ float UP[W2][LD];
+  __shared__ float UQ[W2][LD];
+  const int tid = threadIdx.x;
+  const int npairs = nb / 2;
+  int item = blockIdx.x;
+  if (item < n_atiles) {
+    int P, Q;
+    tri_tile(item, npairs, P, Q);
+    int IP, JP, IQ, JQ;
+    block_pair(nb, R, P, IP, JP);
+    block_pair(nb, R, Q, IQ, JQ);
+    if (P == Q) {
+      const float* Sp = Sbuf + (size_t)P * W2 * W2;
+      for (int e = tid; e < W2 * W2; e += 256) {
+        int li = e % W2, lj = e / W2;
+        A32[(size_t)gidx(IP, JP, lj) * N + gidx(IP, JP, li)] = Sp[e];
+      }
+      return;
+    }
+    const float* Up = Ubuf + (size_t)P * W2 * W2;
+    const float* Uq = Ubuf + (size_t)Q * W2 * W2;
+    for (int e = tid; e < W2 * W2; e += 256) {
+      int li = e % W2, lj = e / W2;
+      T[li][lj] = A32[(size_t)gidx(IQ, JQ, lj) * N + gidx(IP, JP, li)];
+      UP[li][lj] = Up[e];
+      UQ[li][lj] = Uq[e];
+    }
+    __syncthreads();
+    const int j = tid % W2, i0 = tid / W2;  // 4 rows i0 + 8k per thread, column j
+    float acc[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) acc[k] = 0.0f;
+    // X = U_P^T T
+#pragma unroll 8
+    for (int l = 0; l < W2; ++l) {
+      float t = T[l][j];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) acc[k] = fmaf(UP[l][i0 + 8 * k], t, acc[k]);
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) X[i0 + 8 * k][j] = acc[k];
+    __syncthreads();
+    // Y = X U_Q
+#pragma unroll
+    for (int k = 0; k < 4; ++k) acc[k] = 0.0f;
+#pragma unroll 8
+    for (int l = 0; l < W2; ++l) {
+      float u = UQ[l][j];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) acc[k] = fmaf(X[i0 + 8 * k][l], u, acc[k]);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < 4; ++k) T[i0 + 8 * k][j] = acc[k];
+    __syncthreads();
+    for (int e = tid; e < W2 * W2; e += 256) {
+      int li = e % W2, lj = e / W2;
+      A32[(size_t)gidx(IQ, JQ, lj) * N + gidx(IP, JP, li)] = T[li][lj];
+      // mirror: entry (cols(Q)[li], rows(P)[lj]) = T[lj][li]
+      A32[(size_t)gidx(IP, JP, lj) * N + gidx(IQ, JQ, li)] = T[lj][li];
+    }
+    return;
+  }
+  // V tile: rows [rc*32, rc*32+32), column set of pair Q
+  int v = item - n_atiles;
+  int nrc = N / W2;
+  int rc = v % nrc, Q = v / nrc;
+  int IQ, JQ;
+  block_pair(nb, R, Q, IQ, JQ);
+  const float* Uq = Ubuf + (size_t)Q * W2 * W2;
+  for (int e = tid; e < W2 * W2; e += 256) {
+    int li = e % W2, lj = e / W2;
+    T[li][lj] = V32[(size_t)gidx(IQ, JQ, lj) * N + rc * W2 + li];
+    UQ[li][lj] = Uq[e];
+  }
+  __syncthreads();
+  const int j = tid % W2, i0 = tid / W2;
+  float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+#pragma unroll 8
+  for (int l = 0; l < W2; ++l) {
+    float u = UQ[l][j];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) acc[k] = fmaf(T[i0 + 8 * k][l], u, acc[k]);
+  }
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < 4; ++k) T[i0 + 8 * k][j] = acc[k];
+  __syncthreads();
+  for (int e = tid; e < W2 * W2; e += 256) {
+    int li = e % W2, lj = e / W2;
+    V32[(size_t)gidx(IQ, JQ, lj) * N + rc * W2 + li] = T[li][lj];
+  }
+}
+
+}  // namespace
+
+int mpj_stage1_padded(int n) { return ((n + W2 - 1) / W2) * W2; }
+
+size_t mpj_stage1_bytes(int n) {
+  size_t N = (size_t)mpj_stage1_padded(n);
+  size_t nb = N / BS;
+  return 2 * N * N * sizeof(float) + 2 * (nb / 2) * W2 * W2 * sizeof(float) + 4096;
+}
+
+cudaError_t mpj_sumsq32(const float* A, int lda, int n, double* partial, double* out, cudaStream_t s);
+
+int mpj_stage1_run(int n, const double* A, int lda, double* Ql, int ldq, double tol32, int max_sweeps, int* sweeps_out,
+                   double* off_out, void* work, double* partial, double* dscal, cudaStream_t s) {
+  const int N = mpj_stage1_padded(n);
+  const int nb = N / BS;
+  float* A32 = (float*)work;
+  float* V32 = A32 + (size_t)N * N;
+  float* Sbuf = V32 + (size_t)N * N;
+  float* Ubuf = Sbuf + (size_t)(nb / 2) * W2 * W2;
+  init32<<<1024, 256, 0, s>>>(A, lda, n, N, A32, V32);
+  MPJ_CUDA_TRY(cudaGetLastError());
+  double off2 = 0.0;
+  MPJ_CUDA_TRY(mpj_sumsq32(A32, N, N, partial, dscal, s));
+  MPJ_CUDA_TRY(cudaMemcpyAsync(&off2, dscal, sizeof(double), cudaMemcpyDeviceToHost, s));
+  MPJ_CUDA_TRY(cudaStreamSynchronize(s));
+  double off = sqrt(off2);
+  int sweeps = 0, status = MPJ_OK;
+  const int npairs = nb / 2;
+  const int n_atiles = npairs * (npairs + 1) / 2;
+  const int grid_u = n_atiles + (N / W2) * npairs;
+  while (off > tol32) {
+    if (sweeps >= max_sweeps) {
+      status = MPJ_NOT_CONVERGED;
+      break;
+    }
+    for (int R = 0; R < nb - 1; ++R) {
+      solve32<<<npairs, 256, 0, s>>>(A32, N, nb, R, Sbuf, Ubuf);
+      update32<<<grid_u, 256, 0, s>>>(A32, V32, N, nb, R, Sbuf, Ubuf, n_atiles);
+    }
+    MPJ_CUDA_TRY(cudaGetLastError());
+    ++sweeps;
+    MPJ_CUDA_TRY(mpj_sumsq32(A32, N, N, partial, dscal, s));
+    MPJ_CUDA_TRY(cudaMemcpyAsync(&off2, dscal, sizeof(double), cudaMemcpyDeviceToHost, s));
+    MPJ_CUDA_TRY(cudaStreamSynchronize(s));
+    off = sqrt(off2);
+  }
+  widen<<<1024, 256, 0, s>>>(V32, N, n, Ql, ldq);
+  MPJ_CUDA_TRY(cudaGetLastError());
+  if (sweeps_out) *sweeps_out = sweeps;
+  if (off_out) *off_out = off;
+  return status;
+}

@@ -1,0 +1,521 @@
+// syev.cu -- host driver and C ABI of libmpjacobi: the mixed precision
+// Jacobi eigensolver of Algorithm 9 (Sec. 5.1) and the plain FP64 Jacobi.
+//
+//   mixed:  A --(stage 1, FP32 block round-robin Jacobi)--> Q_l
+//             --(Newton-Schulz x ns_steps, FP64 DMMA)--> Q_d
+//             --(A_cond = Q_d^T (A Q_d), FP64 DMMA, symmetric)--> A_cond
+//             --(FP64 Jacobi sweeps, V from I, until off <= tol)--> diag, V
+//             --> W = diag (sorted), Q = Q_d V (columns permuted to match)
+//   plain:  FP64 Jacobi sweeps on a copy of A with V from I; W = diag, Q = V.
+//
+// Workspace (mixed, n): three n x n FP64 buffers (X = Q_l/Q_d, M = X^T X then
+// A_cond, Y = NS temporary then V), the stage-1 FP32 buffers (A32, V32 and
+// the per-pair S, U; reused for the permuted V at the end) and a small
+// scratch area.  About 24 n^2 + 8 N^2 bytes: 512 MiB at n = 4096.
+#include <stdio.h>
+#include <string.h>
+
+#include <cmath>
+
+#include "common.cuh"
+#include "gemm64.cuh"
+#include "jacobi64.cuh"
+#include "stage1.cuh"
+
+static thread_local char g_cuda_err[256] = "";
+
+void mpj_set_cuda_error(cudaError_t e, const char* what, int line) {
+  snprintf(g_cuda_err, sizeof g_cuda_err, "%s (%d) in %s [syev line %d]", cudaGetErrorString(e), (int)e, what, line);
+}
+
+namespace {
+
+inline size_t al(size_t x) { return (x + 255) & ~(size_t)255; }
+
+struct Layout {
+  size_t X, M, Y, S1, scratch, small, total;
+};
+
+Layout layout(int n) {
+  Layout L;
+  size_t sq = al((size_t)n * n * sizeof(double));
+  size_t off = 0;
+  L.X = off;
+  off += sq;
+  L.M = off;
+  off += sq;
+  L.Y = off;
+  off += sq;
+  L.S1 = off;
+  size_t s1 = al(mpj_stage1_bytes(n));
+  if (s1 < sq) s1 = sq;
+  off += s1;
+  L.scratch = off;
+  off += al(mpj_jacobi64_scratch_bytes(n));
+  L.small = off;
+  // flags + scalar (256 B), partials (2048 B), ranks (4n B, then rounded up to 256), w (8n B)
+  off += al(2560 + 256 + (size_t)n * (sizeof(int) + sizeof(double)));
+  L.total = off;
+  return L;
+}
+
+// small area: [0] flags (unsigned), [8] dscal (double), [256..] partials (256 doubles),
+// [2304..] ranks (int n), then w (double n)
+struct Small {
+  unsigned* flags;
+  double* dscal;
+  double* partial;
+  int* rank;
+  double* w;
+};
+
+Small small_ptrs(char* base, int n) {
+  Small s;
+  s.flags = (unsigned*)base;
+  s.dscal = (double*)(base + 8);
+  s.partial = (double*)(base + 256);
+  s.rank = (int*)(base + 256 + 256 * sizeof(double));
+  s.w = (double*)(base + al(256 + 256 * sizeof(double) + (size_t)n * sizeof(int)));
+  return s;
+}
+
+__global__ void set_identity(double* V, int ldv, int n) {
+  size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  size_t total = (size_t)n * n;
+  for (; idx < total; idx += (size_t)gridDim.x * blockDim.x) {
+    int i = (int)(idx % n), j = (int)(idx / n);
+    V[(size_t)j * ldv + i] = (i == j) ? 1.0 : 0.0;
+  }
+}
+
+__global__ void copy_mat(const double* __restrict__ A, int lda, double* __restrict__ B, int ldb, int n) {
+  size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  size_t total = (size_t)n * n;
+  for (; idx < total; idx += (size_t)gridDim.x * blockDim.x) {
+    int i = (int)(idx % n), j = (int)(idx / n);
+    B[(size_t)j * ldb + i] = A[(size_t)j * lda + i];
+  }
+}
+
+// rank_i = #{j : w_j < w_i or (w_j == w_i and j < i)}  (ascending, stable)
+__global__ void rank_diag(const double* __restrict__ Ac, int ldc, int n, int sort, int* __restrict__ rank,
+                          double* __restrict__ w) {
+  extern __shared__ double sw[];
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  double wi = i < n ? Ac[(size_t)i * ldc + i] : 0.0;
+  int r = 0;
+  for (int j0 = 0; j0 < n; j0 += blockDim.x) {
+    __syncthreads();
+    int j = j0 + threadIdx.x;
+    if (j < n) sw[threadIdx.x] = Ac[(size_t)j * ldc + j];
+    __syncthreads();
+    int lim = min((int)blockDim.x, n - j0);
+    if (i < n && sort)
+      for (int k = 0; k < lim; ++k) {
+        double wj = sw[k];
+        int jj = j0 + k;
+        r += (wj < wi) || (wj == wi && jj < i);
+      }
+  }
+  if (i < n) {
+    rank[i] = sort ? r : i;
+    w[i] = wi;
+  }
+}
+
+// Vp(:, rank_j) = V(:, j);  W(rank_j) = w_j
+__global__ void permute_cols(const double* __restrict__ V, int ldv, double* __restrict__ Vp, int ldp, int n,
+                             const int* __restrict__ rank, const double* __restrict__ w, double* __restrict__ W) {
+  int j = blockIdx.y;
+  int rj = rank[j];
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    Vp[(size_t)rj * ldp + i] = V[(size_t)j * ldv + i];
+  if (blockIdx.x == 0 && threadIdx.x == 0) W[rj] = w[j];
+}
+
+int blocks_for(size_t total) {
+  size_t b = (total + 255) / 256;
+  return (int)(b > 4096 ? 4096 : (b < 1 ? 1 : b));
+}
+
+struct Timer {
+  cudaEvent_t ev[7];
+  int k = 0;
+  bool on = false;
+  cudaStream_t s;
+  void start(cudaStream_t st) {
+    s = st;
+    on = true;
+    for (auto& e : ev) cudaEventCreate(&e);
+    cudaEventRecord(ev[0], s);
+  }
+  void mark(int i) {
+    if (on) cudaEventRecord(ev[i], s);
+  }
+  void finish(mpj_info* info) {
+    if (!on) return;
+    cudaEventSynchronize(ev[6]);
+    if (info) {
+      for (int i = 0; i < 5; ++i) {
+        float ms = 0;
+        cudaEventElapsedTime(&ms, ev[i], ev[i + 1]);
+        info->ms_stage[i] = ms;
+      }
+      float tot = 0;
+      cudaEventElapsedTime(&tot, ev[0], ev[6]);
+      info->ms_stage[5] = tot;
+    }
+    for (auto& e : ev) cudaEventDestroy(e);
+  }
+};
+
+int fill_opts(int n, const mpj_opts* in, mpj_opts* o) {
+  if (in)
+    *o = *in;
+  else
+    mpj_opts_default(o);
+  if (o->max_sweeps64 <= 0) o->max_sweeps64 = 30;
+  if (o->max_sweeps32 <= 0) o->max_sweeps32 = 15;
+  if (o->ns_steps <= 0) o->ns_steps = (n < 52000) ? 2 : 3;
+  if (o->ordering != MPJ_ORDER_CYCLIC && o->ordering != MPJ_ORDER_ROUND_ROBIN) return MPJ_EINVAL;
+  if (o->method != MPJ_METHOD_MIXED && o->method != MPJ_METHOD_PLAIN) return MPJ_EINVAL;
+  return MPJ_OK;
+}
+
+// Newton-Schulz X <- X (3I - X^T X) / 2 as X <- 1.5 X - 0.5 X (X^T X):
+// SYRK-like symmetric M = X^T X (n^3 flops) then the product with the fused
+// epilogue (2 n^3 flops).  X, M, Y are n x n with ld n; the result ends in *X.
+int ns_steps_run(int n, double** X, double* M, double** Y, int steps, cudaStream_t s) {
+  for (int k = 0; k < steps; ++k) {
+    MPJ_CUDA_TRY(mpj_gemm64(true, false, n, n, n, 1.0, *X, n, *X, n, 0.0, nullptr, n, M, n, 1, s));
+    MPJ_CUDA_TRY(mpj_gemm64(false, false, n, n, n, -0.5, *X, n, M, n, 1.5, *X, n, *Y, n, 0, s));
+    double* t = *X;
+    *X = *Y;
+    *Y = t;
+  }
+  return MPJ_OK;
+}
+
+}  // namespace
+
+// =========================================================================== C ABI
+extern "C" {
+
+void mpj_opts_default(mpj_opts* o) {
+  memset(o, 0, sizeof *o);
+  o->ordering = MPJ_ORDER_ROUND_ROBIN;
+  o->method = MPJ_METHOD_MIXED;
+  o->sort = 1;
+}
+
+const char* mpj_status_str(int st) {
+  switch (st) {
+    case MPJ_OK: return "MPJ_OK";
+    case MPJ_NOT_CONVERGED: return "MPJ_NOT_CONVERGED";
+    case MPJ_EINVAL: return "MPJ_EINVAL";
+    case MPJ_ENOTSYM: return "MPJ_ENOTSYM";
+    case MPJ_ENONFINITE: return "MPJ_ENONFINITE";
+    case MPJ_ECUDA: return "MPJ_ECUDA";
+    case MPJ_ENOMEM: return "MPJ_ENOMEM";
+    case MPJ_EDEGENERATE: return "MPJ_EDEGENERATE";
+    case MPJ_EWORKSPACE: return "MPJ_EWORKSPACE";
+    case MPJ_ETIMEOUT: return "MPJ_ETIMEOUT";
+    default: return "MPJ_UNKNOWN";
+  }
+}
+
+const char* mpj_last_cuda_error(void) { return g_cuda_err; }
+
+size_t mpj_syev_workspace(int n, const mpj_opts* o) {
+  (void)o;
+  if (n <= 0) return 0;
+  return layout(n).total;
+}
+
+int mpj_syev_ex(int n, const double* A, int lda, double* W, double* Q, int ldq, const mpj_opts* opts_in,
+                mpj_info* info, void* work, size_t work_bytes, void* stream) {
+  cudaStream_t s = (cudaStream_t)stream;
+  mpj_opts o;
+  if (info) memset(info, 0, sizeof *info);
+  if (n < 0 || (n > 0 && (!A || !W || !Q)) || lda < (n > 1 ? n : 1) || ldq < (n > 1 ? n : 1)) return MPJ_EINVAL;
+  if (fill_opts(n, opts_in, &o) != MPJ_OK) return MPJ_EINVAL;
+  if (n == 0) return MPJ_OK;
+  Layout L = layout(n);
+  bool own = false;
+  if (work) {
+    if (work_bytes < L.total) return MPJ_EWORKSPACE;
+  } else {
+    cudaError_t e = cudaMallocAsync(&work, L.total, s);
+    if (e != cudaSuccess) {
+      mpj_set_cuda_error(e, "cudaMallocAsync(workspace)", __LINE__);
+      return MPJ_ENOMEM;
+    }
+    own = true;
+  }
+  int st = MPJ_OK;
+  char* base = (char*)work;
+  double* X = (double*)(base + L.X);
+  double* M = (double*)(base + L.M);
+  double* Y = (double*)(base + L.Y);
+  void* S1 = base + L.S1;
+  void* scratch = base + L.scratch;
+  Small sm = small_ptrs(base + L.small, n);
+  Timer tm;
+  double norm2 = 0.0;
+  unsigned flags = 0;
+  double tol = 0.0;
+  int sweeps32 = 0, sweeps64 = 0;
+  double off32 = 0.0, offc = 0.0, offf = 0.0;
+  double* Ac = nullptr;
+  double* V = nullptr;
+  double* Qd = nullptr;
+
+  tm.start(s);
+  // a0: validation and norms
+  if (cudaMemsetAsync(sm.flags, 0, sizeof(unsigned), s) != cudaSuccess) {
+    st = MPJ_ECUDA;
+    goto done;
+  }
+  if (mpj_sumsq(A, lda, n, false, sm.partial, sm.dscal, sm.flags, s) != cudaSuccess) {
+    st = MPJ_ECUDA;
+    goto done;
+  }
+  if (o.check_symmetry && mpj_check_symmetric(A, lda, n, sm.flags, s) != cudaSuccess) {
+    st = MPJ_ECUDA;
+    goto done;
+  }
+  cudaMemcpyAsync(&norm2, sm.dscal, sizeof(double), cudaMemcpyDeviceToHost, s);
+  cudaMemcpyAsync(&flags, sm.flags, sizeof(unsigned), cudaMemcpyDeviceToHost, s);
+  if (cudaStreamSynchronize(s) != cudaSuccess) {
+    mpj_set_cuda_error(cudaGetLastError(), "validation", __LINE__);
+    st = MPJ_ECUDA;
+    goto done;
+  }
+  if (flags & MPJ_FLAG_NONFINITE) {
+    st = MPJ_ENONFINITE;
+    goto done;
+  }
+  if (flags & MPJ_FLAG_NOTSYM) {
+    st = MPJ_ENOTSYM;
+    goto done;
+  }
+  {
+    double normA = std::sqrt(norm2);
+    tol = o.tol > 0 ? o.tol : (double)n * 0x1p-53 * normA;
+    double tol32 = o.tol32 > 0 ? o.tol32 : (double)n * 0x1p-24 * normA;
+    if (info) {
+      info->norm_fro = normA;
+      info->tol = tol;
+    }
+    if (o.method == MPJ_METHOD_MIXED) {
+      // stage 1 -> X = Q_l
+      int r1 = mpj_stage1_run(n, A, lda, X, n, tol32, o.max_sweeps32, &sweeps32, &off32, S1, sm.partial, sm.dscal, s);
+      if (r1 < 0) {
+        st = r1;
+        goto done;
+      }
+      tm.mark(1);
+      // stage 2: Newton-Schulz -> X = Q_d
+      double* Xp = X;
+      double* Yp = Y;
+      if ((st = ns_steps_run(n, &Xp, M, &Yp, o.ns_steps, s)) != MPJ_OK) goto done;
+      tm.mark(2);
+      // stage 3: A_cond = Q_d^T (A Q_d) -> M (symmetric), Yp = A Q_d
+      if (mpj_gemm64(false, false, n, n, n, 1.0, A, lda, Xp, n, 0.0, nullptr, n, Yp, n, 0, s) != cudaSuccess ||
+          mpj_gemm64(true, false, n, n, n, 1.0, Xp, n, Yp, n, 0.0, nullptr, n, M, n, 1, s) != cudaSuccess) {
+        mpj_set_cuda_error(cudaGetLastError(), "transform", __LINE__);
+        st = MPJ_ECUDA;
+        goto done;
+      }
+      tm.mark(3);
+      Qd = Xp;
+      Ac = M;
+      V = Yp;
+    } else {
+      tm.mark(1);
+      tm.mark(2);
+      copy_mat<<<blocks_for((size_t)n * n), 256, 0, s>>>(A, lda, M, n, n);
+      tm.mark(3);
+      Ac = M;
+      V = Y;
+    }
+    // stage 4: FP64 sweeps from V = I
+    set_identity<<<blocks_for((size_t)n * n), 256, 0, s>>>(V, n, n);
+    {
+      int r4 = mpj_jacobi64_run(n, Ac, n, V, n, tol, o.ordering, o.max_sweeps64, &sweeps64, &offf, &offc, scratch, s);
+      if (r4 < 0) {
+        st = r4;
+        goto done;
+      }
+      if (r4 == MPJ_NOT_CONVERGED) st = MPJ_NOT_CONVERGED;
+    }
+    tm.mark(4);
+    // stage 5: W = diag(A_cond), sorted; Q = Q_d V with V's columns permuted
+    {
+      rank_diag<<<(n + 255) / 256, 256, 256 * sizeof(double), s>>>(Ac, n, n, o.sort, sm.rank, sm.w);
+      double* Vp = (double*)S1;  // the stage-1 area is free now
+      if (o.method == MPJ_METHOD_PLAIN) {
+        permute_cols<<<dim3((n + 255) / 256 > 16 ? 16 : (n + 255) / 256, n), 256, 0, s>>>(V, n, Q, ldq, n, sm.rank,
+                                                                                            sm.w, W);
+      } else {
+        permute_cols<<<dim3((n + 255) / 256 > 16 ? 16 : (n + 255) / 256, n), 256, 0, s>>>(V, n, Vp, n, n, sm.rank,
+                                                                                            sm.w, W);
+        if (mpj_gemm64(false, false, n, n, n, 1.0, Qd, n, Vp, n, 0.0, nullptr, n, Q, ldq, 0, s) != cudaSuccess) {
+          mpj_set_cuda_error(cudaGetLastError(), "final product", __LINE__);
+          st = MPJ_ECUDA;
+          goto done;
+        }
+      }
+      if (o.polish) {
+        // one more Newton-Schulz step on Q (not in the paper)
+        double* T = (o.method == MPJ_METHOD_PLAIN) ? X : Vp;
+        if (mpj_gemm64(true, false, n, n, n, 1.0, Q, ldq, Q, ldq, 0.0, nullptr, n, M, n, 1, s) != cudaSuccess ||
+            mpj_gemm64(false, false, n, n, n, -0.5, Q, ldq, M, n, 1.5, Q, ldq, T, n, 0, s) != cudaSuccess) {
+          mpj_set_cuda_error(cudaGetLastError(), "polish", __LINE__);
+          st = MPJ_ECUDA;
+          goto done;
+        }
+        copy_mat<<<blocks_for((size_t)n * n), 256, 0, s>>>(T, n, Q, ldq, n);
+      }
+      cudaError_t e = cudaGetLastError();
+      if (e != cudaSuccess) {
+        mpj_set_cuda_error(e, "finalize", __LINE__);
+        st = MPJ_ECUDA;
+        goto done;
+      }
+    }
+    tm.mark(5);
+  }
+done:
+  tm.mark(6);
+  tm.finish(info);
+  if (own) cudaFreeAsync(work, s);
+  {
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess && st >= 0) {
+      mpj_set_cuda_error(e, "final sync", __LINE__);
+      st = MPJ_ECUDA;
+    }
+  }
+  if (info) {
+    info->status = st;
+    info->sweeps32 = sweeps32;
+    info->sweeps64 = sweeps64;
+    info->ns_steps = (o.method == MPJ_METHOD_MIXED) ? o.ns_steps : 0;
+    info->off32 = off32;
+    info->off_final = offf;
+    info->off_cond = offc;
+  }
+  return st;
+}
+
+int mpj_syev(int n, const double* A, int lda, double* W, double* Q, double tol, void* stream) {
+  mpj_opts o;
+  mpj_opts_default(&o);
+  o.tol = tol;
+  return mpj_syev_ex(n, A, lda, W, Q, n, &o, nullptr, nullptr, 0, stream);
+}
+
+// ----------------------------------------------------------------- stage entry points
+int mpj_stage1(int n, const double* A, int lda, double* Ql, int ldq, double tol32, int max_sweeps, int* sweeps,
+               double* off32, void* stream) {
+  cudaStream_t s = (cudaStream_t)stream;
+  if (n <= 0 || !A || !Ql || lda < n || ldq < n) return MPJ_EINVAL;
+  size_t bytes = al(mpj_stage1_bytes(n)) + 4096;
+  void* w = nullptr;
+  if (cudaMallocAsync(&w, bytes, s) != cudaSuccess) return MPJ_ENOMEM;
+  double* partial = (double*)((char*)w + al(mpj_stage1_bytes(n)));
+  double* dscal = partial + 256;
+  int st = MPJ_OK;
+  double norm2 = 0;
+  if (tol32 <= 0) {
+    if (mpj_sumsq(A, lda, n, false, partial, dscal, nullptr, s) != cudaSuccess ||
+        cudaMemcpyAsync(&norm2, dscal, sizeof(double), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+      st = MPJ_ECUDA;
+    tol32 = (double)n * 0x1p-24 * std::sqrt(norm2);
+  }
+  if (st == MPJ_OK)
+    st = mpj_stage1_run(n, A, lda, Ql, ldq, tol32, max_sweeps > 0 ? max_sweeps : 15, sweeps, off32, w, partial, dscal,
+                        s);
+  cudaFreeAsync(w, s);
+  if (cudaStreamSynchronize(s) != cudaSuccess && st >= 0) st = MPJ_ECUDA;
+  return st;
+}
+
+int mpj_newton_schulz(int n, double* X, int ldx, int steps, void* stream) {
+  cudaStream_t s = (cudaStream_t)stream;
+  if (n <= 0 || !X || ldx < n || steps < 0) return MPJ_EINVAL;
+  void* w = nullptr;
+  size_t sq = al((size_t)n * n * sizeof(double));
+  if (cudaMallocAsync(&w, 3 * sq, s) != cudaSuccess) return MPJ_ENOMEM;
+  double* Xc = (double*)w;
+  double* M = (double*)((char*)w + sq);
+  double* Y = (double*)((char*)w + 2 * sq);
+  copy_mat<<<blocks_for((size_t)n * n), 256, 0, s>>>(X, ldx, Xc, n, n);
+  double* Xp = Xc;
+  double* Yp = Y;
+  int st = ns_steps_run(n, &Xp, M, &Yp, steps, s);
+  if (st == MPJ_OK) copy_mat<<<blocks_for((size_t)n * n), 256, 0, s>>>(Xp, n, X, ldx, n);
+  cudaFreeAsync(w, s);
+  if (cudaStreamSynchronize(s) != cudaSuccess && st >= 0) st = MPJ_ECUDA;
+  return st;
+}
+
+int mpj_precondition(int n, const double* A, int lda, const double* Qd, int ldq, double* Ac, int ldc, void* stream) {
+  cudaStream_t s = (cudaStream_t)stream;
+  if (n <= 0 || !A || !Qd || !Ac || lda < n || ldq < n || ldc < n) return MPJ_EINVAL;
+  void* w = nullptr;
+  if (cudaMallocAsync(&w, (size_t)n * n * sizeof(double), s) != cudaSuccess) return MPJ_ENOMEM;
+  double* Wt = (double*)w;
+  int st = MPJ_OK;
+  if (mpj_gemm64(false, false, n, n, n, 1.0, A, lda, Qd, ldq, 0.0, nullptr, n, Wt, n, 0, s) != cudaSuccess ||
+      mpj_gemm64(true, false, n, n, n, 1.0, Qd, ldq, Wt, n, 0.0, nullptr, n, Ac, ldc, 1, s) != cudaSuccess)
+    st = MPJ_ECUDA;
+  cudaFreeAsync(w, s);
+  if (cudaStreamSynchronize(s) != cudaSuccess && st >= 0) st = MPJ_ECUDA;
+  return st;
+}
+
+int mpj_jacobi64(int n, double* A, int lda, double* V, int ldv, double tol, int ordering, int max_sweeps, int* sweeps,
+                 double* off_final, void* stream) {
+  cudaStream_t s = (cudaStream_t)stream;
+  if (n <= 0 || !A || !V || lda < n || ldv < n) return MPJ_EINVAL;
+  if (ordering != MPJ_ORDER_CYCLIC && ordering != MPJ_ORDER_ROUND_ROBIN) return MPJ_EINVAL;
+  void* w = nullptr;
+  if (cudaMallocAsync(&w, mpj_jacobi64_scratch_bytes(n) + 4096, s) != cudaSuccess) return MPJ_ENOMEM;
+  int st = MPJ_OK;
+  if (tol <= 0) {
+    double* partial = (double*)w;
+    double* dscal = partial + 256;
+    double norm2 = 0;
+    if (mpj_sumsq(A, lda, n, false, partial, dscal, nullptr, s) != cudaSuccess ||
+        cudaMemcpyAsync(&norm2, dscal, sizeof(double), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+      st = MPJ_ECUDA;
+    tol = (double)n * 0x1p-53 * std::sqrt(norm2);
+  }
+  if (st == MPJ_OK)
+    st = mpj_jacobi64_run(n, A, lda, V, ldv, tol, ordering, max_sweeps > 0 ? max_sweeps : 30, sweeps, off_final, nullptr,
+                          w, s);
+  cudaFreeAsync(w, s);
+  if (cudaStreamSynchronize(s) != cudaSuccess && st >= 0) st = MPJ_ECUDA;
+  return st;
+}
+
+int mpj_dgemm(char transa, char transb, int m, int n, int k, double alpha, const double* A, int lda, const double* B,
+              int ldb, double beta, double* C, int ldc, void* stream) {
+  bool ta = (transa == 'T' || transa == 't'), tb = (transb == 'T' || transb == 't');
+  if (!ta && !(transa == 'N' || transa == 'n')) return MPJ_EINVAL;
+  if (!tb && !(transb == 'N' || transb == 'n')) return MPJ_EINVAL;
+  if (m < 0 || n < 0 || k < 0 || !A || !B || !C) return MPJ_EINVAL;
+  if (lda < (ta ? k : m) || ldb < (tb ? n : k) || ldc < m || lda < 1 || ldb < 1 || ldc < 1) return MPJ_EINVAL;
+  cudaError_t e = mpj_gemm64(ta, tb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, C, ldc, 0, (cudaStream_t)stream);
+  if (e != cudaSuccess) {
+    mpj_set_cuda_error(e, "mpj_dgemm", __LINE__);
+    return MPJ_ECUDA;
+  }
+  return MPJ_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,68 @@
+"""The C ABI: the library builds, loads and exports every entry point that
+include/*.h declares; host-side argument checks need no GPU."""
+import ctypes
+import glob
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="session")
+def libpath():
+    from paper_2509_00495_gb300 import build
+    return build.build()
+
+
+def declared_functions():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        src = open(h).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        for m in re.finditer(r"^\s*(?:const\s+)?[A-Za-z_][\w\s\*]*?\b(mpj_\w+)\s*\(", src, flags=re.M):
+            names.add(m.group(1))
+    return sorted(names)
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ["mpj_syev", "mpj_syev_ex", "mpj_syev_workspace", "mpj_syev_batched", "mpj_syev_backward",
+                     "mpj_status_str", "mpj_stage1", "mpj_newton_schulz", "mpj_precondition", "mpj_jacobi64",
+                     "mpj_dgemm", "mpj_opts_default", "mpj_last_cuda_error"]:
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(libpath):
+    L = ctypes.CDLL(libpath)
+    missing = [n for n in declared_functions() if not hasattr(L, n)]
+    assert not missing, missing
+
+
+def test_host_side_helpers_without_gpu(libpath):
+    from paper_2509_00495_gb300 import mpj
+    L = mpj.lib()
+    assert mpj.status_str(0) == "MPJ_OK"
+    assert mpj.status_str(-3) == "MPJ_ENONFINITE"
+    o = mpj.default_opts()
+    assert o.ordering == mpj.ORDER_ROUND_ROBIN and o.method == mpj.METHOD_MIXED and o.sort == 1
+    # workspace grows like n^2 and is zero for n = 0
+    assert mpj.syev_workspace(0) == 0
+    w1, w2 = mpj.syev_workspace(512), mpj.syev_workspace(1024)
+    assert 3.5 < w2 / w1 < 4.5
+    # argument errors are caught on the host before any CUDA call
+    assert L.mpj_syev(-1, None, 1, None, None, 0.0, None) == mpj.MPJ_EINVAL
+    assert L.mpj_syev(4, None, 4, None, None, 0.0, None) == mpj.MPJ_EINVAL
+    assert L.mpj_dgemm(b"X", b"N", 2, 2, 2, 1.0, None, 2, None, 2, 0.0, None, 2, None) == mpj.MPJ_EINVAL
+    assert L.mpj_jacobi64(4, ctypes.c_void_p(8), 2, ctypes.c_void_p(8), 4, 0.0, 1, 0, None, None, None) == mpj.MPJ_EINVAL
+    bad = mpj.default_opts(ordering=7)
+    assert L.mpj_syev_ex(4, ctypes.c_void_p(8), 4, ctypes.c_void_p(8), ctypes.c_void_p(8), 4, ctypes.byref(bad), None,
+                         None, 0, None) == mpj.MPJ_EINVAL
+
+
+def test_binding_refuses_cpu_tensors(libpath):
+    import torch
+    from paper_2509_00495_gb300 import mpj
+    with pytest.raises(TypeError):
+        mpj.syev(torch.eye(3, dtype=torch.float64))

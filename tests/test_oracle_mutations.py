@@ -34,6 +34,8 @@ MUTATIONS = {
     "backward_gap_sign": ("double gap = W[j] - W[i];", "double gap = W[i] - W[j];"),
     "backward_no_diag": ("g = dW ? dW[i] : 0.0;", "g = 0.0;"),
     "precondition_untransposed": ("orc_gemm_tn_d(n, n, n, Qd, ldq, W, n, Ac, ldc);", "orc_gemm_nn_d(n, n, n, Qd, ldq, W, n, Ac, ldc);"),
+    "block_local_map": ("int gy = ly < ORC_BLK ? I * ORC_BLK + ly : J * ORC_BLK + (ly - ORC_BLK);",
+                        "int gy = ly < ORC_BLK ? I * ORC_BLK + ly : J * ORC_BLK + ly;"),
     "float_pair_tau": ("float tau = (aqq - app) / (2.0f * apq);", "float tau = (aqq - app) / (apq);"),
 }
 

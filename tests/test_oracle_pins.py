@@ -405,3 +405,43 @@ def test_backward_rejects_repeated_eigenvalue():
     Q = np.eye(3)
     with pytest.raises(ZeroDivisionError):
         oracle.eigh_backward(np.array([1.0, 1.0, 2.0]), Q, dQ=np.ones((3, 3)))
+
+
+# ---------------------------------------------------------------- block round-robin (FP32 stage ordering)
+@pytest.mark.parametrize("n", [5, 32, 40, 70])
+def test_block_schedule_coverage(n):
+    sched = oracle.block_schedule(n)
+    B = oracle.BLOCK
+    N = ((n + 2 * B - 1) // (2 * B)) * 2 * B
+    nb = N // B
+    assert len(sched) == nb - 1
+    from collections import Counter
+    cnt = Counter()
+    for rnd in sched:
+        used = set()
+        for inner in rnd:  # one block pair: its index set is disjoint from the others of the round
+            idx = {i for pairs in inner for pq in pairs for i in pq}
+            assert not (idx & used)
+            used |= idx
+            for pairs in inner:
+                flat = [i for pq in pairs for i in pq]
+                assert len(flat) == len(set(flat))
+                cnt.update(pairs)
+    for p in range(n):
+        for q in range(p + 1, n):
+            same = p // B == q // B
+            assert cnt[(p, q)] == (nb - 1 if same else 1), (p, q)
+    assert set(cnt) == {(p, q) for p in range(n) for q in range(p + 1, n)}
+
+
+@pytest.mark.parametrize("n", [3, 6, 40])
+def test_block_ordering_jacobi_against_eigh(n):
+    A = inputs.randn_sym(n, 77 + n)
+    a, v, sw, rot, of, cap = oracle.jacobi(A, ordering=oracle.BLOCK_ROUND_ROBIN, tol=n * U_D * np.linalg.norm(A))
+    assert not cap
+    assert np.allclose(np.sort(np.diag(a)), np.linalg.eigh(A)[0], atol=32 * n * U_D * np.linalg.norm(A, 2))
+    assert np.linalg.norm(A @ v - v @ np.diag(np.diag(a))) <= 32 * n * U_D * np.linalg.norm(A, 2)
+    # FP32 variant of the same ordering reaches the FP32 level
+    a32, v32, sw32, _, of32, cap32 = oracle.jacobi(A, ordering=oracle.BLOCK_ROUND_ROBIN, tol=n * U_L * np.linalg.norm(A),
+                                                   skip_tol=U_L, dtype=np.float32)
+    assert not cap32 and of32 <= n * U_L * np.linalg.norm(A)
