@@ -90,6 +90,10 @@ const char* mpj_status_str(int status);
 /* Text of the last CUDA error seen by this thread inside the library. */
 const char* mpj_last_cuda_error(void);
 
+/* Diagnostic: number of CUDA kernels this library has enqueued since it was
+ * loaded (all threads).  The difference around a call counts its launches. */
+long long mpj_kernel_launches(void);
+
 /* Bytes of device workspace mpj_syev_ex needs for size n under `o` (NULL: defaults). */
 size_t mpj_syev_workspace(int n, const mpj_opts* o);
 

@@ -107,6 +107,7 @@ def _declare(L):
     L.orc_syev_plain.restype = _i
     L.orc_eigh_backward.argtypes = [_i, _dp, _dp, _i, _dp, _dp, _i, _dp, _i]
     L.orc_eigh_backward.restype = _i
+    L.orc_sample_rotations.argtypes = [_i, ctypes.c_void_p, _i, ctypes.c_void_p, _i, ctypes.c_longlong, _i]
 
 
 def _f64(a) -> np.ndarray:
@@ -312,6 +313,32 @@ def syev_plain(A, **kw):
     ci = _Info()
     _load().orc_syev_plain(n, _ptr(a), n, _ptr(W), _ptr(Q), n, ctypes.byref(_opts(n, **kw)), ctypes.byref(ci))
     return W, Q, _info(ci)
+
+
+def sample_rotations(A, nrot: int, dtype=np.float64) -> float:
+    """Run the first `nrot` rotations of a cyclic sweep on a copy of A (timing
+    sample); returns the seconds the C loop took."""
+    import time
+    n = A.shape[0]
+    a = np.array(A, dtype=dtype, order="F")
+    v = np.asfortranarray(np.eye(n, dtype=dtype))
+    L = _load()
+    t0 = time.perf_counter()
+    L.orc_sample_rotations(n, a.ctypes.data, n, v.ctypes.data, n, nrot, 0 if dtype == np.float64 else 1)
+    return time.perf_counter() - t0
+
+
+def sample_gemm(A, B) -> float:
+    """Time one oracle product A @ B (plain triple loop); returns seconds."""
+    import time
+    a, b = _f64(A), _f64(B)
+    m, k = a.shape
+    n = b.shape[1]
+    c = np.zeros((m, n), order="F")
+    L = _load()
+    t0 = time.perf_counter()
+    L.orc_gemm_nn_d(m, n, k, _ptr(a), m, _ptr(b), k, _ptr(c), m)
+    return time.perf_counter() - t0
 
 
 def eigh_backward(W, Q, dW=None, dQ=None) -> np.ndarray:

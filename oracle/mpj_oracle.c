@@ -206,6 +206,28 @@ static void symmetrize_f(int n, float* A, int lda) {
     }
 }
 
+/* Timing sample of the oracle's inner loop (for the CPU-baseline estimate
+ * only): the first `nrot` rotations of a cyclic-by-row sweep, each with its
+ * Algorithm 2 parameters and the paper's row/column/vector update, in FP64
+ * (dtype 0) or FP32 (dtype 1), without the skip test.                      */
+void orc_sample_rotations(int n, void* A, int lda, void* V, int ldv, long long nrot, int dtype) {
+  long long k = 0;
+  for (int p = 0; p < n - 1 && k < nrot; ++p)
+    for (int q = p + 1; q < n && k < nrot; ++q, ++k) {
+      if (dtype == 0) {
+        double* a = (double*)A;
+        double c, s;
+        orc_jacobi_pair_d(AT(a, lda, p, p), AT(a, lda, q, q), AT(a, lda, p, q), &c, &s);
+        rotate_d(n, a, lda, (double*)V, ldv, p, q, c, s);
+      } else {
+        float* a = (float*)A;
+        float c, s;
+        orc_jacobi_pair_f(AT(a, lda, p, p), AT(a, lda, q, q), AT(a, lda, p, q), &c, &s);
+        rotate_f(n, a, lda, (float*)V, ldv, p, q, c, s);
+      }
+    }
+}
+
 /* Cyclic Jacobi, Algorithm 4, FP64.
  *  - skip rule: pair (p,q) is rotated iff |a_pq| > skip_tol * sqrt(|a_pp a_qq|)
  *    (Algorithm 4's test; skip_tol = 2^-53 in the paper's experiments);

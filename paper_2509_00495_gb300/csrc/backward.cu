@@ -68,6 +68,7 @@ extern "C" int mpj_syev_backward(int batch, int n, const double* W, const double
   if (e == cudaSuccess) {  // T = sym(G) (into T), then M = Q T, then dA = M Q^T (symmetric)
     dim3 grid((n + 255) / 256 > 8 ? 8 : (n + 255) / 256, n, batch);
     adjoint_core<<<grid, 256, 0, s>>>(dQ ? M : nullptr, W, dW, n, T, flags);
+    mpj_count_launch();
     e = cudaGetLastError();
   }
   if (e == cudaSuccess) {

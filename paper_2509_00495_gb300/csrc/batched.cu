@@ -341,6 +341,7 @@ extern "C" int mpj_syev_batched(int batch, const int* n_host, const double* cons
   if (e == cudaSuccess) {
     batched_syev<<<grid, NTH, 0, s>>>(d_order, d_n, A_dev, W_dev, Q_dev, batch, tol, 15, 30, 2, work, per_cta,
                                       d_counter, d_sweeps, d_flags);
+    mpj_count_launch();
     e = cudaGetLastError();
   }
   if (e == cudaSuccess && sweeps_host)

@@ -160,3 +160,5 @@ MPJ_DEV float ld_cg(const float* p) { return __ldcg(p); }
 
 // Host-side helpers implemented in syev.cu
 void mpj_set_cuda_error(cudaError_t e, const char* what, int line);
+// Counts every kernel this library enqueues (diagnostic, mpj_kernel_launches).
+void mpj_count_launch();

@@ -173,5 +173,6 @@ cudaError_t mpj_gemm64_launch(const GemmArgs& g, bool ta, bool tb, int batch, cu
     dgemm_kernel<false, true><<<grid, NT, 0, stream>>>(g);
   else
     dgemm_kernel<true, true><<<grid, NT, 0, stream>>>(g);
+  mpj_count_launch();
   return cudaGetLastError();
 }

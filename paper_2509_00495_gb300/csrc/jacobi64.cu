@@ -286,18 +286,23 @@ cudaError_t mpj_sumsq(const double* A, int lda, int n, bool off_only, double* pa
     sumsq_partial<double, true><<<RED_CTAS, 256, 0, s>>>(A, lda, n, partial, flags);
   else
     sumsq_partial<double, false><<<RED_CTAS, 256, 0, s>>>(A, lda, n, partial, flags);
+  mpj_count_launch();
   reduce_partials<<<1, 256, 0, s>>>(partial, RED_CTAS, out);
+  mpj_count_launch();
   return cudaGetLastError();
 }
 
 cudaError_t mpj_sumsq32(const float* A, int lda, int n, double* partial, double* out, cudaStream_t s) {
   sumsq_partial<float, true><<<RED_CTAS, 256, 0, s>>>(A, lda, n, partial, nullptr);
+  mpj_count_launch();
   reduce_partials<<<1, 256, 0, s>>>(partial, RED_CTAS, out);
+  mpj_count_launch();
   return cudaGetLastError();
 }
 
 cudaError_t mpj_check_symmetric(const double* A, int lda, int n, unsigned* flags, cudaStream_t s) {
   check_symmetric<<<RED_CTAS, 256, 0, s>>>(A, lda, n, flags);
+  mpj_count_launch();
   return cudaGetLastError();
 }
 
@@ -339,6 +344,7 @@ int mpj_jacobi64_run(int n, double* A, int lda, double* V, int ldv, double tol, 
     long long k = 0;  // global step counter (record buffer parity)
     if (off > tol && n > 1) {
       rr_init_params<<<(half + 127) / 128, 128, 0, s>>>(A, lda, n, m, 0, skip, rec0);
+      mpj_count_launch();
       MPJ_CUDA_TRY(cudaGetLastError());
     }
     while (off > tol && n > 1) {
@@ -350,6 +356,7 @@ int mpj_jacobi64_run(int n, double* A, int lda, double* V, int ldv, double tol, 
         RotRec<double>* cur = (k & 1) ? rec1 : rec0;
         RotRec<double>* nxt = (k & 1) ? rec0 : rec1;
         rr_step64<<<grid, 256, 0, s>>>(A, lda, V, ldv, n, m, r, skip, cur, nxt, nt, n_atiles, vrc);
+        mpj_count_launch();
       }
       MPJ_CUDA_TRY(cudaGetLastError());
       ++sweeps;
@@ -365,6 +372,7 @@ int mpj_jacobi64_run(int n, double* A, int lda, double* V, int ldv, double tol, 
         break;
       }
       cyclic_sweep64<<<1, 1024, 0, s>>>(A, lda, V, ldv, n, skip, iscal);
+      mpj_count_launch();
       MPJ_CUDA_TRY(cudaGetLastError());
       int rotated = 0;
       ++sweeps;

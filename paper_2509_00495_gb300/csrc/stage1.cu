@@ -274,6 +274,7 @@ int mpj_stage1_run(int n, const double* A, int lda, double* Ql, int ldq, double 
   float* Sbuf = V32 + (size_t)N * N;
   float* Ubuf = Sbuf + (size_t)(nb / 2) * W2 * W2;
   init32<<<1024, 256, 0, s>>>(A, lda, n, N, A32, V32);
+  mpj_count_launch();
   MPJ_CUDA_TRY(cudaGetLastError());
   double off2 = 0.0;
   MPJ_CUDA_TRY(mpj_sumsq32(A32, N, N, partial, dscal, s));
@@ -291,7 +292,9 @@ int mpj_stage1_run(int n, const double* A, int lda, double* Ql, int ldq, double 
     }
     for (int R = 0; R < nb - 1; ++R) {
       solve32<<<npairs, 256, 0, s>>>(A32, N, nb, R, Sbuf, Ubuf);
+      mpj_count_launch();
       update32<<<grid_u, 256, 0, s>>>(A32, V32, N, nb, R, Sbuf, Ubuf, n_atiles);
+      mpj_count_launch();
     }
     MPJ_CUDA_TRY(cudaGetLastError());
     ++sweeps;
@@ -301,6 +304,7 @@ int mpj_stage1_run(int n, const double* A, int lda, double* Ql, int ldq, double 
     off = sqrt(off2);
   }
   widen<<<1024, 256, 0, s>>>(V32, N, n, Ql, ldq);
+  mpj_count_launch();
   MPJ_CUDA_TRY(cudaGetLastError());
   if (sweeps_out) *sweeps_out = sweeps;
   if (off_out) *off_out = off;

@@ -22,7 +22,12 @@
 #include "jacobi64.cuh"
 #include "stage1.cuh"
 
+#include <atomic>
+
 static thread_local char g_cuda_err[256] = "";
+static std::atomic<long long> g_launches{0};
+
+void mpj_count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
 void mpj_set_cuda_error(cudaError_t e, const char* what, int line) {
   snprintf(g_cuda_err, sizeof g_cuda_err, "%s (%d) in %s [syev line %d]", cudaGetErrorString(e), (int)e, what, line);
@@ -138,9 +143,11 @@ int blocks_for(size_t total) {
   return (int)(b > 4096 ? 4096 : (b < 1 ? 1 : b));
 }
 
+// CUDA events around the stages; marks that an early exit skipped are
+// recorded at the end so every elapsed-time query sees recorded events.
 struct Timer {
   cudaEvent_t ev[7];
-  int k = 0;
+  bool rec[7] = {false, false, false, false, false, false, false};
   bool on = false;
   cudaStream_t s;
   void start(cudaStream_t st) {
@@ -148,12 +155,18 @@ struct Timer {
     on = true;
     for (auto& e : ev) cudaEventCreate(&e);
     cudaEventRecord(ev[0], s);
+    rec[0] = true;
   }
   void mark(int i) {
-    if (on) cudaEventRecord(ev[i], s);
+    if (on) {
+      cudaEventRecord(ev[i], s);
+      rec[i] = true;
+    }
   }
   void finish(mpj_info* info) {
     if (!on) return;
+    for (int i = 1; i < 7; ++i)
+      if (!rec[i]) cudaEventRecord(ev[i], s);
     cudaEventSynchronize(ev[6]);
     if (info) {
       for (int i = 0; i < 5; ++i) {
@@ -226,6 +239,8 @@ const char* mpj_status_str(int st) {
 
 const char* mpj_last_cuda_error(void) { return g_cuda_err; }
 
+long long mpj_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
+
 size_t mpj_syev_workspace(int n, const mpj_opts* o) {
   (void)o;
   if (n <= 0) return 0;
@@ -272,17 +287,15 @@ int mpj_syev_ex(int n, const double* A, int lda, double* W, double* Q, int ldq, 
 
   tm.start(s);
   // a0: validation and norms
-  if (cudaMemsetAsync(sm.flags, 0, sizeof(unsigned), s) != cudaSuccess) {
-    st = MPJ_ECUDA;
-    goto done;
-  }
-  if (mpj_sumsq(A, lda, n, false, sm.partial, sm.dscal, sm.flags, s) != cudaSuccess) {
-    st = MPJ_ECUDA;
-    goto done;
-  }
-  if (o.check_symmetry && mpj_check_symmetric(A, lda, n, sm.flags, s) != cudaSuccess) {
-    st = MPJ_ECUDA;
-    goto done;
+  {
+    cudaError_t e = cudaMemsetAsync(sm.flags, 0, sizeof(unsigned), s);
+    if (e == cudaSuccess) e = mpj_sumsq(A, lda, n, false, sm.partial, sm.dscal, sm.flags, s);
+    if (e == cudaSuccess && o.check_symmetry) e = mpj_check_symmetric(A, lda, n, sm.flags, s);
+    if (e != cudaSuccess) {
+      mpj_set_cuda_error(e, "validation", __LINE__);
+      st = MPJ_ECUDA;
+      goto done;
+    }
   }
   cudaMemcpyAsync(&norm2, sm.dscal, sizeof(double), cudaMemcpyDeviceToHost, s);
   cudaMemcpyAsync(&flags, sm.flags, sizeof(unsigned), cudaMemcpyDeviceToHost, s);
@@ -335,12 +348,14 @@ int mpj_syev_ex(int n, const double* A, int lda, double* W, double* Q, int ldq, 
       tm.mark(1);
       tm.mark(2);
       copy_mat<<<blocks_for((size_t)n * n), 256, 0, s>>>(A, lda, M, n, n);
+      mpj_count_launch();
       tm.mark(3);
       Ac = M;
       V = Y;
     }
     // stage 4: FP64 sweeps from V = I
     set_identity<<<blocks_for((size_t)n * n), 256, 0, s>>>(V, n, n);
+    mpj_count_launch();
     {
       int r4 = mpj_jacobi64_run(n, Ac, n, V, n, tol, o.ordering, o.max_sweeps64, &sweeps64, &offf, &offc, scratch, s);
       if (r4 < 0) {
@@ -353,13 +368,16 @@ int mpj_syev_ex(int n, const double* A, int lda, double* W, double* Q, int ldq, 
     // stage 5: W = diag(A_cond), sorted; Q = Q_d V with V's columns permuted
     {
       rank_diag<<<(n + 255) / 256, 256, 256 * sizeof(double), s>>>(Ac, n, n, o.sort, sm.rank, sm.w);
+      mpj_count_launch();
       double* Vp = (double*)S1;  // the stage-1 area is free now
       if (o.method == MPJ_METHOD_PLAIN) {
         permute_cols<<<dim3((n + 255) / 256 > 16 ? 16 : (n + 255) / 256, n), 256, 0, s>>>(V, n, Q, ldq, n, sm.rank,
                                                                                             sm.w, W);
+        mpj_count_launch();
       } else {
         permute_cols<<<dim3((n + 255) / 256 > 16 ? 16 : (n + 255) / 256, n), 256, 0, s>>>(V, n, Vp, n, n, sm.rank,
                                                                                             sm.w, W);
+        mpj_count_launch();
         if (mpj_gemm64(false, false, n, n, n, 1.0, Qd, n, Vp, n, 0.0, nullptr, n, Q, ldq, 0, s) != cudaSuccess) {
           mpj_set_cuda_error(cudaGetLastError(), "final product", __LINE__);
           st = MPJ_ECUDA;
@@ -376,6 +394,7 @@ int mpj_syev_ex(int n, const double* A, int lda, double* W, double* Q, int ldq, 
           goto done;
         }
         copy_mat<<<blocks_for((size_t)n * n), 256, 0, s>>>(T, n, Q, ldq, n);
+        mpj_count_launch();
       }
       cudaError_t e = cudaGetLastError();
       if (e != cudaSuccess) {
@@ -453,10 +472,14 @@ int mpj_newton_schulz(int n, double* X, int ldx, int steps, void* stream) {
   double* M = (double*)((char*)w + sq);
   double* Y = (double*)((char*)w + 2 * sq);
   copy_mat<<<blocks_for((size_t)n * n), 256, 0, s>>>(X, ldx, Xc, n, n);
+  mpj_count_launch();
   double* Xp = Xc;
   double* Yp = Y;
   int st = ns_steps_run(n, &Xp, M, &Yp, steps, s);
-  if (st == MPJ_OK) copy_mat<<<blocks_for((size_t)n * n), 256, 0, s>>>(Xp, n, X, ldx, n);
+  if (st == MPJ_OK) {
+    copy_mat<<<blocks_for((size_t)n * n), 256, 0, s>>>(Xp, n, X, ldx, n);
+    mpj_count_launch();
+  }
   cudaFreeAsync(w, s);
   if (cudaStreamSynchronize(s) != cudaSuccess && st >= 0) st = MPJ_ECUDA;
   return st;
