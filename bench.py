@@ -162,6 +162,7 @@ def main():
     ap.add_argument("--no-plain", action="store_true", help="skip the plain FP64 Jacobi timing")
     ap.add_argument("--no-extras", action="store_true", help="skip the batched and backward workloads")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end timing")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--ref-step-seconds", type=float, default=8.0)
     ap.add_argument("--ref-sweeps32", type=int, default=8)
@@ -256,7 +257,7 @@ def main():
     W_host = torch.empty(n, dtype=torch.float64).pin_memory()
     Q_host = torch.empty(n, n, dtype=torch.float64).pin_memory()
     A_e2e = torch.empty_like(A)
-    e2e_steps = max(1, min(args.steps, 3))
+    e2e_steps = 0 if args.no_e2e else max(1, min(args.steps, 3))
     torch.cuda.synchronize()
     barrier()
     t0 = time.perf_counter()
@@ -271,8 +272,8 @@ def main():
         t = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         e2e_s = t.item()
-    e2e = {"value": world * e2e_steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": n * n * 8,
-           "d2h_bytes_per_step": n * 8 + n * n * 8}
+    e2e = {"value": world * e2e_steps / e2e_s if e2e_steps else None, "unit": UNIT,
+           "h2d_bytes_per_step": n * n * 8, "d2h_bytes_per_step": n * 8 + n * n * 8}
 
     info = step_info[-1]
     ms_mixed = statistics.median(step_ms)
