@@ -49,7 +49,8 @@ typedef enum {
   MPJ_ENOMEM = -5,        /* workspace allocation failed */
   MPJ_EDEGENERATE = -6,   /* backward: w_i == w_j for i != j with a nonzero coupling */
   MPJ_EWORKSPACE = -7,    /* caller workspace too small (see mpj_syev_workspace) */
-  MPJ_ETIMEOUT = -8       /* a device-side barrier gave up after its iteration limit */
+  MPJ_ETIMEOUT = -8,      /* a device-side barrier gave up after its iteration limit */
+  MPJ_ETOOLARGE = -9      /* n exceeds the fixed scratch of an allocation-free entry point */
 } mpj_status;
 
 enum { MPJ_ORDER_CYCLIC = 0, MPJ_ORDER_ROUND_ROBIN = 1 };
@@ -153,6 +154,27 @@ int mpj_precondition(int n, const double* A_dev, int lda, const double* Qd_dev, 
  * Returns MPJ_NOT_CONVERGED at the cap. */
 int mpj_jacobi64(int n, double* A_dev, int lda, double* V_dev, int ldv, double tol, int ordering, int max_sweeps,
                  int* sweeps, double* off_final, void* stream);
+
+/* Allocation-free variant of mpj_jacobi64 (the paper has no counterpart).
+ * For callers that may not allocate device memory during the call: code that
+ * runs with its whole memory budget already committed, latency-critical
+ * loops that must stay clear of the allocator, or hosts where allocation
+ * calls are not allowed at that point.  Same arguments, behaviour and results
+ * as mpj_jacobi64, but the sweep's scratch (rotation records and reduction
+ * partials, about 32 n + 3 KB bytes) lives in one fixed array of
+ * MPJ_NOALLOC_SCRATCH_BYTES bytes in device memory, reserved in every GPU
+ * that loads the library until the process exits; no cudaMalloc, cudaFree or
+ * allocating library routine is called.  n > MPJ_NOALLOC_MAX_N returns
+ * MPJ_ETOOLARGE before any work.  The first call on a device looks up the
+ * array's device address (once per device, with that device current); make
+ * that first call before any stream capture.  All calls share the one array:
+ * calls whose work overlaps on the GPU (other streams, other host threads)
+ * race on it and must be serialized by the caller.  Every scratch word is
+ * written before it is read, so nothing carries over between calls. */
+#define MPJ_NOALLOC_MAX_N 8192
+#define MPJ_NOALLOC_SCRATCH_BYTES 266240
+int mpj_jacobi64_noalloc(int n, double* A_dev, int lda, double* V_dev, int ldv, double tol, int ordering,
+                         int max_sweeps, int* sweeps, double* off_final, void* stream);
 
 /* FP64 matrix product on the library's DMMA kernel:
  * C = alpha op(A) op(B) + beta C, op(X) = X or X^T (trans = 'N' or 'T'),

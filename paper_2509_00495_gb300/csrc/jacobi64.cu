@@ -388,3 +388,75 @@ int mpj_jacobi64_run(int n, double* A, int lda, double* V, int ldv, double tol, 
   if (off_out) *off_out = off;
   return status;
 }
+
+// ---------------------------------------------------------------------------
+// Allocation-free entry point (see mpj_jacobi64_noalloc in mpjacobi.h): the
+// sweep scratch lives in this file-scope device array instead of memory from
+// cudaMallocAsync.  In host code `g_noalloc_scratch` names a host-side shadow,
+// not device memory, so the kernels get the device address looked up with
+// cudaGetSymbolAddress, once per device, with that device current.
+#include <mutex>
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[MPJ_NOALLOC_SCRATCH_BYTES];
+
+namespace {
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+void* g_noalloc_ptr[kMaxDevices] = {nullptr};
+
+int noalloc_scratch_for_current_device(void** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) {
+    mpj_set_cuda_error(e, "cudaGetDevice", __LINE__);
+    return MPJ_ECUDA;
+  }
+  if (dev < 0 || dev >= kMaxDevices) return MPJ_EINVAL;
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p) {
+      mpj_set_cuda_error(e, "cudaGetSymbolAddress(g_noalloc_scratch)", __LINE__);
+      return MPJ_ECUDA;
+    }
+    g_noalloc_ptr[dev] = p;
+  }
+  *out = g_noalloc_ptr[dev];
+  return MPJ_OK;
+}
+}  // namespace
+
+extern "C" int mpj_jacobi64_noalloc(int n, double* A, int lda, double* V, int ldv, double tol, int ordering,
+                                    int max_sweeps, int* sweeps, double* off_final, void* stream) {
+  cudaStream_t s = (cudaStream_t)stream;
+  if (n <= 0 || !A || !V || lda < n || ldv < n) return MPJ_EINVAL;
+  if (ordering != MPJ_ORDER_CYCLIC && ordering != MPJ_ORDER_ROUND_ROBIN) return MPJ_EINVAL;
+  if (n > MPJ_NOALLOC_MAX_N || mpj_jacobi64_scratch_bytes(n) > (size_t)MPJ_NOALLOC_SCRATCH_BYTES)
+    return MPJ_ETOOLARGE;
+  void* w = nullptr;
+  int st = noalloc_scratch_for_current_device(&w);
+  if (st != MPJ_OK) return st;
+  if (tol <= 0) {
+    // default tolerance n 2^-53 ||A||_F; the reduction uses the front of the scratch
+    double* partial = (double*)w;
+    double* dscal = partial + RED_CTAS;
+    double norm2 = 0;
+    cudaError_t e = mpj_sumsq(A, lda, n, false, partial, dscal, nullptr, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&norm2, dscal, sizeof(double), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+      mpj_set_cuda_error(e, "mpj_jacobi64_noalloc norm", __LINE__);
+      return MPJ_ECUDA;
+    }
+    tol = (double)n * 0x1p-53 * sqrt(norm2);
+  }
+  st = mpj_jacobi64_run(n, A, lda, V, ldv, tol, ordering, max_sweeps > 0 ? max_sweeps : 30, sweeps, off_final, nullptr,
+                        w, s);
+  cudaError_t e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess && st >= 0) {
+    mpj_set_cuda_error(e, "mpj_jacobi64_noalloc sync", __LINE__);
+    st = MPJ_ECUDA;
+  }
+  return st;
+}

@@ -233,6 +233,7 @@ const char* mpj_status_str(int st) {
     case MPJ_EDEGENERATE: return "MPJ_EDEGENERATE";
     case MPJ_EWORKSPACE: return "MPJ_EWORKSPACE";
     case MPJ_ETIMEOUT: return "MPJ_ETIMEOUT";
+    case MPJ_ETOOLARGE: return "MPJ_ETOOLARGE";
     default: return "MPJ_UNKNOWN";
   }
 }
