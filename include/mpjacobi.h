@@ -67,11 +67,15 @@ typedef struct {
   int polish;        /* 1: one more FP64 Newton-Schulz step on the final Q (not in the paper) */
   int sort;          /* 1 (default): W ascending, Q's columns permuted to match              */
   int check_symmetry;/* 1: fail with MPJ_ENOTSYM unless A is exactly symmetric               */
+  int precond_passes;/* mixed method: 1 (default) = Algorithm 9; 2 = stages 1-3 applied again to
+                        A_cond (FP32 Jacobi on fl32(A_cond), Newton-Schulz, Q_d2^T A_cond Q_d2,
+                        Q_d = Q_d1 Q_d2) before the FP64 sweeps -- not in the paper            */
 } mpj_opts;
 
 typedef struct {
   int status;        /* mpj_status of the solve                                               */
   int sweeps32;      /* stage-1 (FP32) sweeps                                                 */
+  int sweeps32_pass2;/* stage-1 sweeps of the second preconditioning pass (0 if not run)      */
   int sweeps64;      /* FP64 sweeps (the quantity the paper reports as "iterations")          */
   int ns_steps;      /* Newton-Schulz steps applied                                           */
   double norm_fro;   /* ||A||_F                                                               */
@@ -160,10 +164,12 @@ int mpj_jacobi64(int n, double* A_dev, int lda, double* V_dev, int ldv, double t
  * runs with its whole memory budget already committed, latency-critical
  * loops that must stay clear of the allocator, or hosts where allocation
  * calls are not allowed at that point.  Same arguments, behaviour and results
- * as mpj_jacobi64, but the sweep's scratch (rotation records and reduction
- * partials, about 32 n + 3 KB bytes) lives in one fixed array of
- * MPJ_NOALLOC_SCRATCH_BYTES bytes in device memory, reserved in every GPU
- * that loads the library until the process exits; no cudaMalloc, cudaFree or
+ * as mpj_jacobi64, but the sweep's scratch (rotation records, scale vectors,
+ * reduction partials and a batch of rotation multipliers for V: about
+ * (72 + 8 r) n bytes with r rounds per V batch, r = 64 down to 1 as n grows)
+ * lives in one fixed array of MPJ_NOALLOC_SCRATCH_BYTES bytes in device
+ * memory, reserved in every GPU that loads the library until the process
+ * exits; no cudaMalloc, cudaFree or
  * allocating library routine is called.  n > MPJ_NOALLOC_MAX_N returns
  * MPJ_ETOOLARGE before any work.  The first call on a device looks up the
  * array's device address (once per device, with that device current); make
@@ -172,7 +178,7 @@ int mpj_jacobi64(int n, double* A_dev, int lda, double* V_dev, int ldv, double t
  * race on it and must be serialized by the caller.  Every scratch word is
  * written before it is read, so nothing carries over between calls. */
 #define MPJ_NOALLOC_MAX_N 8192
-#define MPJ_NOALLOC_SCRATCH_BYTES 266240
+#define MPJ_NOALLOC_SCRATCH_BYTES 1048576
 int mpj_jacobi64_noalloc(int n, double* A_dev, int lda, double* V_dev, int ldv, double tol, int ordering,
                          int max_sweeps, int* sweeps, double* off_final, void* stream);
 

@@ -3,15 +3,23 @@
 //
 // Two orderings:
 //  * round-robin (the fast form): each sweep is m-1 rounds of m/2 disjoint
-//    pairs (circle method, see rr_slot); one kernel launch per round updates
-//    the whole matrix.  The matrix splits into 2x2 blocks indexed by
-//    (slot a, slot b); block (a,b) becomes J_a^T B J_b.  Blocks with a >= b
-//    are computed (in 16x16-slot tiles) and written together with their mirror,
-//    so A stays exactly symmetric and the FP64 work is 2 FMA per entry of the
-//    lower half per rotation side.  The same launch also builds the rotation
-//    records of the next round: the coupling a_ij of a next-round pair (i,j) is
-//    an entry of some block updated here, and the new diagonals come from this
-//    round's records, so each round needs one launch and no extra pass.
+//    pairs (circle method, see rr_slot).  The matrix splits into 2x2 blocks
+//    indexed by (slot a, slot b); block (a,b) becomes J_a^T B J_b.  Blocks with
+//    a >= b are computed in 16x16-slot tiles and written with their mirror, so
+//    A stays exactly symmetric.  Rotations are applied in scaled form: off the
+//    diagonal A = D At D and V = Vt D with one scale vector d (kept in
+//    double-double), so a rotation costs one FMA per entry and side,
+//      At_x <- At_x - mx At_y,   At_y <- At_y + my At_x,
+//    mx = tau d_y / d_x, my = tau d_x / d_y, tau = +-t, while d_x, d_y take the
+//    factor c = 1/sqrt(1 + t^2) (the paper's rotation, Sec. 3.1.1, with the
+//    scaling split off).  The true diagonal is kept in A's diagonal entries.
+//    One launch per round updates A and, from the coupling entries it has
+//    just written, builds the next round's rotation records.  V is updated in
+//    batches: each round's multipliers go to a history buffer and a second
+//    kernel applies up to 64 rounds to row chunks of V held in shared memory,
+//    so V is read and written once per batch instead of once per round.
+//    Every 512 rounds and at the end of a sweep the scales are folded back
+//    into A and V (d = 1), which keeps d far from underflow.
 //  * cyclic-by-row (the paper's ordering, the faithful form): pairs
 //    (0,1),(0,2),...,(n-2,n-1) one after another, each applied as the paper's
 //    row update, then column update, then vector update, with the paper's
@@ -26,13 +34,66 @@
 
 namespace {
 
-constexpr int TS = 16;       // slots per tile side (a 32 x 32 entry region)
-constexpr int VROWS = 256;   // rows of V per V work item
-constexpr int VSLOTS = 8;    // slots per V work item
+constexpr int TS = 16;        // slots per tile side (a 32 x 32 entry region)
 constexpr int RED_CTAS = 256;
+constexpr int RV_MAX = 64;    // rounds per batched V update
+constexpr int RS = 512;       // rounds between scale folds
 
-__global__ void rr_init_params(const double* __restrict__ A, int lda, int n, int m, int r, double skip,
-                               RotRec<double>* __restrict__ rec) {
+// Scaled-rotation record of one slot (see the file comment); mx == my == 0
+// means "not rotated".  dx, dy: true diagonal entries after the rotation.
+struct FRec {
+  double mx, my, dx, dy;
+};
+
+// Bit test instead of an FP64 compare: on this GPU FP64 compares issue on the
+// same slow FP64 pipe as the FMAs.  "Not rotated" records hold +0.0 exactly.
+MPJ_DEV bool frec_rotated(const FRec& r) {
+  return (__double_as_longlong(r.mx) | __double_as_longlong(r.my)) != 0;
+}
+
+// c - 1 of a record: t^2 = mx my.
+MPJ_DEV double frec_cm1(const FRec& r) {
+  double t2 = r.mx * r.my;
+  double h = sqrt(1.0 + t2);
+  return -t2 / (h * (1.0 + h));
+}
+
+// d' = d (1 + cm1) in double-double (Fast2Sum renormalization, |cm1| < 0.3).
+MPJ_DEV double2 dd_scale(double2 d, double cm1) {
+  double sum = fma(cm1, d.x, fma(cm1, d.y, d.y));
+  double hi = d.x + sum;
+  double lo = sum - (hi - d.x);
+  return make_double2(hi, lo);
+}
+
+// Record of pair (i, j) of round r from true diagonals di, dj, true coupling
+// aij and the scales si, sj the round will see.  Returns the slot.
+MPJ_DEV int rr_make_frec(int m, int n, int r, int i, int j, double di, double dj, double aij, double si, double sj,
+                         double skip, FRec& rec) {
+  int slot, iy;
+  rr_slot_of(m, r, i, slot, iy);
+  int p = i < j ? i : j, q = i < j ? j : i;
+  double app = (p == i) ? di : dj, aqq = (p == i) ? dj : di;
+  double t, cm1, s;
+  bool rot = (q < n) && jacobi_pair<double>(app, aqq, aij, skip, t, cm1, s);
+  double np = app, nq = aqq;
+  if (rot) {
+    np = app - t * aij;
+    nq = aqq + t * aij;
+  }
+  int x = iy ? j : i;
+  double tau = (x == p) ? t : -t;
+  double sx = (x == i) ? si : sj, sy = (x == i) ? sj : si;
+  rec.mx = rot ? tau * (sy / sx) : 0.0;
+  rec.my = rot ? tau * (sx / sy) : 0.0;
+  rec.dx = (x == p) ? np : nq;
+  rec.dy = (x == p) ? nq : np;
+  return slot;
+}
+
+// Records of round r from A's true entries when all scales are 1.
+__global__ void rr_init_frec(const double* __restrict__ A, int lda, int n, int m, int r, double skip,
+                             FRec* __restrict__ rec) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= m / 2) return;
   int x, y;
@@ -40,140 +101,220 @@ __global__ void rr_init_params(const double* __restrict__ A, int lda, int n, int
   double dx = x < n ? A[(size_t)x * lda + x] : 0.0;
   double dy = y < n ? A[(size_t)y * lda + y] : 0.0;
   double axy = (x < n && y < n) ? A[(size_t)y * lda + x] : 0.0;
-  RotRec<double> rr;
-  rr_make_rec<double>(m, n, r, x, y, dx, dy, axy, skip, rr);
-  rec[i] = rr;
+  FRec fr;
+  rr_make_frec(m, n, r, x, y, dx, dy, axy, 1.0, 1.0, skip, fr);
+  rec[i] = fr;
 }
 
-__device__ __forceinline__ void tri_tile(int t, int nt, int& ti, int& tj) {
-  // t enumerates the lower-triangular tiles column by column
-  tj = 0;
-  while (t >= nt - tj) {
-    t -= nt - tj;
-    ++tj;
-  }
-  ti = tj + t;
+__global__ void d_reset(double2* __restrict__ d, int n) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) d[i] = make_double2(1.0, 0.0);
 }
 
-__global__ void __launch_bounds__(256) rr_step64(double* __restrict__ A, int lda, double* __restrict__ V, int ldv,
-                                                 int n, int m, int r, double skip,
-                                                 const RotRec<double>* __restrict__ rec,
-                                                 RotRec<double>* __restrict__ rec_next, int nt, int n_atiles,
-                                                 int v_row_chunks) {
+// Lower-triangular tiles (ti >= tj) enumerated row by row: t = ti (ti+1)/2 + tj.
+__device__ __forceinline__ void tri_tile(int t, int& ti, int& tj) {
+  int r = (int)((sqrtf(8.0f * (float)t + 1.0f) - 1.0f) * 0.5f);
+  while (r * (r + 1) / 2 > t) --r;
+  while ((r + 1) * (r + 2) / 2 <= t) ++r;
+  ti = r;
+  tj = t - r * (r + 1) / 2;
+}
+
+// One round on A (scaled form) + next round's records + this round's V multipliers.
+__global__ void __launch_bounds__(256) rr_step64(double* __restrict__ A, int lda, int n, int m, int r, double skip,
+                                                 const FRec* __restrict__ rec, FRec* __restrict__ rec_next,
+                                                 const double2* __restrict__ dcur, double2* __restrict__ dnext,
+                                                 double2* __restrict__ hist_row) {
   const int half = m / 2;
   const int rn = (r + 1 == m - 1) ? 0 : r + 1;  // next round (wraps into the next sweep)
-  int item = blockIdx.x;
-  if (item < n_atiles) {
-    int ti, tj;
-    tri_tile(item, nt, ti, tj);
-    int a = ti * TS + (threadIdx.x % TS);
-    int b = tj * TS + (threadIdx.x / TS);
-    if (a >= half || b >= half || a < b) return;
-    int xa, ya, xb, yb;
-    rr_slot(m, r, a, xa, ya);
-    rr_slot(m, r, b, xb, yb);
-    RotRec<double> ra = rec[a];
-    bool rota = rec_rotated(ra.cm1, ra.sig);
-    bool vxa = xa < n, vya = ya < n;
-    if (a == b) {
-      // the pair's own 2x2 block: new diagonal from the record, a_xy annihilated
-      double axy;
-      if (rota) {
-        A[(size_t)xa * lda + xa] = ra.dx;
-        A[(size_t)ya * lda + ya] = ra.dy;
-        A[(size_t)ya * lda + xa] = 0.0;
-        A[(size_t)xa * lda + ya] = 0.0;
-        axy = 0.0;
-      } else {
-        axy = (vxa && vya) ? A[(size_t)ya * lda + xa] : 0.0;
-      }
-      // next-round records that this block owns:
-      // (1) the unpaired index of round rn when n is odd (slot 0 pairs it with the dummy)
-      if ((n & 1) && (xa == rn || ya == rn)) {
-        RotRec<double> z;
-        z.cm1 = 0.0;
-        z.sig = 0.0;
-        z.dx = (xa == rn) ? ra.dx : ra.dy;
-        z.dy = 0.0;
-        rec_next[0] = z;
-      }
-      // (2) m == 2: the same pair again in the next sweep
-      if (vxa && vya && rr_partner(m, rn, xa) == ya) {
-        RotRec<double> nr;
-        int s = rr_make_rec<double>(m, n, rn, xa, ya, ra.dx, ra.dy, axy, skip, nr);
-        rec_next[s] = nr;
-      }
-      return;
+  int ti, tj;
+  tri_tile(blockIdx.x, ti, tj);
+  const int a = ti * TS + (threadIdx.x % TS);
+  const int b = tj * TS + (threadIdx.x / TS);
+  if (a >= half || b >= half || a < b) return;
+  int xa, ya;
+  rr_slot(m, r, a, xa, ya);
+  const FRec ra = rec[a];
+  const bool rota = frec_rotated(ra);
+  const bool vxa = xa < n, vya = ya < n;
+  if (a == b) {
+    const double cm1 = rota ? frec_cm1(ra) : 0.0;
+    double2 sx = vxa ? dd_scale(dcur[xa], cm1) : make_double2(1.0, 0.0);
+    double2 sy = vya ? dd_scale(dcur[ya], cm1) : make_double2(1.0, 0.0);
+    if (vxa) dnext[xa] = sx;
+    if (vya) dnext[ya] = sy;
+    hist_row[a] = make_double2(ra.mx, ra.my);
+    double axy_s;  // scaled coupling after the round
+    if (rota) {
+      A[(size_t)xa * lda + xa] = ra.dx;
+      A[(size_t)ya * lda + ya] = ra.dy;
+      A[(size_t)ya * lda + xa] = 0.0;
+      A[(size_t)xa * lda + ya] = 0.0;
+      axy_s = 0.0;
+    } else {
+      axy_s = (vxa && vya) ? A[(size_t)ya * lda + xa] : 0.0;
     }
-    RotRec<double> rb = rec[b];
-    bool rotb = rec_rotated(rb.cm1, rb.sig);
-    bool vxb = xb < n, vyb = yb < n;
-    size_t cxb = (size_t)xb * lda, cyb = (size_t)yb * lda;
-    double vxx = (vxa && vxb) ? A[cxb + xa] : 0.0;
-    double vxy = (vxa && vyb) ? A[cyb + xa] : 0.0;
-    double vyx = (vya && vxb) ? A[cxb + ya] : 0.0;
-    double vyy = (vya && vyb) ? A[cyb + ya] : 0.0;
-    if (rota) {  // rows x_a, y_a: J_a^T
-      rot_apply(ra.cm1, ra.sig, vxx, vyx);
-      rot_apply(ra.cm1, ra.sig, vxy, vyy);
+    // the unpaired index of round rn when n is odd (slot 0 pairs it with the dummy)
+    if ((n & 1) && (xa == rn || ya == rn)) {
+      FRec z;
+      z.mx = 0.0;
+      z.my = 0.0;
+      z.dx = (xa == rn) ? ra.dx : ra.dy;
+      z.dy = 0.0;
+      rec_next[0] = z;
     }
-    if (rotb) {  // columns x_b, y_b: J_b
-      rot_apply(rb.cm1, rb.sig, vxx, vxy);
-      rot_apply(rb.cm1, rb.sig, vyx, vyy);
-    }
-    if (rota || rotb) {
-      if (vxa && vxb) {
-        A[cxb + xa] = vxx;
-        A[(size_t)xa * lda + xb] = vxx;
-      }
-      if (vxa && vyb) {
-        A[cyb + xa] = vxy;
-        A[(size_t)xa * lda + yb] = vxy;
-      }
-      if (vya && vxb) {
-        A[cxb + ya] = vyx;
-        A[(size_t)ya * lda + xb] = vyx;
-      }
-      if (vya && vyb) {
-        A[cyb + ya] = vyy;
-        A[(size_t)ya * lda + yb] = vyy;
-      }
-    }
-    // next-round records owned by this block
-#pragma unroll
-    for (int side = 0; side < 2; ++side) {
-      int i = side ? ya : xa;
-      if (i >= n) continue;
-      int j = rr_partner(m, rn, i);
-      if (j >= n || (j != xb && j != yb)) continue;
-      double di = side ? ra.dy : ra.dx;
-      double dj = (j == xb) ? rb.dx : rb.dy;
-      double aij = side ? ((j == xb) ? vyx : vyy) : ((j == xb) ? vxx : vxy);
-      RotRec<double> nr;
-      int s = rr_make_rec<double>(m, n, rn, i, j, di, dj, aij, skip, nr);
-      rec_next[s] = nr;
+    // m == 2: the same pair again in the next sweep
+    if (vxa && vya && rr_partner(m, rn, xa) == ya) {
+      FRec nr;
+      int sl = rr_make_frec(m, n, rn, xa, ya, ra.dx, ra.dy, axy_s * sx.x * sy.x, sx.x, sy.x, skip, nr);
+      rec_next[sl] = nr;
     }
     return;
   }
-  // V work item: rows [rc*VROWS, +VROWS), slots [sc*VSLOTS, +VSLOTS)
-  int v = item - n_atiles;
-  int rc = v % v_row_chunks, sc = v / v_row_chunks;
-  int i = rc * VROWS + threadIdx.x;
-  if (i >= n) return;
-#pragma unroll 2
-  for (int k = 0; k < VSLOTS; ++k) {
-    int b = sc * VSLOTS + k;
-    if (b >= half) break;
-    RotRec<double> rb = rec[b];
-    if (!rec_rotated(rb.cm1, rb.sig)) continue;
-    int xb, yb;
-    rr_slot(m, r, b, xb, yb);
-    double* px = V + (size_t)xb * ldv + i;
-    double* py = V + (size_t)yb * ldv + i;
-    double vx = *px, vy = *py;
-    rot_apply(rb.cm1, rb.sig, vx, vy);
-    *px = vx;
-    *py = vy;
+  int xb, yb;
+  rr_slot(m, r, b, xb, yb);
+  const FRec rb = rec[b];
+  const bool rotb = frec_rotated(rb);
+  const bool vxb = xb < n, vyb = yb < n;
+  // next-round pairs hosted by this block: (x_a or y_a) with (x_b or y_b)
+  int jx = vxa ? rr_partner(m, rn, xa) : -1;
+  int jy = vya ? rr_partner(m, rn, ya) : -1;
+  bool nx = jx >= 0 && jx < n && (jx == xb || jx == yb);
+  bool ny = jy >= 0 && jy < n && (jy == xb || jy == yb);
+  if (!rota && !rotb && !nx && !ny) return;
+  size_t cxb = (size_t)xb * lda, cyb = (size_t)yb * lda;
+  double vxx = (vxa && vxb) ? A[cxb + xa] : 0.0;
+  double vxy = (vxa && vyb) ? A[cyb + xa] : 0.0;
+  double vyx = (vya && vxb) ? A[cxb + ya] : 0.0;
+  double vyy = (vya && vyb) ? A[cyb + ya] : 0.0;
+  if (rota) {  // rows x_a, y_a
+    double t0 = fma(-ra.mx, vyx, vxx), t1 = fma(ra.my, vxx, vyx);
+    double t2 = fma(-ra.mx, vyy, vxy), t3 = fma(ra.my, vxy, vyy);
+    vxx = t0;
+    vyx = t1;
+    vxy = t2;
+    vyy = t3;
+  }
+  if (rotb) {  // columns x_b, y_b
+    double t0 = fma(-rb.mx, vxy, vxx), t1 = fma(rb.my, vxx, vxy);
+    double t2 = fma(-rb.mx, vyy, vyx), t3 = fma(rb.my, vyx, vyy);
+    vxx = t0;
+    vxy = t1;
+    vyx = t2;
+    vyy = t3;
+  }
+  if (rota || rotb) {
+    if (vxa && vxb) {
+      A[cxb + xa] = vxx;
+      A[(size_t)xa * lda + xb] = vxx;
+    }
+    if (vxa && vyb) {
+      A[cyb + xa] = vxy;
+      A[(size_t)xa * lda + yb] = vxy;
+    }
+    if (vya && vxb) {
+      A[cxb + ya] = vyx;
+      A[(size_t)ya * lda + xb] = vyx;
+    }
+    if (vya && vyb) {
+      A[cyb + ya] = vyy;
+      A[(size_t)ya * lda + yb] = vyy;
+    }
+  }
+  if (nx || ny) {
+    const double cma = rota ? frec_cm1(ra) : 0.0, cmb = rotb ? frec_cm1(rb) : 0.0;
+#pragma unroll
+    for (int side = 0; side < 2; ++side) {
+      if (side == 0 && !nx) continue;
+      if (side == 1 && !ny) continue;
+      int i = side ? ya : xa;
+      int j = side ? jy : jx;
+      double di = side ? ra.dy : ra.dx;
+      double dj = (j == xb) ? rb.dx : rb.dy;
+      double aij_s = side ? ((j == xb) ? vyx : vyy) : ((j == xb) ? vxx : vxy);
+      double si = dd_scale(dcur[i], cma).x;
+      double sj = dd_scale(dcur[j], cmb).x;
+      FRec nr;
+      int sl = rr_make_frec(m, n, rn, i, j, di, dj, aij_s * si * sj, si, sj, skip, nr);
+      rec_next[sl] = nr;
+    }
+  }
+}
+
+// Apply rounds r0 .. r0+nr-1 of the history to a chunk of ROWS consecutive
+// rows of Vt held in shared memory as S[row * n + col]; one thread per slot
+// and round, looping over the chunk's rows (2 FMA per row).
+template <int ROWS>
+__global__ void __launch_bounds__(512) v_apply_rounds(double* __restrict__ V, int ldv, int n, int m, int r0, int nr,
+                                                      const double2* __restrict__ hist) {
+  extern __shared__ double S[];
+  const int half = m / 2;
+  const int row0 = blockIdx.x * ROWS;
+  const int rc = min(ROWS, n - row0);
+  for (int e = threadIdx.x; e < n * ROWS; e += blockDim.x) {
+    int col = e / ROWS, row = e % ROWS;
+    S[row * n + col] = (row < rc) ? V[(size_t)col * ldv + row0 + row] : 0.0;
+  }
+  __syncthreads();
+  for (int k = 0; k < nr; ++k) {
+    const int r = r0 + k;
+    const double2* h = hist + (size_t)k * half;
+    for (int b = threadIdx.x; b < half; b += blockDim.x) {
+      double2 mm = h[b];
+      if ((__double_as_longlong(mm.x) | __double_as_longlong(mm.y)) == 0) continue;
+      int x, y;
+      rr_slot(m, r, b, x, y);
+#pragma unroll
+      for (int row = 0; row < ROWS; ++row) {
+        double vx = S[row * n + x], vy = S[row * n + y];
+        S[row * n + x] = fma(-mm.x, vy, vx);
+        S[row * n + y] = fma(mm.y, vx, vy);
+      }
+    }
+    __syncthreads();
+  }
+  for (int e = threadIdx.x; e < n * ROWS; e += blockDim.x) {
+    int col = e / ROWS, row = e % ROWS;
+    if (row < rc) V[(size_t)col * ldv + row0 + row] = S[row * n + col];
+  }
+}
+
+template <int ROWS>
+static cudaError_t launch_v_apply(double* V, int ldv, int n, int m, int r0, int nr, const double2* hist,
+                                  cudaStream_t s) {
+  size_t smem = (size_t)ROWS * n * sizeof(double);
+  cudaError_t e = cudaFuncSetAttribute(v_apply_rounds<ROWS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  v_apply_rounds<ROWS><<<(n + ROWS - 1) / ROWS, 512, smem, s>>>(V, ldv, n, m, r0, nr, hist);
+  mpj_count_launch();
+  return cudaGetLastError();
+}
+
+// rows of V per CTA: as many as fit in about 200 KB of shared memory (<= 8)
+static cudaError_t v_apply(double* V, int ldv, int n, int m, int r0, int nr, const double2* hist, cudaStream_t s) {
+  int rows = (200 * 1024) / (8 * (n > 0 ? n : 1));
+  if (rows >= 8) return launch_v_apply<8>(V, ldv, n, m, r0, nr, hist, s);
+  if (rows >= 6) return launch_v_apply<6>(V, ldv, n, m, r0, nr, hist, s);
+  if (rows >= 4) return launch_v_apply<4>(V, ldv, n, m, r0, nr, hist, s);
+  if (rows >= 2) return launch_v_apply<2>(V, ldv, n, m, r0, nr, hist, s);
+  return launch_v_apply<1>(V, ldv, n, m, r0, nr, hist, s);
+}
+
+// Fold the scales into A (off the diagonal) and V: A_ij *= d_i d_j, V_ij *= d_j.
+__global__ void fold_scales(double* __restrict__ A, int lda, double* __restrict__ V, int ldv, int n,
+                            const double2* __restrict__ d) {
+  size_t total = (size_t)n * n;
+  for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (size_t)gridDim.x * blockDim.x) {
+    int i = (int)(idx % n), j = (int)(idx / n);
+    double2 dj = d[j];
+    double sj = dj.x + dj.y;
+    if (i != j) {
+      double2 di = d[i];
+      double si = di.x + di.y;
+      A[(size_t)j * lda + i] = (A[(size_t)j * lda + i] * si) * sj;
+    }
+    V[(size_t)j * ldv + i] *= sj;
   }
 }
 
@@ -306,25 +447,49 @@ cudaError_t mpj_check_symmetric(const double* A, int lda, int n, unsigned* flags
   return cudaGetLastError();
 }
 
-size_t mpj_jacobi64_scratch_bytes(int n) {
-  int m = n + (n & 1);
-  size_t recs = 2 * (size_t)(m / 2 + 1) * sizeof(RotRec<double>);
-  // records, then (256-aligned) the reduction partials, two scalars and an int flag
-  return ((recs + 255) & ~(size_t)255) + RED_CTAS * sizeof(double) + 4 * sizeof(double) + 256;
-}
-
 static inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
-int mpj_jacobi64_run(int n, double* A, int lda, double* V, int ldv, double tol, int ordering, int max_sweeps,
-                     int* sweeps_out, double* off_out, double* off_initial, void* scratch, cudaStream_t s) {
-  const double skip = 0x1p-53;
+// Scratch layout: 2 record arrays, 2 scale arrays (double2), reduction
+// partials and scalars, then the V history (rv rounds of m/2 double2).
+static size_t scratch_fixed(int n) {
   int m = n + (n & 1);
+  return 2 * align256((size_t)(m / 2 + 1) * sizeof(FRec)) + 2 * align256((size_t)n * sizeof(double2)) +
+         align256(RED_CTAS * sizeof(double) + 4 * sizeof(double) + 64);
+}
+
+size_t mpj_jacobi64_scratch_bytes_rv(int n, int rv) {
+  int m = n + (n & 1);
+  return scratch_fixed(n) + (size_t)rv * (m / 2) * sizeof(double2);
+}
+
+size_t mpj_jacobi64_scratch_bytes(int n) { return mpj_jacobi64_scratch_bytes_rv(n, RV_MAX); }
+
+int mpj_jacobi64_run(int n, double* A, int lda, double* V, int ldv, double tol, int ordering, int max_sweeps,
+                     int* sweeps_out, double* off_out, double* off_initial, void* scratch, size_t scratch_bytes,
+                     cudaStream_t s) {
+  const double skip = 0x1p-53;
+  const int m = n + (n & 1);
+  const int half = m / 2;
   char* base = (char*)scratch;
-  RotRec<double>* rec0 = (RotRec<double>*)base;
-  RotRec<double>* rec1 = rec0 + (m / 2 + 1);
-  double* partial = (double*)(base + align256(2 * (size_t)(m / 2 + 1) * sizeof(RotRec<double>)));
+  FRec* rec[2];
+  double2* dsc[2];
+  size_t off_b = 0;
+  rec[0] = (FRec*)(base + off_b);
+  off_b += align256((size_t)(half + 1) * sizeof(FRec));
+  rec[1] = (FRec*)(base + off_b);
+  off_b += align256((size_t)(half + 1) * sizeof(FRec));
+  dsc[0] = (double2*)(base + off_b);
+  off_b += align256((size_t)n * sizeof(double2));
+  dsc[1] = (double2*)(base + off_b);
+  off_b += align256((size_t)n * sizeof(double2));
+  double* partial = (double*)(base + off_b);
   double* dscal = partial + RED_CTAS;
   int* iscal = (int*)(dscal + 2);
+  off_b += align256(RED_CTAS * sizeof(double) + 4 * sizeof(double) + 64);
+  double2* hist = (double2*)(base + off_b);
+  int rv = RV_MAX;
+  while (rv > 1 && mpj_jacobi64_scratch_bytes_rv(n, rv) > scratch_bytes) rv >>= 1;
+  if (mpj_jacobi64_scratch_bytes_rv(n, rv) > scratch_bytes) return MPJ_EWORKSPACE;
 
   double off2 = 0.0;
   MPJ_CUDA_TRY(mpj_sumsq(A, lda, n, true, partial, dscal, nullptr, s));
@@ -335,30 +500,50 @@ int mpj_jacobi64_run(int n, double* A, int lda, double* V, int ldv, double tol, 
   int sweeps = 0;
   int status = MPJ_OK;
   if (ordering == MPJ_ORDER_ROUND_ROBIN) {
-    const int half = m / 2;
     const int nt = (half + TS - 1) / TS;
-    const int n_atiles = nt * (nt + 1) / 2;
-    const int vrc = (n + VROWS - 1) / VROWS;
-    const int vsc = (half + VSLOTS - 1) / VSLOTS;
-    const int grid = n_atiles + vrc * vsc;
-    long long k = 0;  // global step counter (record buffer parity)
-    if (off > tol && n > 1) {
-      rr_init_params<<<(half + 127) / 128, 128, 0, s>>>(A, lda, n, m, 0, skip, rec0);
-      mpj_count_launch();
-      MPJ_CUDA_TRY(cudaGetLastError());
-    }
+    const int n_atiles = nt * (nt + 1) / 2;  // lower-triangular 16x16-slot tiles
+    const int fgrid = (int)(((size_t)n * n + 255) / 256 > 4096 ? 4096 : ((size_t)n * n + 255) / 256);
+    int k = 0;  // buffer parity of records and scales
+    bool need_init = true;
     while (off > tol && n > 1) {
       if (sweeps >= max_sweeps) {
         status = MPJ_NOT_CONVERGED;
         break;
       }
-      for (int r = 0; r < m - 1; ++r, ++k) {
-        RotRec<double>* cur = (k & 1) ? rec1 : rec0;
-        RotRec<double>* nxt = (k & 1) ? rec0 : rec1;
-        rr_step64<<<grid, 256, 0, s>>>(A, lda, V, ldv, n, m, r, skip, cur, nxt, nt, n_atiles, vrc);
+      if (need_init) {
+        d_reset<<<(n + 255) / 256, 256, 0, s>>>(dsc[k], n);
+        mpj_count_launch();
+        rr_init_frec<<<(half + 127) / 128, 128, 0, s>>>(A, lda, n, m, 0, skip, rec[k]);
         mpj_count_launch();
       }
+      int pending = 0, since_fold = 0;
+      for (int r = 0; r < m - 1; ++r) {
+        rr_step64<<<n_atiles, 256, 0, s>>>(A, lda, n, m, r, skip, rec[k], rec[k ^ 1], dsc[k], dsc[k ^ 1],
+                                           hist + (size_t)pending * half);
+        mpj_count_launch();
+        k ^= 1;
+        ++pending;
+        ++since_fold;
+        const bool last = (r == m - 2);
+        const bool fold = last || since_fold == RS;
+        if (pending == rv || fold) {
+          MPJ_CUDA_TRY(v_apply(V, ldv, n, m, r - pending + 1, pending, hist, s));
+          pending = 0;
+        }
+        if (fold) {
+          fold_scales<<<fgrid, 256, 0, s>>>(A, lda, V, ldv, n, dsc[k]);
+          mpj_count_launch();
+          since_fold = 0;
+          if (!last) {  // records of round r+1 were built for the old scales
+            d_reset<<<(n + 255) / 256, 256, 0, s>>>(dsc[k], n);
+            mpj_count_launch();
+            rr_init_frec<<<(half + 127) / 128, 128, 0, s>>>(A, lda, n, m, r + 1, skip, rec[k]);
+            mpj_count_launch();
+          }
+        }
+      }
       MPJ_CUDA_TRY(cudaGetLastError());
+      need_init = true;
       ++sweeps;
       MPJ_CUDA_TRY(mpj_sumsq(A, lda, n, true, partial, dscal, nullptr, s));
       MPJ_CUDA_TRY(cudaMemcpyAsync(&off2, dscal, sizeof(double), cudaMemcpyDeviceToHost, s));
@@ -432,7 +617,7 @@ extern "C" int mpj_jacobi64_noalloc(int n, double* A, int lda, double* V, int ld
   cudaStream_t s = (cudaStream_t)stream;
   if (n <= 0 || !A || !V || lda < n || ldv < n) return MPJ_EINVAL;
   if (ordering != MPJ_ORDER_CYCLIC && ordering != MPJ_ORDER_ROUND_ROBIN) return MPJ_EINVAL;
-  if (n > MPJ_NOALLOC_MAX_N || mpj_jacobi64_scratch_bytes(n) > (size_t)MPJ_NOALLOC_SCRATCH_BYTES)
+  if (n > MPJ_NOALLOC_MAX_N || mpj_jacobi64_scratch_bytes_rv(n, 1) > (size_t)MPJ_NOALLOC_SCRATCH_BYTES)
     return MPJ_ETOOLARGE;
   void* w = nullptr;
   int st = noalloc_scratch_for_current_device(&w);
@@ -452,7 +637,7 @@ extern "C" int mpj_jacobi64_noalloc(int n, double* A, int lda, double* V, int ld
     tol = (double)n * 0x1p-53 * sqrt(norm2);
   }
   st = mpj_jacobi64_run(n, A, lda, V, ldv, tol, ordering, max_sweeps > 0 ? max_sweeps : 30, sweeps, off_final, nullptr,
-                        w, s);
+                        w, (size_t)MPJ_NOALLOC_SCRATCH_BYTES, s);
   cudaError_t e = cudaStreamSynchronize(s);
   if (e != cudaSuccess && st >= 0) {
     mpj_set_cuda_error(e, "mpj_jacobi64_noalloc sync", __LINE__);

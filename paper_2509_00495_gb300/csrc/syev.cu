@@ -38,10 +38,11 @@ namespace {
 inline size_t al(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct Layout {
-  size_t X, M, Y, S1, scratch, small, total;
+  size_t X, M, Y, Z, S1, scratch, small, total;
 };
 
-Layout layout(int n) {
+// Z (a fourth n x n buffer) only exists when a second preconditioning pass is run.
+Layout layout(int n, int passes) {
   Layout L;
   size_t sq = al((size_t)n * n * sizeof(double));
   size_t off = 0;
@@ -51,6 +52,8 @@ Layout layout(int n) {
   off += sq;
   L.Y = off;
   off += sq;
+  L.Z = off;
+  if (passes >= 2) off += sq;
   L.S1 = off;
   size_t s1 = al(mpj_stage1_bytes(n));
   if (s1 < sq) s1 = sq;
@@ -245,7 +248,8 @@ long long mpj_kernel_launches(void) { return g_launches.load(std::memory_order_r
 size_t mpj_syev_workspace(int n, const mpj_opts* o) {
   (void)o;
   if (n <= 0) return 0;
-  return layout(n).total;
+  int passes = (o && o->precond_passes >= 2 && o->method == MPJ_METHOD_MIXED) ? 2 : 1;
+  return layout(n, passes).total;
 }
 
 int mpj_syev_ex(int n, const double* A, int lda, double* W, double* Q, int ldq, const mpj_opts* opts_in,
@@ -256,7 +260,8 @@ int mpj_syev_ex(int n, const double* A, int lda, double* W, double* Q, int ldq, 
   if (n < 0 || (n > 0 && (!A || !W || !Q)) || lda < (n > 1 ? n : 1) || ldq < (n > 1 ? n : 1)) return MPJ_EINVAL;
   if (fill_opts(n, opts_in, &o) != MPJ_OK) return MPJ_EINVAL;
   if (n == 0) return MPJ_OK;
-  Layout L = layout(n);
+  const int passes = (o.method == MPJ_METHOD_MIXED && o.precond_passes >= 2) ? 2 : 1;
+  Layout L = layout(n, passes);
   bool own = false;
   if (work) {
     if (work_bytes < L.total) return MPJ_EWORKSPACE;
@@ -273,6 +278,7 @@ int mpj_syev_ex(int n, const double* A, int lda, double* W, double* Q, int ldq, 
   double* X = (double*)(base + L.X);
   double* M = (double*)(base + L.M);
   double* Y = (double*)(base + L.Y);
+  double* Z = (double*)(base + L.Z);
   void* S1 = base + L.S1;
   void* scratch = base + L.scratch;
   Small sm = small_ptrs(base + L.small, n);
@@ -280,7 +286,7 @@ int mpj_syev_ex(int n, const double* A, int lda, double* W, double* Q, int ldq, 
   double norm2 = 0.0;
   unsigned flags = 0;
   double tol = 0.0;
-  int sweeps32 = 0, sweeps64 = 0;
+  int sweeps32 = 0, sweeps32b = 0, sweeps64 = 0;
   double off32 = 0.0, offc = 0.0, offf = 0.0;
   double* Ac = nullptr;
   double* V = nullptr;
@@ -341,10 +347,47 @@ int mpj_syev_ex(int n, const double* A, int lda, double* W, double* Q, int ldq, 
         st = MPJ_ECUDA;
         goto done;
       }
-      tm.mark(3);
       Qd = Xp;
       Ac = M;
       V = Yp;
+      if (passes >= 2) {
+        // second pass (not in the paper): stages 1-3 on A_cond.  Its FP32
+        // rounding is relative to each entry, so the FP32 Jacobi resolves the
+        // eigenvalues that stage 1 on A could not separate.
+        double offc2 = 0.0;
+        if (mpj_sumsq(M, n, n, true, sm.partial, sm.dscal, nullptr, s) != cudaSuccess ||
+            cudaMemcpyAsync(&offc2, sm.dscal, sizeof(double), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+            cudaStreamSynchronize(s) != cudaSuccess) {
+          mpj_set_cuda_error(cudaGetLastError(), "pass-2 off", __LINE__);
+          st = MPJ_ECUDA;
+          goto done;
+        }
+        double tol32b = (double)n * 0x1p-24 * std::sqrt(offc2);
+        double* Ql2 = Yp;  // A Q_d (pass 1) is no longer needed
+        int r1b = mpj_stage1_run(n, M, n, Ql2, n, tol32b, o.max_sweeps32, &sweeps32b, nullptr, S1, sm.partial, sm.dscal,
+                                 s);
+        if (r1b < 0) {
+          st = r1b;
+          goto done;
+        }
+        double* X2 = Ql2;
+        double* Y2 = (double*)S1;  // the stage-1 area is free again
+        if ((st = ns_steps_run(n, &X2, Z, &Y2, o.ns_steps, s)) != MPJ_OK) goto done;
+        // A_cond2 = Q_d2^T (A_cond Q_d2): T = A_cond Q_d2 into Z, then into M (A_cond is consumed)
+        double* T = (X2 == Ql2) ? (double*)S1 : Ql2;
+        if (mpj_gemm64(false, false, n, n, n, 1.0, M, n, X2, n, 0.0, nullptr, n, Z, n, 0, s) != cudaSuccess ||
+            mpj_gemm64(true, false, n, n, n, 1.0, X2, n, Z, n, 0.0, nullptr, n, M, n, 1, s) != cudaSuccess ||
+            mpj_gemm64(false, false, n, n, n, 1.0, Xp, n, X2, n, 0.0, nullptr, n, Z, n, 0, s) != cudaSuccess) {
+          mpj_set_cuda_error(cudaGetLastError(), "pass-2 transform", __LINE__);
+          st = MPJ_ECUDA;
+          goto done;
+        }
+        (void)T;
+        Qd = Z;   // Q_d = Q_d1 Q_d2
+        Ac = M;
+        V = Xp;   // Q_d1 is folded into Z
+      }
+      tm.mark(3);
     } else {
       tm.mark(1);
       tm.mark(2);
@@ -358,7 +401,8 @@ int mpj_syev_ex(int n, const double* A, int lda, double* W, double* Q, int ldq, 
     set_identity<<<blocks_for((size_t)n * n), 256, 0, s>>>(V, n, n);
     mpj_count_launch();
     {
-      int r4 = mpj_jacobi64_run(n, Ac, n, V, n, tol, o.ordering, o.max_sweeps64, &sweeps64, &offf, &offc, scratch, s);
+      int r4 = mpj_jacobi64_run(n, Ac, n, V, n, tol, o.ordering, o.max_sweeps64, &sweeps64, &offf, &offc, scratch,
+                                mpj_jacobi64_scratch_bytes(n), s);
       if (r4 < 0) {
         st = r4;
         goto done;
@@ -420,6 +464,7 @@ done:
   if (info) {
     info->status = st;
     info->sweeps32 = sweeps32;
+    info->sweeps32_pass2 = sweeps32b;
     info->sweeps64 = sweeps64;
     info->ns_steps = (o.method == MPJ_METHOD_MIXED) ? o.ns_steps : 0;
     info->off32 = off32;
@@ -507,7 +552,8 @@ int mpj_jacobi64(int n, double* A, int lda, double* V, int ldv, double tol, int 
   if (n <= 0 || !A || !V || lda < n || ldv < n) return MPJ_EINVAL;
   if (ordering != MPJ_ORDER_CYCLIC && ordering != MPJ_ORDER_ROUND_ROBIN) return MPJ_EINVAL;
   void* w = nullptr;
-  if (cudaMallocAsync(&w, mpj_jacobi64_scratch_bytes(n) + 4096, s) != cudaSuccess) return MPJ_ENOMEM;
+  size_t wbytes = mpj_jacobi64_scratch_bytes(n) + 4096;
+  if (cudaMallocAsync(&w, wbytes, s) != cudaSuccess) return MPJ_ENOMEM;
   int st = MPJ_OK;
   if (tol <= 0) {
     double* partial = (double*)w;
@@ -521,7 +567,7 @@ int mpj_jacobi64(int n, double* A, int lda, double* V, int ldv, double tol, int 
   }
   if (st == MPJ_OK)
     st = mpj_jacobi64_run(n, A, lda, V, ldv, tol, ordering, max_sweeps > 0 ? max_sweeps : 30, sweeps, off_final, nullptr,
-                          w, s);
+                          w, wbytes, s);
   cudaFreeAsync(w, s);
   if (cudaStreamSynchronize(s) != cudaSuccess && st >= 0) st = MPJ_ECUDA;
   return st;

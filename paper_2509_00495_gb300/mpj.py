@@ -46,11 +46,13 @@ _dp = ctypes.POINTER(ctypes.c_double)
 
 class Opts(ctypes.Structure):
     _fields_ = [("tol", _d), ("tol32", _d), ("max_sweeps64", _i), ("max_sweeps32", _i), ("ns_steps", _i),
-                ("ordering", _i), ("method", _i), ("polish", _i), ("sort", _i), ("check_symmetry", _i)]
+                ("ordering", _i), ("method", _i), ("polish", _i), ("sort", _i), ("check_symmetry", _i),
+                ("precond_passes", _i)]
 
 
 class Info(ctypes.Structure):
-    _fields_ = [("status", _i), ("sweeps32", _i), ("sweeps64", _i), ("ns_steps", _i), ("norm_fro", _d),
+    _fields_ = [("status", _i), ("sweeps32", _i), ("sweeps32_pass2", _i), ("sweeps64", _i), ("ns_steps", _i),
+                ("norm_fro", _d),
                 ("tol", _d), ("off32", _d), ("off_cond", _d), ("off_final", _d), ("ms_stage", ctypes.c_float * 6)]
 
     def as_dict(self) -> dict:

@@ -377,3 +377,30 @@ def test_autograd_matches_central_differences():
         fd = (loss(A.detach() + h * E) - loss(A.detach() - h * E)) / (2 * h)
         an = (g * E).sum().item()
         assert fd == pytest.approx(an, rel=1e-6, abs=1e-7)
+
+
+# ---------------------------------------------------------------- second preconditioning pass (option)
+@pytest.mark.parametrize("n", [96, 257])
+def test_two_pass_preconditioning_vs_oracle(n):
+    A, lam = inputs.geo_matrix(n, 1e6, seed=17 * n)
+    r1 = mpj().syev_ex(dev(A))
+    r2 = mpj().syev_ex(dev(A), precond_passes=2)
+    W, Q = host(r2.W), host(r2.Q)
+    Wr, _, _ = oracle.syev_mixed(A, ordering32=oracle.BLOCK_ROUND_ROBIN, ordering64=oracle.ROUND_ROBIN)
+    nA = np.linalg.norm(A, 2)
+    assert r2.status == 0 and r2.info["sweeps32_pass2"] >= 1
+    assert np.abs(W - Wr).max() <= 1e-12 * nA
+    assert np.abs(W - np.sort(lam)).max() <= 1e-12 * nA
+    be, orF = triple(A, W, Q)
+    assert be <= 4 and orF <= 4, (be, orF)
+    assert r2.info["sweeps64"] <= r1.info["sweeps64"]
+
+
+def test_two_pass_geo_4096_properties():
+    A, lam = inputs.geo_4096(seed=0)
+    A_t = dev(A)
+    r = mpj().syev_ex(A_t, precond_passes=2)
+    assert r.status == 0
+    assert np.abs(host(r.W) - np.sort(lam)).max() <= 1e-12
+    be, orF = _gpu_triple(A_t, r.W, r.Q)
+    assert be <= 4 and orF <= 4, (be, orF)
