@@ -297,10 +297,14 @@ def main():
     st = info["ms_stage"]
     dominant = "rr_step64" if st[3] >= max(st[1], st[2]) else "dgemm_kernel"
     if rounds > 0:
+        # one round = rr_step64 (A) + its share of v_apply_rounds (V); per round the
+        # scaled rotations need one FMA (2 flops) per entry and side: the lower half
+        # of A twice (rows, columns) and all of V once -> 4 n^2 flops
         avg_launch_s = st[3] / 1000.0 / rounds
-        flops = 6.0 * n * n  # per round: A (lower half) 2 sides x 3 flops + V 3 flops per entry
+        flops = 4.0 * n * n
         achieved = flops / avg_launch_s / 1e12
-        out["roofline"] = {"kernel": "rr_step64", "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
+        out["roofline"] = {"kernel": "rr_step64+v_apply_rounds (one round)", "bound": "alu", "achieved": achieved,
+                           "peak": FP64_PEAK_TFLOPS,
                            "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
                            "peak_source": "nominal FP64 of the recipe table (not in MEASURED_PEAKS.json)",
                            "algorithmic_flops_per_launch": flops, "avg_launch_ms": avg_launch_s * 1e3,

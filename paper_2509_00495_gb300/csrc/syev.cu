@@ -364,8 +364,10 @@ int mpj_syev_ex(int n, const double* A, int lda, double* W, double* Q, int ldq, 
         }
         double tol32b = (double)n * 0x1p-24 * std::sqrt(offc2);
         double* Ql2 = Yp;  // A Q_d (pass 1) is no longer needed
-        int r1b = mpj_stage1_run(n, M, n, Ql2, n, tol32b, o.max_sweeps32, &sweeps32b, nullptr, S1, sm.partial, sm.dscal,
-                                 s);
+        // the second FP32 pass mostly resolves near-degenerate groups; its gains
+        // level off after a few sweeps, so it gets a smaller cap
+        int cap2 = o.max_sweeps32 < 8 ? o.max_sweeps32 : 8;
+        int r1b = mpj_stage1_run(n, M, n, Ql2, n, tol32b, cap2, &sweeps32b, nullptr, S1, sm.partial, sm.dscal, s);
         if (r1b < 0) {
           st = r1b;
           goto done;
