@@ -34,15 +34,16 @@
 
 namespace {
 
-constexpr int TS = 32;        // slots per tile side (a 64 x 64 entry region)
+constexpr int TS = 16;        // slots per tile side (a 32 x 32 entry region)
 constexpr int RED_CTAS = 256;
 constexpr int RV_MAX = 64;    // rounds per batched V update
 constexpr int RS = 512;       // rounds between scale folds
 
 // Scaled-rotation record of one slot (see the file comment); mx == my == 0
-// means "not rotated".  dx, dy: true diagonal entries after the rotation.
+// means "not rotated".  cm1 = c - 1 of the rotation (for the scale update),
+// dx, dy: true diagonal entries after the rotation.
 struct FRec {
-  double mx, my, dx, dy;
+  double mx, my, cm1, dx, dy;
 };
 
 // Bit test instead of an FP64 compare: on this GPU FP64 compares issue on the
@@ -51,12 +52,9 @@ MPJ_DEV bool frec_rotated(const FRec& r) {
   return (__double_as_longlong(r.mx) | __double_as_longlong(r.my)) != 0;
 }
 
-// c - 1 of a record: t^2 = mx my.
-MPJ_DEV double frec_cm1(const FRec& r) {
-  double t2 = r.mx * r.my;
-  double h = sqrt(1.0 + t2);
-  return -t2 / (h * (1.0 + h));
-}
+// c - 1 of a record, computed once per slot when the record is built (kept in
+// the record so the per-entry path never evaluates sqrt or a division).
+MPJ_DEV double frec_cm1(const FRec& r) { return r.cm1; }
 
 // d' = d (1 + cm1) in double-double (Fast2Sum renormalization, |cm1| < 0.3).
 MPJ_DEV double2 dd_scale(double2 d, double cm1) {
@@ -86,6 +84,7 @@ MPJ_DEV int rr_make_frec(int m, int n, int r, int i, int j, double di, double dj
   double sx = (x == i) ? si : sj, sy = (x == i) ? sj : si;
   rec.mx = rot ? tau * (sy / sx) : 0.0;
   rec.my = rot ? tau * (sx / sy) : 0.0;
+  rec.cm1 = rot ? cm1 : 0.0;
   rec.dx = (x == p) ? np : nq;
   rec.dy = (x == p) ? nq : np;
   return slot;
@@ -120,36 +119,8 @@ __device__ __forceinline__ void tri_tile(int t, int& ti, int& tj) {
   tj = t - r * (r + 1) / 2;
 }
 
-// Next-round records hosted by block (a, b): the coupling of a next-round
-// pair (i in slot a, j in slot b) is one of the block's four new entries.
-MPJ_DEV void next_records(int m, int n, int rn, double skip, int xa, int ya, int xb, int yb, int jx, int jy, bool nx,
-                          bool ny, const FRec& ra, const FRec& rb, bool rota, bool rotb, double vxx, double vxy,
-                          double vyx, double vyy, const double2* __restrict__ dcur, FRec* __restrict__ rec_next) {
-  const double cma = rota ? frec_cm1(ra) : 0.0, cmb = rotb ? frec_cm1(rb) : 0.0;
-#pragma unroll
-  for (int side = 0; side < 2; ++side) {
-    if (side == 0 && !nx) continue;
-    if (side == 1 && !ny) continue;
-    int i = side ? ya : xa;
-    int j = side ? jy : jx;
-    double di = side ? ra.dy : ra.dx;
-    double dj = (j == xb) ? rb.dx : rb.dy;
-    double aij_s = side ? ((j == xb) ? vyx : vyy) : ((j == xb) ? vxx : vxy);
-    double si = dd_scale(dcur[i], cma).x;
-    double sj = dd_scale(dcur[j], cmb).x;
-    FRec nr;
-    int sl = rr_make_frec(m, n, rn, i, j, di, dj, aij_s * si * sj, si, sj, skip, nr);
-    rec_next[sl] = nr;
-  }
-}
-
-// One round on A (scaled form) + next round's records + this round's V
-// multipliers.  A CTA owns a lower-triangular tile of TS x TS slot blocks
-// (a 2TS x 2TS entry region and its mirror); thread (la, w) handles the
-// blocks (a, b) with a = ti*TS + la and b = tj*TS + w + 8k, k = 0..KB-1,
-// issuing all their loads before any arithmetic.
-constexpr int KB = TS / 8;
-__global__ void __launch_bounds__(256, 2) rr_step64(double* __restrict__ A, int lda, int n, int m, int r, double skip,
+// One round on A (scaled form) + next round's records + this round's V multipliers.
+__global__ void __launch_bounds__(256) rr_step64(double* __restrict__ A, int lda, int n, int m, int r, double skip,
                                                  const FRec* __restrict__ rec, FRec* __restrict__ rec_next,
                                                  const double2* __restrict__ dcur, double2* __restrict__ dnext,
                                                  double2* __restrict__ hist_row) {
@@ -158,87 +129,14 @@ __global__ void __launch_bounds__(256, 2) rr_step64(double* __restrict__ A, int 
   int ti, tj;
   tri_tile(blockIdx.x, ti, tj);
   const int a = ti * TS + (threadIdx.x % TS);
-  if (a >= half) return;
+  const int b = tj * TS + (threadIdx.x / TS);
+  if (a >= half || b >= half || a < b) return;
   int xa, ya;
   rr_slot(m, r, a, xa, ya);
   const FRec ra = rec[a];
   const bool rota = frec_rotated(ra);
   const bool vxa = xa < n, vya = ya < n;
-  const int jx = vxa ? rr_partner(m, rn, xa) : -1;
-  const int jy = vya ? rr_partner(m, rn, ya) : -1;
-  const int w = threadIdx.x / TS;
-
-  double v[KB][4];
-  int xb[KB], yb[KB];
-  bool act[KB];
-#pragma unroll
-  for (int k = 0; k < KB; ++k) {
-    const int b = tj * TS + w + 8 * k;
-    act[k] = b < half && b < a;
-    xb[k] = yb[k] = 0;
-    v[k][0] = v[k][1] = v[k][2] = v[k][3] = 0.0;
-    if (!act[k]) continue;
-    rr_slot(m, r, b, xb[k], yb[k]);
-    const bool vxb = xb[k] < n, vyb = yb[k] < n;
-    const size_t cx = (size_t)xb[k] * lda, cy = (size_t)yb[k] * lda;
-    if (vxa && vxb) v[k][0] = A[cx + xa];
-    if (vxa && vyb) v[k][1] = A[cy + xa];
-    if (vya && vxb) v[k][2] = A[cx + ya];
-    if (vya && vyb) v[k][3] = A[cy + ya];
-  }
-#pragma unroll
-  for (int k = 0; k < KB; ++k) {
-    if (!act[k]) continue;
-    const int b = tj * TS + w + 8 * k;
-    const double2 mb = *reinterpret_cast<const double2*>(&rec[b]);  // (mx, my) of slot b
-    const bool rotb = (__double_as_longlong(mb.x) | __double_as_longlong(mb.y)) != 0;
-    double vxx = v[k][0], vxy = v[k][1], vyx = v[k][2], vyy = v[k][3];
-    if (rota) {  // rows x_a, y_a
-      double t0 = fma(-ra.mx, vyx, vxx), t1 = fma(ra.my, vxx, vyx);
-      double t2 = fma(-ra.mx, vyy, vxy), t3 = fma(ra.my, vxy, vyy);
-      vxx = t0;
-      vyx = t1;
-      vxy = t2;
-      vyy = t3;
-    }
-    if (rotb) {  // columns x_b, y_b
-      double t0 = fma(-mb.x, vxy, vxx), t1 = fma(mb.y, vxx, vxy);
-      double t2 = fma(-mb.x, vyy, vyx), t3 = fma(mb.y, vyx, vyy);
-      vxx = t0;
-      vxy = t1;
-      vyx = t2;
-      vyy = t3;
-    }
-    const bool vxb = xb[k] < n, vyb = yb[k] < n;
-    if (rota || rotb) {
-      const size_t cx = (size_t)xb[k] * lda, cy = (size_t)yb[k] * lda;
-      if (vxa && vxb) {
-        A[cx + xa] = vxx;
-        A[(size_t)xa * lda + xb[k]] = vxx;
-      }
-      if (vxa && vyb) {
-        A[cy + xa] = vxy;
-        A[(size_t)xa * lda + yb[k]] = vxy;
-      }
-      if (vya && vxb) {
-        A[cx + ya] = vyx;
-        A[(size_t)ya * lda + xb[k]] = vyx;
-      }
-      if (vya && vyb) {
-        A[cy + ya] = vyy;
-        A[(size_t)ya * lda + yb[k]] = vyy;
-      }
-    }
-    const bool nx = jx >= 0 && jx < n && (jx == xb[k] || jx == yb[k]);
-    const bool ny = jy >= 0 && jy < n && (jy == xb[k] || jy == yb[k]);
-    if (nx || ny) {
-      const FRec rb = rec[b];
-      next_records(m, n, rn, skip, xa, ya, xb[k], yb[k], jx, jy, nx, ny, ra, rb, rota, rotb, vxx, vxy, vyx, vyy,
-                   dcur, rec_next);
-    }
-  }
-  // the pair's own 2x2 block, in diagonal tiles (b == a)
-  if (ti == tj && (a - tj * TS) % 8 == w) {
+  if (a == b) {
     const double cm1 = rota ? frec_cm1(ra) : 0.0;
     double2 sx = vxa ? dd_scale(dcur[xa], cm1) : make_double2(1.0, 0.0);
     double2 sy = vya ? dd_scale(dcur[ya], cm1) : make_double2(1.0, 0.0);
@@ -260,6 +158,7 @@ __global__ void __launch_bounds__(256, 2) rr_step64(double* __restrict__ A, int 
       FRec z;
       z.mx = 0.0;
       z.my = 0.0;
+      z.cm1 = 0.0;
       z.dx = (xa == rn) ? ra.dx : ra.dy;
       z.dy = 0.0;
       rec_next[0] = z;
@@ -268,6 +167,75 @@ __global__ void __launch_bounds__(256, 2) rr_step64(double* __restrict__ A, int 
     if (vxa && vya && rr_partner(m, rn, xa) == ya) {
       FRec nr;
       int sl = rr_make_frec(m, n, rn, xa, ya, ra.dx, ra.dy, axy_s * sx.x * sy.x, sx.x, sy.x, skip, nr);
+      rec_next[sl] = nr;
+    }
+    return;
+  }
+  int xb, yb;
+  rr_slot(m, r, b, xb, yb);
+  const FRec rb = rec[b];
+  const bool rotb = frec_rotated(rb);
+  const bool vxb = xb < n, vyb = yb < n;
+  // next-round pairs hosted by this block: (x_a or y_a) with (x_b or y_b)
+  int jx = vxa ? rr_partner(m, rn, xa) : -1;
+  int jy = vya ? rr_partner(m, rn, ya) : -1;
+  bool nx = jx >= 0 && jx < n && (jx == xb || jx == yb);
+  bool ny = jy >= 0 && jy < n && (jy == xb || jy == yb);
+  if (!rota && !rotb && !nx && !ny) return;
+  size_t cxb = (size_t)xb * lda, cyb = (size_t)yb * lda;
+  double vxx = (vxa && vxb) ? A[cxb + xa] : 0.0;
+  double vxy = (vxa && vyb) ? A[cyb + xa] : 0.0;
+  double vyx = (vya && vxb) ? A[cxb + ya] : 0.0;
+  double vyy = (vya && vyb) ? A[cyb + ya] : 0.0;
+  if (rota) {  // rows x_a, y_a
+    double t0 = fma(-ra.mx, vyx, vxx), t1 = fma(ra.my, vxx, vyx);
+    double t2 = fma(-ra.mx, vyy, vxy), t3 = fma(ra.my, vxy, vyy);
+    vxx = t0;
+    vyx = t1;
+    vxy = t2;
+    vyy = t3;
+  }
+  if (rotb) {  // columns x_b, y_b
+    double t0 = fma(-rb.mx, vxy, vxx), t1 = fma(rb.my, vxx, vxy);
+    double t2 = fma(-rb.mx, vyy, vyx), t3 = fma(rb.my, vyx, vyy);
+    vxx = t0;
+    vxy = t1;
+    vyx = t2;
+    vyy = t3;
+  }
+  if (rota || rotb) {
+    if (vxa && vxb) {
+      A[cxb + xa] = vxx;
+      A[(size_t)xa * lda + xb] = vxx;
+    }
+    if (vxa && vyb) {
+      A[cyb + xa] = vxy;
+      A[(size_t)xa * lda + yb] = vxy;
+    }
+    if (vya && vxb) {
+      A[cxb + ya] = vyx;
+      A[(size_t)ya * lda + xb] = vyx;
+    }
+    if (vya && vyb) {
+      A[cyb + ya] = vyy;
+      A[(size_t)ya * lda + yb] = vyy;
+    }
+  }
+  if (nx || ny) {
+    const double cma = rota ? frec_cm1(ra) : 0.0, cmb = rotb ? frec_cm1(rb) : 0.0;
+#pragma unroll
+    for (int side = 0; side < 2; ++side) {
+      if (side == 0 && !nx) continue;
+      if (side == 1 && !ny) continue;
+      int i = side ? ya : xa;
+      int j = side ? jy : jx;
+      double di = side ? ra.dy : ra.dx;
+      double dj = (j == xb) ? rb.dx : rb.dy;
+      double aij_s = side ? ((j == xb) ? vyx : vyy) : ((j == xb) ? vxx : vxy);
+      double si = dd_scale(dcur[i], cma).x;
+      double sj = dd_scale(dcur[j], cmb).x;
+      FRec nr;
+      int sl = rr_make_frec(m, n, rn, i, j, di, dj, aij_s * si * sj, si, sj, skip, nr);
       rec_next[sl] = nr;
     }
   }
