@@ -153,17 +153,43 @@ __device__ __forceinline__ void tri_tile(int t, int nt, int& ti, int& tj) {
 }
 
 // Blocked application of the round's U's: lower tiles of A32 (with mirror)
-// and 32-row tiles of V32.
-__global__ void __launch_bounds__(256) update32(float* __restrict__ A32, float* __restrict__ V32, int N, int nb,
-                                                int R, const float* __restrict__ Sbuf,
-                                                const float* __restrict__ Ubuf, int n_atiles) {
-  __shared__ float T[W2][LD];
-  __shared__ float X[W2][LD];
-  __shared__ float UP[W2][LD];
-  __shared__ float UQ[W2][LD];
+// and 32-row tiles of V32.  One 64-thread CTA per 32 x 32 tile; each thread
+// owns a 4 x 4 block of the result, so every pair of float4 shared-memory
+// loads feeds 16 FMAs.
+constexpr int UT = 64;  // threads per update tile
+constexpr int LD4 = 36; // padded row length (keeps rows 16-byte aligned)
+
+// acc[a][b] = sum_l Lt[l][i4 + a] * R[l][j4 + b]  (a 4 x 4 block of Lt^T R, both
+// operands 32 x 32 row-major in shared memory).
+MPJ_DEV void tile_mm(const float (*Lt)[LD4], const float (*R)[LD4], float acc[4][4], int i4, int j4) {
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) acc[a][b] = 0.0f;
+#pragma unroll 8
+  for (int l = 0; l < W2; ++l) {
+    float4 x = *reinterpret_cast<const float4*>(&Lt[l][i4]);  // op(L)[i4..i4+3][l]
+    float4 y = *reinterpret_cast<const float4*>(&R[l][j4]);   // R[l][j4..j4+3]
+    float xa[4] = {x.x, x.y, x.z, x.w}, yb[4] = {y.x, y.y, y.z, y.w};
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) acc[a][b] = fmaf(xa[a], yb[b], acc[a][b]);
+  }
+}
+
+__global__ void __launch_bounds__(UT) update32(float* __restrict__ A32, float* __restrict__ V32, int N, int nb, int R,
+                                               const float* __restrict__ Sbuf, const float* __restrict__ Ubuf,
+                                               int n_atiles) {
+  __shared__ __align__(16) float T[W2][LD4];   // the tile, row-major T[i][j]
+  __shared__ __align__(16) float XT[W2][LD4];  // (U_P^T T)^T, i.e. XT[l][i] = X[i][l]
+  __shared__ __align__(16) float UP[W2][LD4];  // U_P[l][i]
+  __shared__ __align__(16) float UQ[W2][LD4];  // U_Q[l][j]
   const int tid = threadIdx.x;
+  const int i4 = (tid % 8) * 4, j4 = (tid / 8) * 4;
   const int npairs = nb / 2;
   int item = blockIdx.x;
+  float acc[4][4];
   if (item < n_atiles) {
     int P, Q;
     tri_tile(item, npairs, P, Q);
@@ -172,49 +198,36 @@ __global__ void __launch_bounds__(256) update32(float* __restrict__ A32, float* 
     block_pair(nb, R, Q, IQ, JQ);
     if (P == Q) {
       const float* Sp = Sbuf + (size_t)P * W2 * W2;
-      for (int e = tid; e < W2 * W2; e += 256) {
+      for (int e = tid; e < W2 * W2; e += UT) {
         int li = e % W2, lj = e / W2;
         A32[(size_t)gidx(IP, JP, lj) * N + gidx(IP, JP, li)] = Sp[e];
       }
       return;
     }
-    const float* Up = Ubuf + (size_t)P * W2 * W2;
+    const float* Up = Ubuf + (size_t)P * W2 * W2;  // column-major 32 x 32: Up[li + 32 lj] = U_P(li, lj)
     const float* Uq = Ubuf + (size_t)Q * W2 * W2;
-    for (int e = tid; e < W2 * W2; e += 256) {
+    for (int e = tid; e < W2 * W2; e += UT) {
       int li = e % W2, lj = e / W2;
       T[li][lj] = A32[(size_t)gidx(IQ, JQ, lj) * N + gidx(IP, JP, li)];
       UP[li][lj] = Up[e];
       UQ[li][lj] = Uq[e];
     }
     __syncthreads();
-    const int j = tid % W2, i0 = tid / W2;  // 4 rows i0 + 8k per thread, column j
-    float acc[4];
+    // X = U_P^T T: X[i][j] = sum_l U_P[l][i] T[l][j]; store XT[j][i]
+    tile_mm(UP, T, acc, i4, j4);
 #pragma unroll
-    for (int k = 0; k < 4; ++k) acc[k] = 0.0f;
-    // X = U_P^T T
-#pragma unroll 8
-    for (int l = 0; l < W2; ++l) {
-      float t = T[l][j];
+    for (int a = 0; a < 4; ++a)
 #pragma unroll
-      for (int k = 0; k < 4; ++k) acc[k] = fmaf(UP[l][i0 + 8 * k], t, acc[k]);
-    }
-#pragma unroll
-    for (int k = 0; k < 4; ++k) X[i0 + 8 * k][j] = acc[k];
+      for (int b = 0; b < 4; ++b) XT[j4 + b][i4 + a] = acc[a][b];
     __syncthreads();
-    // Y = X U_Q
+    // Y = X U_Q: Y[i][j] = sum_l X[i][l] U_Q[l][j] = sum_l XT[l][i] U_Q[l][j]
+    tile_mm(XT, UQ, acc, i4, j4);
 #pragma unroll
-    for (int k = 0; k < 4; ++k) acc[k] = 0.0f;
-#pragma unroll 8
-    for (int l = 0; l < W2; ++l) {
-      float u = UQ[l][j];
+    for (int a = 0; a < 4; ++a)
 #pragma unroll
-      for (int k = 0; k < 4; ++k) acc[k] = fmaf(X[i0 + 8 * k][l], u, acc[k]);
-    }
+      for (int b = 0; b < 4; ++b) T[i4 + a][j4 + b] = acc[a][b];
     __syncthreads();
-#pragma unroll
-    for (int k = 0; k < 4; ++k) T[i0 + 8 * k][j] = acc[k];
-    __syncthreads();
-    for (int e = tid; e < W2 * W2; e += 256) {
+    for (int e = tid; e < W2 * W2; e += UT) {
       int li = e % W2, lj = e / W2;
       A32[(size_t)gidx(IQ, JQ, lj) * N + gidx(IP, JP, li)] = T[li][lj];
       // mirror: entry (cols(Q)[li], rows(P)[lj]) = T[lj][li]
@@ -222,32 +235,26 @@ __global__ void __launch_bounds__(256) update32(float* __restrict__ A32, float* 
     }
     return;
   }
-  // V tile: rows [rc*32, rc*32+32), column set of pair Q
+  // V tile: rows [rc*32, rc*32+32), column set of pair Q:  Y = T U_Q
   int v = item - n_atiles;
   int nrc = N / W2;
   int rc = v % nrc, Q = v / nrc;
   int IQ, JQ;
   block_pair(nb, R, Q, IQ, JQ);
   const float* Uq = Ubuf + (size_t)Q * W2 * W2;
-  for (int e = tid; e < W2 * W2; e += 256) {
+  for (int e = tid; e < W2 * W2; e += UT) {
     int li = e % W2, lj = e / W2;
-    T[li][lj] = V32[(size_t)gidx(IQ, JQ, lj) * N + rc * W2 + li];
+    XT[lj][li] = V32[(size_t)gidx(IQ, JQ, lj) * N + rc * W2 + li];  // XT[l][i] = T[i][l]
     UQ[li][lj] = Uq[e];
   }
   __syncthreads();
-  const int j = tid % W2, i0 = tid / W2;
-  float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-#pragma unroll 8
-  for (int l = 0; l < W2; ++l) {
-    float u = UQ[l][j];
+  tile_mm(XT, UQ, acc, i4, j4);
 #pragma unroll
-    for (int k = 0; k < 4; ++k) acc[k] = fmaf(T[i0 + 8 * k][l], u, acc[k]);
-  }
-  __syncthreads();
+  for (int a = 0; a < 4; ++a)
 #pragma unroll
-  for (int k = 0; k < 4; ++k) T[i0 + 8 * k][j] = acc[k];
+    for (int b = 0; b < 4; ++b) T[i4 + a][j4 + b] = acc[a][b];
   __syncthreads();
-  for (int e = tid; e < W2 * W2; e += 256) {
+  for (int e = tid; e < W2 * W2; e += UT) {
     int li = e % W2, lj = e / W2;
     V32[(size_t)gidx(IQ, JQ, lj) * N + rc * W2 + li] = T[li][lj];
   }
@@ -293,7 +300,7 @@ int mpj_stage1_run(int n, const double* A, int lda, double* Ql, int ldq, double 
     for (int R = 0; R < nb - 1; ++R) {
       solve32<<<npairs, 256, 0, s>>>(A32, N, nb, R, Sbuf, Ubuf);
       mpj_count_launch();
-      update32<<<grid_u, 256, 0, s>>>(A32, V32, N, nb, R, Sbuf, Ubuf, n_atiles);
+      update32<<<grid_u, UT, 0, s>>>(A32, V32, N, nb, R, Sbuf, Ubuf, n_atiles);
       mpj_count_launch();
     }
     MPJ_CUDA_TRY(cudaGetLastError());
