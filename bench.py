@@ -89,6 +89,19 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(self.rows)}
 
 
+# ---------------------------------------------------------------- multi-rank aggregation
+def aggregate(value_ms: float, world: int, steps: int, dist=None, device=None) -> tuple[float, float]:
+    """Replicas-only scaling: every rank solves its own matrices; the job's time
+    is the slowest rank's.  Returns (max_ms over ranks, whole-job solves/s =
+    world * steps / max_seconds).  With world == 1 no collective is used."""
+    if world > 1 and dist is not None:
+        import torch
+        t = torch.tensor([value_ms], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        value_ms = float(t.item())
+    return value_ms, world * steps / (value_ms / 1000.0)
+
+
 # ---------------------------------------------------------------- CPU oracle baseline
 def cpu_baseline_estimate(A: np.ndarray, sweeps32: int, sweeps64: int, budget_s: float = 15.0) -> dict:
     """Time the oracle (as it stands, one core) on a bounded sample of the n=4096
@@ -239,11 +252,7 @@ def main():
     total_ms = ev0.elapsed_time(ev1)
     launches = mpj.lib().mpj_kernel_launches() - launches0
     clocks = sampler.stop()
-    if world > 1:
-        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = t.item()
-    value = world * args.steps / (total_ms / 1000.0)
+    total_ms, value = aggregate(total_ms, world, args.steps, dist if world > 1 else None, dev)
     W_last, Q_last = r.W, r.Q
 
     # accuracy of the timed result (outside the timed region)
@@ -270,11 +279,11 @@ def main():
         Q_host.copy_(re.Q, non_blocking=True)
         torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
-    if world > 1:
-        t = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = t.item()
-    e2e = {"value": world * e2e_steps / e2e_s if e2e_steps else None, "unit": UNIT,
+    if e2e_steps:
+        e2e_ms, e2e_value = aggregate(e2e_s * 1000.0, world, e2e_steps, dist if world > 1 else None, dev)
+    else:
+        e2e_value = None
+    e2e = {"value": e2e_value, "unit": UNIT,
            "h2d_bytes_per_step": n * n * 8, "d2h_bytes_per_step": n * 8 + n * n * 8}
 
     info = step_info[-1]

@@ -88,9 +88,9 @@ MPJ_DEV void rr_slot(int m, int r, int i, int& x, int& y) {
 MPJ_DEV int rr_partner(int m, int r, int idx) {
   if (idx == m - 1) return r;
   if (idx == r) return m - 1;
-  int v = 2 * r - idx;
-  v %= (m - 1);
+  int v = 2 * r - idx;  // in (-(m-1), 2(m-1)): one correction at most
   if (v < 0) v += m - 1;
+  if (v >= m - 1) v -= m - 1;
   return v;
 }
 

@@ -161,15 +161,15 @@ MPJ_DEV int tile_index(int m, int n, int r, int a0, int i) {
   return v < n ? v : -1;
 }
 
-// Queue the loads of tile (ti, tj) into Tb (column-major, Tb[j][i] = A(R[i], C[j])).
-MPJ_DEV void tile_load(const double* __restrict__ A, int lda, int m, int n, int r, int ti, int tj,
-                       double (*Tb)[2 * TS + 1]) {
+// Queue the loads of a tile into Tb (column-major, Tb[j][i] = A(R[i], C[j]));
+// R, C: the tile's row and column index lists (-1 = no such index).
+MPJ_DEV void tile_load(const double* __restrict__ A, int lda, const int* R, const int* C, double (*Tb)[2 * TS + 1]) {
   const int i = threadIdx.x % (2 * TS), jg = threadIdx.x / (2 * TS);
-  const int Ri = tile_index(m, n, r, ti * TS, i);
+  const int Ri = R[i];
 #pragma unroll
   for (int k = 0; k < (2 * TS * 2 * TS) / 256; ++k) {
     const int j = jg + k * (256 / (2 * TS));
-    const int Cj = tile_index(m, n, r, tj * TS, j);
+    const int Cj = C[j];
     if (Ri >= 0 && Cj >= 0)
       cp_async8(&Tb[j][i], A + (size_t)Cj * lda + Ri);
     else
@@ -183,43 +183,53 @@ MPJ_DEV void tile_load(const double* __restrict__ A, int lda, int m, int n, int 
 // (2TS x 2TS entries); each tile is loaded into shared memory with cp.async
 // while the previous one is computed, updated in place (thread (la, lb) owns
 // the 2x2 block of slots a = a0 + la, b = b0 + lb) and written back together
-// with its mirror, both coalesced.
+// with its mirror, both coalesced.  Index lists are built once per tile.
 __global__ void __launch_bounds__(256) rr_step64(double* __restrict__ A, int lda, int n, int m, int r, double skip,
                                                  const FRec* __restrict__ rec, FRec* __restrict__ rec_next,
                                                  const double2* __restrict__ dcur, double2* __restrict__ dnext,
                                                  double2* __restrict__ hist_row, int n_atiles) {
   __shared__ double Tb[2][2 * TS][2 * TS + 1];
+  __shared__ int RC[2][2][2 * TS];  // [buffer][rows, cols][i]
   const int half = m / 2;
   const int rn = (r + 1 == m - 1) ? 0 : r + 1;  // next round (wraps into the next sweep)
   const int la = threadIdx.x % TS, lb = threadIdx.x / TS;
   int t = blockIdx.x;
   if (t >= n_atiles) return;
-  int ti, tj;
-  tri_tile(t, ti, tj);
-  tile_load(A, lda, m, n, r, ti, tj, Tb[0]);
+  auto build_lists = [&](int tt, int buf) {
+    if (threadIdx.x < 4 * TS) {
+      int ti2, tj2;
+      tri_tile(tt, ti2, tj2);
+      const int which = threadIdx.x / (2 * TS), i = threadIdx.x % (2 * TS);
+      RC[buf][which][i] = tile_index(m, n, r, (which ? tj2 : ti2) * TS, i);
+    }
+  };
+  build_lists(t, 0);
+  __syncthreads();
+  tile_load(A, lda, RC[0][0], RC[0][1], Tb[0]);
   for (int it = 0; t < n_atiles; ++it, t += gridDim.x) {
     const int cur = it & 1;
+    int ti, tj;
     tri_tile(t, ti, tj);
     const int tn = t + gridDim.x;
     if (tn < n_atiles) {
-      int tin, tjn;
-      tri_tile(tn, tin, tjn);
-      tile_load(A, lda, m, n, r, tin, tjn, Tb[cur ^ 1]);
+      build_lists(tn, cur ^ 1);
+      __syncthreads();
+      tile_load(A, lda, RC[cur ^ 1][0], RC[cur ^ 1][1], Tb[cur ^ 1]);
       cp_async_wait_1();
     } else {
       cp_async_wait_0();
     }
     __syncthreads();
     double (*T)[2 * TS + 1] = Tb[cur];
+    const int* R = RC[cur][0];
+    const int* C = RC[cur][1];
     const int a = ti * TS + la, b = tj * TS + lb;
     bool changed = false;
     if (a < half && b < half && (ti != tj || a >= b)) {
-      int xa, ya, xb, yb;
-      rr_slot(m, r, a, xa, ya);
-      rr_slot(m, r, b, xb, yb);
+      const int xa = R[la], ya = R[TS + la], xb = C[lb], yb = C[TS + lb];  // -1: no such index
       const FRec ra = rec[a];
       const bool rota = frec_rotated(ra);
-      const bool vxa = xa < n, vya = ya < n;
+      const bool vxa = xa >= 0, vya = ya >= 0;
       if (a == b) {
         const double cm1 = rota ? ra.cm1 : 0.0;
         double2 sx = vxa ? dd_scale(dcur[xa], cm1) : make_double2(1.0, 0.0);
@@ -236,7 +246,8 @@ __global__ void __launch_bounds__(256) rr_step64(double* __restrict__ A, int lda
           axy_s = 0.0;
           changed = true;
         }
-        // the unpaired index of round rn when n is odd (slot 0 pairs it with the dummy)
+        // the unpaired index of round rn when n is odd: slot 0 of round rn
+        // pairs rn with the dummy index m - 1 = n
         if ((n & 1) && (xa == rn || ya == rn)) {
           FRec z;
           z.mx = 0.0;
@@ -298,26 +309,26 @@ __global__ void __launch_bounds__(256) rr_step64(double* __restrict__ A, int lda
     if (any) {
       // tile: A(R[i], C[j]) = T[j][i], coalesced over i
       const int i = threadIdx.x % (2 * TS), jg = threadIdx.x / (2 * TS);
-      const int Ri = tile_index(m, n, r, ti * TS, i);
+      const int Ri = R[i];
 #pragma unroll
       for (int k = 0; k < (2 * TS * 2 * TS) / 256; ++k) {
         const int j = jg + k * (256 / (2 * TS));
-        const int Cj = tile_index(m, n, r, tj * TS, j);
+        const int Cj = C[j];
         if (Ri >= 0 && Cj >= 0) A[(size_t)Cj * lda + Ri] = T[j][i];
       }
       if (ti != tj) {
         // mirror: A(C[j], R[i]) = T[j][i], coalesced over j
         const int j = threadIdx.x % (2 * TS), ig = threadIdx.x / (2 * TS);
-        const int Cj = tile_index(m, n, r, tj * TS, j);
+        const int Cj = C[j];
 #pragma unroll
         for (int k = 0; k < (2 * TS * 2 * TS) / 256; ++k) {
           const int i2 = ig + k * (256 / (2 * TS));
-          const int Ri2 = tile_index(m, n, r, ti * TS, i2);
+          const int Ri2 = R[i2];
           if (Ri2 >= 0 && Cj >= 0) A[(size_t)Ri2 * lda + Cj] = T[j][i2];
         }
       }
     }
-    __syncthreads();  // T is refilled two iterations later
+    __syncthreads();  // T and the lists are refilled two iterations later
   }
 }
 

@@ -181,8 +181,8 @@ MPJ_DEV void tile_mm(const float (*Lt)[LD4], const float (*R)[LD4], float acc[4]
 __global__ void __launch_bounds__(UT) update32(float* __restrict__ A32, float* __restrict__ V32, int N, int nb, int R,
                                                const float* __restrict__ Sbuf, const float* __restrict__ Ubuf,
                                                int n_atiles) {
-  __shared__ __align__(16) float T[W2][LD4];   // the tile, row-major T[i][j]
-  __shared__ __align__(16) float XT[W2][LD4];  // (U_P^T T)^T, i.e. XT[l][i] = X[i][l]
+  // three 32 x 32 buffers (13.5 KB): the tile (later X^T), U_P, U_Q
+  __shared__ __align__(16) float T[W2][LD4];
   __shared__ __align__(16) float UP[W2][LD4];  // U_P[l][i]
   __shared__ __align__(16) float UQ[W2][LD4];  // U_Q[l][j]
   const int tid = threadIdx.x;
@@ -213,15 +213,17 @@ __global__ void __launch_bounds__(UT) update32(float* __restrict__ A32, float* _
       UQ[li][lj] = Uq[e];
     }
     __syncthreads();
-    // X = U_P^T T: X[i][j] = sum_l U_P[l][i] T[l][j]; store XT[j][i]
+    // X = U_P^T T: X[i][j] = sum_l U_P[l][i] T[l][j]
     tile_mm(UP, T, acc, i4, j4);
+    __syncthreads();  // every thread is done reading T
 #pragma unroll
     for (int a = 0; a < 4; ++a)
 #pragma unroll
-      for (int b = 0; b < 4; ++b) XT[j4 + b][i4 + a] = acc[a][b];
+      for (int b = 0; b < 4; ++b) T[j4 + b][i4 + a] = acc[a][b];  // T now holds X^T
     __syncthreads();
-    // Y = X U_Q: Y[i][j] = sum_l X[i][l] U_Q[l][j] = sum_l XT[l][i] U_Q[l][j]
-    tile_mm(XT, UQ, acc, i4, j4);
+    // Y = X U_Q: Y[i][j] = sum_l X^T[l][i] U_Q[l][j]
+    tile_mm(T, UQ, acc, i4, j4);
+    __syncthreads();
 #pragma unroll
     for (int a = 0; a < 4; ++a)
 #pragma unroll
@@ -244,11 +246,11 @@ __global__ void __launch_bounds__(UT) update32(float* __restrict__ A32, float* _
   const float* Uq = Ubuf + (size_t)Q * W2 * W2;
   for (int e = tid; e < W2 * W2; e += UT) {
     int li = e % W2, lj = e / W2;
-    XT[lj][li] = V32[(size_t)gidx(IQ, JQ, lj) * N + rc * W2 + li];  // XT[l][i] = T[i][l]
+    UP[lj][li] = V32[(size_t)gidx(IQ, JQ, lj) * N + rc * W2 + li];  // UP holds the chunk transposed
     UQ[li][lj] = Uq[e];
   }
   __syncthreads();
-  tile_mm(XT, UQ, acc, i4, j4);
+  tile_mm(UP, UQ, acc, i4, j4);
 #pragma unroll
   for (int a = 0; a < 4; ++a)
 #pragma unroll

@@ -20,6 +20,7 @@
 #include "common.cuh"
 #include "gemm64.cuh"
 #include "jacobi64.cuh"
+#include "ns_fast.cuh"
 #include "stage1.cuh"
 
 #include <atomic>
@@ -55,8 +56,10 @@ Layout layout(int n, int passes) {
   L.Z = off;
   if (passes >= 2) off += sq;
   L.S1 = off;
+  // stage-1 buffers, or later an n x n FP64 temporary plus the FP32 Newton-Schulz scratch
   size_t s1 = al(mpj_stage1_bytes(n));
-  if (s1 < sq) s1 = sq;
+  size_t s1b = sq + al(mpj_ns_fast_bytes(n));
+  if (s1 < s1b) s1 = s1b;
   off += s1;
   L.scratch = off;
   off += al(mpj_jacobi64_scratch_bytes(n));
@@ -198,13 +201,18 @@ int fill_opts(int n, const mpj_opts* in, mpj_opts* o) {
   return MPJ_OK;
 }
 
-// Newton-Schulz X <- X (3I - X^T X) / 2 as X <- 1.5 X - 0.5 X (X^T X):
-// SYRK-like symmetric M = X^T X (n^3 flops) then the product with the fused
-// epilogue (2 n^3 flops).  X, M, Y are n x n with ld n; the result ends in *X.
-int ns_steps_run(int n, double** X, double* M, double** Y, int steps, cudaStream_t s) {
+// Newton-Schulz X <- X (3I - X^T X) / 2, written X <- X + X E / 2 with
+// E = I - X^T X: the symmetric product M = X^T X on the FP64 DMMA kernel
+// (n^3 flops, lower tiles mirrored), E in FP64, then X E either in FP32 when
+// max|E| <= 2^-30 (ns_fast.cu) or on the FP64 kernel (2 n^3 flops).  X, M, Y
+// are n x n with ld n; `fp32work` holds mpj_ns_fast_bytes(n).  The result
+// ends in *X.
+int ns_steps_run(int n, double** X, double* M, double** Y, int steps, void* fp32work, cudaStream_t s) {
   for (int k = 0; k < steps; ++k) {
     MPJ_CUDA_TRY(mpj_gemm64(true, false, n, n, n, 1.0, *X, n, *X, n, 0.0, nullptr, n, M, n, 1, s));
-    MPJ_CUDA_TRY(mpj_gemm64(false, false, n, n, n, -0.5, *X, n, M, n, 1.5, *X, n, *Y, n, 0, s));
+    int r = mpj_ns_fp32_correction(n, *X, M, *Y, fp32work, nullptr, s);
+    if (r < 0) return r;
+    if (r == 1) MPJ_CUDA_TRY(mpj_gemm64(false, false, n, n, n, 0.5, *X, n, M, n, 1.0, *X, n, *Y, n, 0, s));
     double* t = *X;
     *X = *Y;
     *Y = t;
@@ -338,7 +346,7 @@ int mpj_syev_ex(int n, const double* A, int lda, double* W, double* Q, int ldq, 
       // stage 2: Newton-Schulz -> X = Q_d
       double* Xp = X;
       double* Yp = Y;
-      if ((st = ns_steps_run(n, &Xp, M, &Yp, o.ns_steps, s)) != MPJ_OK) goto done;
+      if ((st = ns_steps_run(n, &Xp, M, &Yp, o.ns_steps, S1, s)) != MPJ_OK) goto done;
       tm.mark(2);
       // stage 3: A_cond = Q_d^T (A Q_d) -> M (symmetric), Yp = A Q_d
       if (mpj_gemm64(false, false, n, n, n, 1.0, A, lda, Xp, n, 0.0, nullptr, n, Yp, n, 0, s) != cudaSuccess ||
@@ -374,7 +382,9 @@ int mpj_syev_ex(int n, const double* A, int lda, double* W, double* Q, int ldq, 
         }
         double* X2 = Ql2;
         double* Y2 = (double*)S1;  // the stage-1 area is free again
-        if ((st = ns_steps_run(n, &X2, Z, &Y2, o.ns_steps, s)) != MPJ_OK) goto done;
+        if ((st = ns_steps_run(n, &X2, Z, &Y2, o.ns_steps, (char*)S1 + al((size_t)n * n * sizeof(double)), s)) !=
+            MPJ_OK)
+          goto done;
         // A_cond2 = Q_d2^T (A_cond Q_d2): T = A_cond Q_d2 into Z, then into M (A_cond is consumed)
         double* T = (X2 == Ql2) ? (double*)S1 : Ql2;
         if (mpj_gemm64(false, false, n, n, n, 1.0, M, n, X2, n, 0.0, nullptr, n, Z, n, 0, s) != cudaSuccess ||
@@ -434,13 +444,15 @@ int mpj_syev_ex(int n, const double* A, int lda, double* W, double* Q, int ldq, 
       if (o.polish) {
         // one more Newton-Schulz step on Q (not in the paper)
         double* T = (o.method == MPJ_METHOD_PLAIN) ? X : Vp;
-        if (mpj_gemm64(true, false, n, n, n, 1.0, Q, ldq, Q, ldq, 0.0, nullptr, n, M, n, 1, s) != cudaSuccess ||
-            mpj_gemm64(false, false, n, n, n, -0.5, Q, ldq, M, n, 1.5, Q, ldq, T, n, 0, s) != cudaSuccess) {
-          mpj_set_cuda_error(cudaGetLastError(), "polish", __LINE__);
-          st = MPJ_ECUDA;
+        double* Qc = (o.method == MPJ_METHOD_PLAIN) ? Y : M;  // Q with ld n (M is reused for Q^T Q below)
+        if (o.method != MPJ_METHOD_PLAIN) Qc = X;               // Q_d is no longer needed
+        copy_mat<<<blocks_for((size_t)n * n), 256, 0, s>>>(Q, ldq, Qc, n, n);
+        mpj_count_launch();
+        double* Qp = Qc;
+        double* Tp = T;
+        if ((st = ns_steps_run(n, &Qp, M, &Tp, 1, (char*)S1 + al((size_t)n * n * sizeof(double)), s)) != MPJ_OK)
           goto done;
-        }
-        copy_mat<<<blocks_for((size_t)n * n), 256, 0, s>>>(T, n, Q, ldq, n);
+        copy_mat<<<blocks_for((size_t)n * n), 256, 0, s>>>(Qp, n, Q, ldq, n);
         mpj_count_launch();
       }
       cudaError_t e = cudaGetLastError();
@@ -515,7 +527,7 @@ int mpj_newton_schulz(int n, double* X, int ldx, int steps, void* stream) {
   if (n <= 0 || !X || ldx < n || steps < 0) return MPJ_EINVAL;
   void* w = nullptr;
   size_t sq = al((size_t)n * n * sizeof(double));
-  if (cudaMallocAsync(&w, 3 * sq, s) != cudaSuccess) return MPJ_ENOMEM;
+  if (cudaMallocAsync(&w, 3 * sq + al(mpj_ns_fast_bytes(n)), s) != cudaSuccess) return MPJ_ENOMEM;
   double* Xc = (double*)w;
   double* M = (double*)((char*)w + sq);
   double* Y = (double*)((char*)w + 2 * sq);
@@ -523,7 +535,7 @@ int mpj_newton_schulz(int n, double* X, int ldx, int steps, void* stream) {
   mpj_count_launch();
   double* Xp = Xc;
   double* Yp = Y;
-  int st = ns_steps_run(n, &Xp, M, &Yp, steps, s);
+  int st = ns_steps_run(n, &Xp, M, &Yp, steps, (char*)w + 3 * sq, s);
   if (st == MPJ_OK) {
     copy_mat<<<blocks_for((size_t)n * n), 256, 0, s>>>(Xp, n, X, ldx, n);
     mpj_count_launch();
