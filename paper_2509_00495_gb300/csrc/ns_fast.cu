@@ -106,14 +106,21 @@ constexpr int RED = 256;
 
 }  // namespace
 
-size_t mpj_ns_fast_bytes(int n) { return 3 * (size_t)n * n * sizeof(float) + RED * sizeof(double) + 256; }
+static inline size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// Layout: E32, X32, C32 (n^2 floats each), then the max partials (doubles);
+// every part starts on a 256-byte boundary.
+size_t mpj_ns_fast_bytes(int n) {
+  return 3 * al256((size_t)n * n * sizeof(float)) + al256((RED + 1) * sizeof(double));
+}
 
 int mpj_ns_fp32_correction(int n, const double* X, double* M, double* Y, void* work, double* max_e,
                            cudaStream_t s) {
+  const size_t fb = al256((size_t)n * n * sizeof(float));
   float* E32 = (float*)work;
-  float* X32 = E32 + (size_t)n * n;
-  float* C32 = X32 + (size_t)n * n;
-  double* part = (double*)(C32 + (size_t)n * n);
+  float* X32 = (float*)((char*)work + fb);
+  float* C32 = (float*)((char*)work + 2 * fb);
+  double* part = (double*)((char*)work + 3 * fb);
   double* dmax = part + RED;
   ns_residual<<<RED, 256, 0, s>>>(M, X, n, E32, X32, part);
   mpj_count_launch();
