@@ -117,13 +117,32 @@ int mpj_syev_ex(int n, const double* A_dev, int lda, double* W_dev, double* Q_de
                 mpj_info* info, void* work_dev, size_t work_bytes, void* stream);
 
 /* Batched solve of `batch` independent matrices (sizes 1 <= n_i <= 256) in one
- * persistent launch: one CTA per matrix from a size-sorted work queue.
- * n_host: host array of sizes.  A_dev, W_dev, Q_dev: device arrays of `batch`
- * device pointers (A read only, lda_i = n_i; Q_i is n_i x n_i, ld n_i).
- * sweeps_host (may be NULL): receives the FP64 sweep count per matrix.
- * Synchronizes `stream`.  Returns MPJ_NOT_CONVERGED if any matrix hit the cap. */
+ * persistent launch (not in the paper; each matrix runs Algorithm 9 in one
+ * thread group).  n_host: host array of sizes.  A_dev, W_dev, Q_dev: device
+ * arrays of `batch` device pointers (A read only, lda_i = n_i; Q_i is
+ * n_i x n_i, ld n_i).  sweeps_host (may be NULL): receives the FP64 sweep count
+ * per matrix.  tol <= 0 selects n_i 2^-53 ||A_i||_F per matrix.
+ * The first call for a given (sizes, pointer arrays, tol) plans: it allocates
+ * a workspace with cudaMalloc, orders the queue by decreasing n, picks the
+ * thread-group size (256, 512 or 1024 threads per matrix) by timing each on
+ * this batch unless the size histogram was tuned before (choices persist in
+ * the file named by the environment variable MPJ_AUTOTUNE_CACHE, if set;
+ * MPJ_BATCHED_GROUP=256|512|1024 fixes the size instead), and
+ * captures [queue reset, kernel, result copies] in a CUDA graph.  Later calls
+ * with the same sizes and pointer arrays only launch that graph on `stream`
+ * (the pointed-to data may change); they may themselves be stream-captured,
+ * the first one may not.  Up to 4 plans are kept (mpj_release_plans frees
+ * them).  Synchronizes `stream`.  Returns MPJ_NOT_CONVERGED if any matrix hit
+ * the sweep cap, MPJ_ENONFINITE if any input holds a NaN or an infinity. */
 int mpj_syev_batched(int batch, const int* n_host, const double* const* A_dev, double* const* W_dev,
                      double* const* Q_dev, double tol, int* sweeps_host, void* stream);
+
+/* Frees the workspaces and graphs of all cached batched plans. */
+void mpj_release_plans(void);
+
+/* The autotuned thread-group size recorded for this batch's size histogram
+ * (256, 512 or 1024), or 0 if none has been tuned yet. */
+int mpj_batched_group_size(int batch, const int* n_host);
 
 /* Eigen-adjoint (not in the paper): with W, Q from a solve (Q n x n, ld ldq),
  * upstream gradients dW (n, may be NULL = 0) and dQ (n x n, ld lddq, may be

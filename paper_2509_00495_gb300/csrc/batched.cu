@@ -1,29 +1,55 @@
 // batched.cu -- many independent symmetric eigenproblems (sizes 1..256) in one
 // persistent launch.  Not in the paper: each matrix runs the mixed method of
-// Algorithm 9 (Sec. 5.1) on its own, inside one CTA.
+// Algorithm 9 (Sec. 5.1) on its own, inside one thread group.
 //
-// One CTA of 1024 threads per SM pulls matrix indices from an atomic work
-// queue ordered by decreasing n (longest job first).  For its matrix the CTA
+// A CTA of 1024 threads holds 1024/G groups of G threads (G = 256, 512 or
+// 1024, picked by the autotuner below); each group pulls matrix indices from
+// an atomic work queue ordered by decreasing n (longest job first) and, for
+// its matrix,
 //   1. FP32 round-robin Jacobi on fl32(A) from V32 = I until
 //      off(A32) <= n 2^-24 ||A||_F (cap max32), Q_l = double(V32);
 //   2. Newton-Schulz X <- 1.5 X - 0.5 X (X^T X), ns_steps times (FP64 DMMA);
 //   3. A_cond = X^T (A X) (FP64 DMMA, lower tiles mirrored);
 //   4. FP64 round-robin Jacobi on A_cond from V = I until off <= tol (cap max64);
 //   5. W = sorted diag, Q = X V (columns permuted), written to the caller.
-// The round-robin ordering, the rotation records and the 2x2-block update
-// are those of the single-matrix kernels (common.cuh); here one round is one
-// __syncthreads-separated phase of the CTA.  The CTA's matrices live in a
-// per-CTA slice of global workspace (L2-resident for the most part); FP64 is
-// the bound: GB300 issues about 2 FP64 FMA per clock per SM, so the batch
-// costs its total FP64 work over 152 SMs.
+// Groups synchronize with named barriers (bar.sync id, G), so small matrices
+// share an SM.  The round-robin ordering, the rotation records and the
+// 2x2-block update are those of common.cuh; one round is one barrier-separated
+// phase of the group.  The group's matrices live in a per-group slice of
+// global workspace.  FP64 is the bound: GB300 issues about 2 FP64 FMA per clock
+// per SM, so the batch costs its total FP64 work over 152 SMs.
+//
+// Planning and replay: the first call for a given batch (sizes, pointer
+// arrays, tolerance) allocates the workspace, sorts the queue, picks G (timed
+// on the batch itself unless a cached choice exists for its size histogram)
+// and captures [queue reset, kernel, result copies] in a CUDA graph; later
+// identical calls only launch that graph.
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <mutex>
+#include <string>
+#include <vector>
+
 #include "common.cuh"
 
 namespace {
 
 constexpr int NTH = 1024;
 constexpr int NMAX = 256;
+constexpr int MAXG = 4;  // groups per CTA at the smallest group size
 
-struct CtaBufs {
+struct Grp {
+  int t;    // thread index in the group
+  int n;    // threads in the group
+  int bar;  // named barrier id (1 + group index)
+  int id;   // group index in the CTA
+};
+
+MPJ_DEV void gsync(const Grp& g) { asm volatile("bar.sync %0, %1;\n" ::"r"(g.bar), "r"(g.n) : "memory"); }
+
+struct Bufs {
   float* A32;
   float* V32;
   double* X;
@@ -32,18 +58,18 @@ struct CtaBufs {
   double* Vp;  // aliases A32/V32 after stage 1
 };
 
-MPJ_DEV double block_sum(double v, double* red) {
+MPJ_DEV double group_sum(const Grp& g, double v, double* red) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  __syncthreads();
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
-  __syncthreads();
+  gsync(g);
+  if ((g.t & 31) == 0) red[g.t >> 5] = v;
+  gsync(g);
   double t = 0.0;
-  if (threadIdx.x < 32) {
-    t = red[threadIdx.x];
+  if (g.t < 32) {
+    t = g.t < (g.n >> 5) ? red[g.t] : 0.0;
     for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-    if (threadIdx.x == 0) red[32] = t;
+    if (g.t == 0) red[32] = t;
   }
-  __syncthreads();
+  gsync(g);
   return red[32];
 }
 
@@ -53,12 +79,12 @@ MPJ_DEV void dmma(double& c0, double& c1, double a, double b) {
                : "d"(a), "d"(b));
 }
 
-// CTA-level D = alpha op(A) op(B) + beta Cin (n x n, column-major, ld n for
-// A/B/C unless given), warp tasks of 16 x 16 outputs on m8n8k4 DMMA.
+// Group-level D = alpha op(A) op(B) + beta Cin (n x n, column-major, ld n),
+// warp tasks of 16 x 16 outputs on m8n8k4 DMMA.
 template <bool TA, bool TB>
-MPJ_DEV void cta_gemm(int n, double alpha, const double* A, int lda, const double* B, int ldb, double beta,
-                      const double* Cin, double* C, int ldc, bool sym) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+MPJ_DEV void grp_gemm(const Grp& g, int n, double alpha, const double* A, const double* B, double beta,
+                      const double* Cin, double* C, bool sym) {
+  const int lane = g.t & 31, warp = g.t >> 5, nw = g.n >> 5;
   const int gid = lane >> 2, tig = lane & 3;
   const int nt = (n + 15) / 16;
   for (int t = warp; t < nt * nt; t += nw) {
@@ -72,12 +98,12 @@ MPJ_DEV void cta_gemm(int n, double alpha, const double* A, int lda, const doubl
 #pragma unroll
       for (int i = 0; i < 2; ++i) {
         int r = m0 + i * 8 + gid;
-        af[i] = (r < n && kk < n) ? (TA ? A[(size_t)r * lda + kk] : A[(size_t)kk * lda + r]) : 0.0;
+        af[i] = (r < n && kk < n) ? (TA ? A[(size_t)r * n + kk] : A[(size_t)kk * n + r]) : 0.0;
       }
 #pragma unroll
       for (int j = 0; j < 2; ++j) {
         int c = n0 + j * 8 + gid;
-        bf[j] = (c < n && kk < n) ? (TB ? B[(size_t)kk * ldb + c] : B[(size_t)c * ldb + kk]) : 0.0;
+        bf[j] = (c < n && kk < n) ? (TB ? B[(size_t)kk * n + c] : B[(size_t)c * n + kk]) : 0.0;
       }
 #pragma unroll
       for (int i = 0; i < 2; ++i)
@@ -93,21 +119,21 @@ MPJ_DEV void cta_gemm(int n, double alpha, const double* A, int lda, const doubl
           int r = m0 + i * 8 + gid, c = n0 + j * 8 + tig * 2 + e;
           if (r >= n || c >= n || (sym && r < c)) continue;
           double v = alpha * acc[i][j][e];
-          if (beta != 0.0) v = fma(beta, Cin[(size_t)c * ldc + r], v);
-          C[(size_t)c * ldc + r] = v;
-          if (sym && r != c) C[(size_t)r * ldc + c] = v;
+          if (beta != 0.0) v = fma(beta, Cin[(size_t)c * n + r], v);
+          C[(size_t)c * n + r] = v;
+          if (sym && r != c) C[(size_t)r * n + c] = v;
         }
   }
-  __syncthreads();
+  gsync(g);
 }
 
-// One round-robin Jacobi sweep at CTA level on a symmetric n x n matrix A
+// One round-robin Jacobi sweep at group level on a symmetric n x n matrix A
 // (ld n) with vectors V (ld n).  rec: m/2 records in shared memory.
 template <typename T>
-MPJ_DEV void cta_rr_sweep(int n, T* A, T* V, RotRec<T>* rec, T skip) {
+MPJ_DEV void grp_rr_sweep(const Grp& g, int n, T* A, T* V, RotRec<T>* rec, T skip) {
   const int m = n + (n & 1), h = m / 2;
   for (int r = 0; r < m - 1; ++r) {
-    for (int i = threadIdx.x; i < h; i += blockDim.x) {
+    for (int i = g.t; i < h; i += g.n) {
       int x, y;
       rr_slot(m, r, i, x, y);
       T dx = x < n ? A[(size_t)x * n + x] : T(0);
@@ -117,8 +143,8 @@ MPJ_DEV void cta_rr_sweep(int n, T* A, T* V, RotRec<T>* rec, T skip) {
       rr_make_rec<T>(m, n, r, x, y, dx, dy, axy, skip, rr);
       rec[i] = rr;
     }
-    __syncthreads();
-    for (int e = threadIdx.x; e < h * h; e += blockDim.x) {
+    gsync(g);
+    for (int e = g.t; e < h * h; e += g.n) {
       int a = e % h, b = e / h;
       if (a < b) continue;
       RotRec<T> ra = rec[a];
@@ -156,7 +182,7 @@ MPJ_DEV void cta_rr_sweep(int n, T* A, T* V, RotRec<T>* rec, T skip) {
       if (vya && vxb) A[(size_t)xb * n + ya] = A[(size_t)ya * n + xb] = vyx;
       if (vya && vyb) A[(size_t)yb * n + ya] = A[(size_t)ya * n + yb] = vyy;
     }
-    for (int e = threadIdx.x; e < n * h; e += blockDim.x) {
+    for (int e = g.t; e < n * h; e += g.n) {
       int row = e % n, b = e / n;
       RotRec<T> rb = rec[b];
       if (!rec_rotated(rb.cm1, rb.sig)) continue;
@@ -167,47 +193,58 @@ MPJ_DEV void cta_rr_sweep(int n, T* A, T* V, RotRec<T>* rec, T skip) {
       V[(size_t)xb * n + row] = vx;
       V[(size_t)yb * n + row] = vy;
     }
-    __syncthreads();
+    gsync(g);
   }
 }
 
 template <typename T>
-MPJ_DEV double cta_off2(int n, const T* A, double* red) {
+MPJ_DEV double grp_off2(const Grp& g, int n, const T* A, double* red) {
   double s = 0.0;
-  for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+  for (int e = g.t; e < n * n; e += g.n) {
     int i = e % n, j = e / n;
     if (i != j) {
       double x = (double)A[e];
       s += x * x;
     }
   }
-  return block_sum(s, red);
+  return group_sum(g, s, red);
 }
 
+size_t group_bytes() {
+  return 2 * (size_t)NMAX * NMAX * sizeof(float) + 3 * (size_t)NMAX * NMAX * sizeof(double);
+}
+
+template <int G>
 __global__ void __launch_bounds__(NTH, 1)
     batched_syev(const int* __restrict__ order, const int* __restrict__ nvec, const double* const* __restrict__ Aptr,
                  double* const* __restrict__ Wptr, double* const* __restrict__ Qptr, int batch, double tol_in,
-                 int max32, int max64, int ns_steps, char* __restrict__ work, size_t per_cta, int* __restrict__ counter,
-                 int* __restrict__ sweeps_out, unsigned* __restrict__ flags) {
-  __shared__ double red[33];
-  __shared__ RotRec<double> rec64[NMAX / 2 + 1];
-  __shared__ RotRec<float> rec32[NMAX / 2 + 1];
-  __shared__ int job;
-  __shared__ int rank_sh[NMAX];
-  char* base = work + (size_t)blockIdx.x * per_cta;
-  CtaBufs B;
+                 int max32, int max64, int ns_steps, char* __restrict__ work, size_t per_group,
+                 int* __restrict__ counter, int* __restrict__ sweeps_out, unsigned* __restrict__ flags) {
+  constexpr int NG = NTH / G;
+  __shared__ double red[NG][33];
+  __shared__ RotRec<double> rec64[NG][NMAX / 2 + 1];
+  __shared__ RotRec<float> rec32[NG][NMAX / 2 + 1];
+  __shared__ int job[NG];
+  __shared__ int rank_sh[NG][NMAX];
+  Grp g;
+  g.id = threadIdx.x / G;
+  g.t = threadIdx.x % G;
+  g.n = G;
+  g.bar = 1 + g.id;
+  char* base = work + ((size_t)blockIdx.x * NG + g.id) * per_group;
+  Bufs B;
   B.A32 = (float*)base;
   B.V32 = B.A32 + NMAX * NMAX;
   B.Vp = (double*)base;
   B.X = (double*)(base + 2 * (size_t)NMAX * NMAX * sizeof(float));
   B.M = B.X + NMAX * NMAX;
   B.Y = B.M + NMAX * NMAX;
-  const int tid = threadIdx.x;
+  const int tid = g.t;
   for (;;) {
-    if (tid == 0) job = atomicAdd(counter, 1);
-    __syncthreads();
-    const int jb = job;
-    __syncthreads();
+    if (tid == 0) job[g.id] = atomicAdd(counter, 1);
+    gsync(g);
+    const int jb = job[g.id];
+    gsync(g);
     if (jb >= batch) break;
     const int idx = order[jb];
     const int n = nvec[idx];
@@ -217,80 +254,215 @@ __global__ void __launch_bounds__(NTH, 1)
     // a0: norms and finiteness
     double s = 0.0;
     bool bad = false;
-    for (int e = tid; e < n * n; e += NTH) {
+    for (int e = tid; e < n * n; e += G) {
       double x = A[e];
       if (!isfinite(x)) bad = true;
       s += x * x;
     }
     if (bad) atomicOr(flags, MPJ_FLAG_NONFINITE);
-    double normA = sqrt(block_sum(s, red));
+    double normA = sqrt(group_sum(g, s, red[g.id]));
     double tol = tol_in > 0 ? tol_in : (double)n * 0x1p-53 * normA;
     double tol32 = (double)n * 0x1p-24 * normA;
     // 1. stage 1 (FP32 round-robin)
-    for (int e = tid; e < n * n; e += NTH) {
+    for (int e = tid; e < n * n; e += G) {
       B.A32[e] = (float)A[e];
       B.V32[e] = (e % n == e / n) ? 1.0f : 0.0f;
     }
-    __syncthreads();
+    gsync(g);
     for (int sw = 0; sw < max32; ++sw) {
-      double off2 = cta_off2<float>(n, B.A32, red);
+      double off2 = grp_off2<float>(g, n, B.A32, red[g.id]);
       if (!(off2 > tol32 * tol32)) break;
-      cta_rr_sweep<float>(n, B.A32, B.V32, rec32, 0x1p-24f);
+      grp_rr_sweep<float>(g, n, B.A32, B.V32, rec32[g.id], 0x1p-24f);
     }
-    for (int e = tid; e < n * n; e += NTH) B.X[e] = (double)B.V32[e];
-    __syncthreads();
+    for (int e = tid; e < n * n; e += G) B.X[e] = (double)B.V32[e];
+    gsync(g);
     // 2. Newton-Schulz
     double* X = B.X;
     double* Y = B.Y;
     for (int k = 0; k < ns_steps; ++k) {
-      cta_gemm<true, false>(n, 1.0, X, n, X, n, 0.0, nullptr, B.M, n, true);
-      cta_gemm<false, false>(n, -0.5, X, n, B.M, n, 1.5, X, Y, n, false);
+      grp_gemm<true, false>(g, n, 1.0, X, X, 0.0, nullptr, B.M, true);
+      grp_gemm<false, false>(g, n, -0.5, X, B.M, 1.5, X, Y, false);
       double* t = X;
       X = Y;
       Y = t;
     }
     // 3. A_cond = X^T (A X) -> M
-    cta_gemm<false, false>(n, 1.0, A, n, X, n, 0.0, nullptr, Y, n, false);
-    cta_gemm<true, false>(n, 1.0, X, n, Y, n, 0.0, nullptr, B.M, n, true);
+    grp_gemm<false, false>(g, n, 1.0, A, X, 0.0, nullptr, Y, false);
+    grp_gemm<true, false>(g, n, 1.0, X, Y, 0.0, nullptr, B.M, true);
     // 4. FP64 sweeps, V = Y from I
     double* V = Y;
-    for (int e = tid; e < n * n; e += NTH) V[e] = (e % n == e / n) ? 1.0 : 0.0;
-    __syncthreads();
+    for (int e = tid; e < n * n; e += G) V[e] = (e % n == e / n) ? 1.0 : 0.0;
+    gsync(g);
     int sweeps = 0;
     for (;;) {
-      double off2 = cta_off2<double>(n, B.M, red);
+      double off2 = grp_off2<double>(g, n, B.M, red[g.id]);
       if (!(off2 > tol * tol) || n < 2) break;
       if (sweeps >= max64) {
         if (tid == 0) atomicOr(flags, MPJ_FLAG_TIMEOUT);  // cap reached: reported as not converged
         break;
       }
-      cta_rr_sweep<double>(n, B.M, V, rec64, 0x1p-53);
+      grp_rr_sweep<double>(g, n, B.M, V, rec64[g.id], 0x1p-53);
       ++sweeps;
     }
     // 5. sort, permute, Q = X Vp
-    for (int i = tid; i < n; i += NTH) {
+    for (int i = tid; i < n; i += G) {
       double wi = B.M[(size_t)i * n + i];
       int r = 0;
       for (int j = 0; j < n; ++j) {
         double wj = B.M[(size_t)j * n + j];
         r += (wj < wi) || (wj == wi && j < i);
       }
-      rank_sh[i] = r;
+      rank_sh[g.id][i] = r;
       W[r] = wi;
     }
-    __syncthreads();
-    for (int e = tid; e < n * n; e += NTH) {
+    gsync(g);
+    for (int e = tid; e < n * n; e += G) {
       int i = e % n, j = e / n;
-      B.Vp[(size_t)rank_sh[j] * n + i] = V[e];
+      B.Vp[(size_t)rank_sh[g.id][j] * n + i] = V[e];
     }
-    __syncthreads();
-    cta_gemm<false, false>(n, 1.0, X, n, B.Vp, n, 0.0, nullptr, Q, n, false);
+    gsync(g);
+    grp_gemm<false, false>(g, n, 1.0, X, B.Vp, 0.0, nullptr, Q, false);
     if (tid == 0) sweeps_out[idx] = sweeps;
-    __syncthreads();
+    gsync(g);
   }
 }
 
+// ---------------------------------------------------------------- host side
+typedef void (*KernelFn)(const int*, const int*, const double* const*, double* const*, double* const*, int, double,
+                         int, int, int, char*, size_t, int*, int*, unsigned*);
+
+KernelFn kernel_for(int G) {
+  if (G == 256) return batched_syev<256>;
+  if (G == 512) return batched_syev<512>;
+  return batched_syev<1024>;
+}
+
+const int kGroupSizes[3] = {256, 512, 1024};
+
+struct Plan {
+  int device = -1;
+  int batch = 0;
+  unsigned long long size_hash = 0, ptr_hash = 0;
+  double tol = 0;
+  int G = 0, grid = 0;
+  void* work = nullptr;      // device workspace (groups) + queue + results
+  int* h_sweeps = nullptr;   // pinned
+  unsigned* h_flags = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  cudaStream_t cap = nullptr;
+};
+
+std::mutex g_mu;
+std::vector<Plan*> g_plans;  // most recent last
+constexpr size_t kMaxPlans = 4;
+
+// Autotune cache: size-histogram signature -> group size.
+struct TuneEntry {
+  std::string key;
+  int G;
+};
+std::vector<TuneEntry> g_tune;
+bool g_tune_loaded = false;
+
+std::string signature(int batch, const int* n) {
+  // counts in 8 size buckets of 32, each rounded to a power of two
+  int c[8] = {0};
+  for (int i = 0; i < batch; ++i) c[(n[i] - 1) / 32]++;
+  char buf[128];
+  int len = 0;
+  for (int k = 0; k < 8; ++k) {
+    int p = 0;
+    while ((1 << p) < c[k]) ++p;
+    len += snprintf(buf + len, sizeof buf - len, "%s%d", k ? "-" : "", c[k] ? p + 1 : 0);
+  }
+  return std::string(buf, len);
+}
+
+void tune_load() {
+  if (g_tune_loaded) return;
+  g_tune_loaded = true;
+  const char* path = getenv("MPJ_AUTOTUNE_CACHE");
+  if (!path) return;
+  FILE* f = fopen(path, "r");
+  if (!f) return;
+  char key[128];
+  int G;
+  while (fscanf(f, "%127s %d", key, &G) == 2) g_tune.push_back({key, G});
+  fclose(f);
+}
+
+void tune_store(const std::string& key, int G) {
+  g_tune.push_back({key, G});
+  const char* path = getenv("MPJ_AUTOTUNE_CACHE");
+  if (!path) return;
+  FILE* f = fopen(path, "a");
+  if (!f) return;
+  fprintf(f, "%s %d\n", key.c_str(), G);
+  fclose(f);
+}
+
+int tune_lookup(const std::string& key) {
+  for (auto& e : g_tune)
+    if (e.key == key) return e.G;
+  return 0;
+}
+
+unsigned long long fnv(const void* p, size_t bytes, unsigned long long h = 1469598103934665603ull) {
+  const unsigned char* c = (const unsigned char*)p;
+  for (size_t i = 0; i < bytes; ++i) h = (h ^ c[i]) * 1099511628211ull;
+  return h;
+}
+
+void free_plan(Plan* p) {
+  if (p->exec) cudaGraphExecDestroy(p->exec);
+  if (p->cap) cudaStreamDestroy(p->cap);
+  if (p->work) cudaFree(p->work);
+  if (p->h_sweeps) cudaFreeHost(p->h_sweeps);
+  if (p->h_flags) cudaFreeHost(p->h_flags);
+  delete p;
+}
+
+struct Layout {
+  size_t groups_bytes, order, nvec, sweeps, counter, total;
+};
+
+Layout layout_for(int batch, int grid) {
+  Layout L;
+  size_t per_group = group_bytes();
+  L.groups_bytes = per_group * (size_t)grid * MAXG;  // enough for the smallest group size
+  L.order = L.groups_bytes;
+  L.nvec = L.order + (((size_t)batch * sizeof(int) + 255) & ~(size_t)255);
+  L.sweeps = L.nvec + (((size_t)batch * sizeof(int) + 255) & ~(size_t)255);
+  L.counter = L.sweeps + (((size_t)batch * sizeof(int) + 255) & ~(size_t)255);
+  L.total = L.counter + 256;
+  return L;
+}
+
+cudaError_t enqueue(const Plan* p, const Layout& L, const double* const* A, double* const* W, double* const* Q,
+                    int G, cudaStream_t s, bool count) {
+  char* base = (char*)p->work;
+  int* d_counter = (int*)(base + L.counter);
+  unsigned* d_flags = (unsigned*)(d_counter + 1);
+  cudaError_t e = cudaMemsetAsync(d_counter, 0, 2 * sizeof(int), s);
+  if (e != cudaSuccess) return e;
+  kernel_for(G)<<<p->grid, NTH, 0, s>>>((const int*)(base + L.order), (const int*)(base + L.nvec), A, W, Q, p->batch,
+                                        p->tol, 15, 30, 2, base, group_bytes(), d_counter, (int*)(base + L.sweeps),
+                                        d_flags);
+  if (count) mpj_count_launch();
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  e = cudaMemcpyAsync(p->h_sweeps, base + L.sweeps, sizeof(int) * p->batch, cudaMemcpyDeviceToHost, s);
+  if (e != cudaSuccess) return e;
+  return cudaMemcpyAsync(p->h_flags, d_flags, sizeof(unsigned), cudaMemcpyDeviceToHost, s);
+}
+
 }  // namespace
+
+extern "C" void mpj_release_plans(void) {
+  std::lock_guard<std::mutex> lock(g_mu);
+  for (Plan* p : g_plans) free_plan(p);
+  g_plans.clear();
+}
 
 extern "C" int mpj_syev_batched(int batch, const int* n_host, const double* const* A_dev, double* const* W_dev,
                                 double* const* Q_dev, double tol, int* sweeps_host, void* stream) {
@@ -302,64 +474,129 @@ extern "C" int mpj_syev_batched(int batch, const int* n_host, const double* cons
   int dev = 0, sms = 0;
   MPJ_CUDA_TRY(cudaGetDevice(&dev));
   MPJ_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  int grid = sms < batch ? sms : batch;
-  // longest job first: order by decreasing n, ties by index
-  int* order = (int*)malloc(sizeof(int) * (size_t)batch);
-  for (int i = 0; i < batch; ++i) order[i] = i;
-  // counting sort on n (1..NMAX), descending
-  {
-    int cnt[NMAX + 2] = {0};
-    for (int i = 0; i < batch; ++i) cnt[n_host[i]]++;
-    int start[NMAX + 2];
-    int acc = 0;
-    for (int v = NMAX; v >= 1; --v) {
-      start[v] = acc;
-      acc += cnt[v];
+  unsigned long long size_hash = fnv(n_host, sizeof(int) * (size_t)batch);
+  unsigned long long ptr_hash = fnv(&A_dev, sizeof A_dev, fnv(&W_dev, sizeof W_dev, fnv(&Q_dev, sizeof Q_dev)));
+
+  std::lock_guard<std::mutex> lock(g_mu);
+  Plan* plan = nullptr;
+  for (Plan* p : g_plans)
+    if (p->device == dev && p->batch == batch && p->size_hash == size_hash && p->ptr_hash == ptr_hash &&
+        p->tol == tol)
+      plan = p;
+  const int grid = sms;  // one CTA of 1024 threads per SM
+  const Layout L = layout_for(batch, grid);
+  if (!plan) {
+    plan = new Plan;
+    plan->device = dev;
+    plan->batch = batch;
+    plan->size_hash = size_hash;
+    plan->ptr_hash = ptr_hash;
+    plan->tol = tol;
+    plan->grid = grid;
+    cudaError_t e = cudaMalloc(&plan->work, L.total);
+    if (e == cudaSuccess) e = cudaMallocHost((void**)&plan->h_sweeps, sizeof(int) * (size_t)batch);
+    if (e == cudaSuccess) e = cudaMallocHost((void**)&plan->h_flags, sizeof(unsigned));
+    if (e != cudaSuccess) {
+      mpj_set_cuda_error(e, "batched plan allocation", __LINE__);
+      free_plan(plan);
+      return MPJ_ENOMEM;
     }
-    for (int i = 0; i < batch; ++i) order[start[n_host[i]]++] = i;
+    // longest job first: order by decreasing n (counting sort), ties by index
+    std::vector<int> order(batch);
+    {
+      int cnt[NMAX + 2] = {0}, start[NMAX + 2];
+      for (int i = 0; i < batch; ++i) cnt[n_host[i]]++;
+      int acc = 0;
+      for (int v = NMAX; v >= 1; --v) {
+        start[v] = acc;
+        acc += cnt[v];
+      }
+      for (int i = 0; i < batch; ++i) order[start[n_host[i]]++] = i;
+    }
+    char* base = (char*)plan->work;
+    e = cudaMemcpy(base + L.order, order.data(), sizeof(int) * (size_t)batch, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(base + L.nvec, n_host, sizeof(int) * (size_t)batch, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+      mpj_set_cuda_error(e, "batched plan upload", __LINE__);
+      free_plan(plan);
+      return MPJ_ECUDA;
+    }
+    // autotune the group size on this batch unless its size histogram is known
+    tune_load();
+    const std::string key = signature(batch, n_host);
+    int G = tune_lookup(key);
+    if (const char* force = getenv("MPJ_BATCHED_GROUP")) {  // fixed group size (testing)
+      int f = atoi(force);
+      if (f == 256 || f == 512 || f == 1024) G = f;
+    }
+    if (!G) {
+      float best = 1e30f;
+      cudaEvent_t e0, e1;
+      cudaEventCreate(&e0);
+      cudaEventCreate(&e1);
+      for (int c = 0; c < 3; ++c) {
+        cudaEventRecord(e0, s);
+        cudaError_t ee = enqueue(plan, L, A_dev, W_dev, Q_dev, kGroupSizes[c], s, true);
+        cudaEventRecord(e1, s);
+        if (ee == cudaSuccess) ee = cudaStreamSynchronize(s);
+        if (ee != cudaSuccess) {
+          mpj_set_cuda_error(ee, "batched autotune", __LINE__);
+          cudaEventDestroy(e0);
+          cudaEventDestroy(e1);
+          free_plan(plan);
+          return MPJ_ECUDA;
+        }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best) {
+          best = ms;
+          G = kGroupSizes[c];
+        }
+      }
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      tune_store(key, G);
+    }
+    plan->G = G;
+    // capture the replayable launch
+    e = cudaStreamCreateWithFlags(&plan->cap, cudaStreamNonBlocking);
+    cudaGraph_t graph = nullptr;
+    if (e == cudaSuccess) e = cudaStreamBeginCapture(plan->cap, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+      cudaError_t eq = enqueue(plan, L, A_dev, W_dev, Q_dev, G, plan->cap, false);
+      e = cudaStreamEndCapture(plan->cap, &graph);
+      if (eq != cudaSuccess) e = eq;
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&plan->exec, graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+      mpj_set_cuda_error(e, "batched graph capture", __LINE__);
+      free_plan(plan);
+      return MPJ_ECUDA;
+    }
+    if (g_plans.size() >= kMaxPlans) {
+      free_plan(g_plans.front());
+      g_plans.erase(g_plans.begin());
+    }
+    g_plans.push_back(plan);
   }
-  size_t per_cta = 2 * (size_t)NMAX * NMAX * sizeof(float) + 3 * (size_t)NMAX * NMAX * sizeof(double);
-  size_t small = 2 * (size_t)batch * sizeof(int) + (size_t)batch * sizeof(int) + 64;
-  void* w = nullptr;
-  cudaError_t e = cudaMallocAsync(&w, per_cta * grid + small, s);
-  if (e != cudaSuccess) {
-    free(order);
-    mpj_set_cuda_error(e, "batched workspace", __LINE__);
-    return MPJ_ENOMEM;
-  }
-  char* work = (char*)w;
-  int* d_order = (int*)(work + per_cta * grid);
-  int* d_n = d_order + batch;
-  int* d_sweeps = d_n + batch;
-  int* d_counter = d_sweeps + batch;
-  unsigned* d_flags = (unsigned*)(d_counter + 1);
-  int st = MPJ_OK;
-  unsigned hflags = 0;
-  e = cudaMemcpyAsync(d_order, order, sizeof(int) * batch, cudaMemcpyHostToDevice, s);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(d_n, n_host, sizeof(int) * batch, cudaMemcpyHostToDevice, s);
-  if (e == cudaSuccess) e = cudaMemsetAsync(d_counter, 0, 2 * sizeof(int), s);
-  if (e == cudaSuccess) {
-    batched_syev<<<grid, NTH, 0, s>>>(d_order, d_n, A_dev, W_dev, Q_dev, batch, tol, 15, 30, 2, work, per_cta,
-                                      d_counter, d_sweeps, d_flags);
-    mpj_count_launch();
-    e = cudaGetLastError();
-  }
-  if (e == cudaSuccess && sweeps_host)
-    e = cudaMemcpyAsync(sweeps_host, d_sweeps, sizeof(int) * batch, cudaMemcpyDeviceToHost, s);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(&hflags, d_flags, sizeof(unsigned), cudaMemcpyDeviceToHost, s);
+  cudaError_t e = cudaGraphLaunch(plan->exec, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) {
     mpj_set_cuda_error(e, "mpj_syev_batched", __LINE__);
-    st = MPJ_ECUDA;
+    return MPJ_ECUDA;
   }
-  cudaFreeAsync(w, s);
-  cudaStreamSynchronize(s);
-  free(order);
-  if (st == MPJ_OK) {
-    if (hflags & MPJ_FLAG_NONFINITE)
-      st = MPJ_ENONFINITE;
-    else if (hflags & MPJ_FLAG_TIMEOUT)
-      st = MPJ_NOT_CONVERGED;
-  }
-  return st;
+  mpj_count_launch();  // the graph's kernel
+  if (sweeps_host) memcpy(sweeps_host, plan->h_sweeps, sizeof(int) * (size_t)batch);
+  unsigned hflags = *plan->h_flags;
+  if (hflags & MPJ_FLAG_NONFINITE) return MPJ_ENONFINITE;
+  if (hflags & MPJ_FLAG_TIMEOUT) return MPJ_NOT_CONVERGED;
+  return MPJ_OK;
+}
+
+extern "C" int mpj_batched_group_size(int batch, const int* n_host) {
+  std::lock_guard<std::mutex> lock(g_mu);
+  tune_load();
+  if (batch <= 0 || !n_host) return 0;
+  return tune_lookup(signature(batch, n_host));
 }

@@ -141,7 +141,11 @@ MPJ_DEV int rr_make_rec(int m, int n, int r, int i, int j, T di, T dj, T aij, T 
   return slot;
 }
 
-MPJ_DEV bool rec_rotated(double cm1, double sig) { return cm1 != 0.0 || sig != 0.0; }
+// bit test rather than FP64 compares (those issue on the slow FP64 pipe);
+// "not rotated" records hold +0.0 exactly
+MPJ_DEV bool rec_rotated(double cm1, double sig) {
+  return (__double_as_longlong(cm1) | __double_as_longlong(sig)) != 0;
+}
 MPJ_DEV bool rec_rotated(float cm1, float sig) { return cm1 != 0.0f || sig != 0.0f; }
 
 // Loads that bypass L1 (data written by other CTAs earlier in the same

@@ -119,216 +119,125 @@ __device__ __forceinline__ void tri_tile(int t, int& ti, int& tj) {
   tj = t - r * (r + 1) / 2;
 }
 
-// Next-round records hosted by block (a, b): the coupling of a next-round
-// pair (i in slot a, j in slot b) is one of the block's four new entries.
-MPJ_DEV void next_records(int m, int n, int rn, double skip, int xa, int ya, int xb, int yb, int jx, int jy, bool nx,
-                          bool ny, const FRec& ra, const FRec& rb, bool rota, bool rotb, double vxx, double vxy,
-                          double vyx, double vyy, const double2* __restrict__ dcur, FRec* __restrict__ rec_next) {
-  const double cma = rota ? ra.cm1 : 0.0, cmb = rotb ? rb.cm1 : 0.0;
-#pragma unroll
-  for (int side = 0; side < 2; ++side) {
-    if (side == 0 && !nx) continue;
-    if (side == 1 && !ny) continue;
-    int i = side ? ya : xa;
-    int j = side ? jy : jx;
-    double di = side ? ra.dy : ra.dx;
-    double dj = (j == xb) ? rb.dx : rb.dy;
-    double aij_s = side ? ((j == xb) ? vyx : vyy) : ((j == xb) ? vxx : vxy);
-    double si = dd_scale(dcur[i], cma).x;
-    double sj = dd_scale(dcur[j], cmb).x;
-    FRec nr;
-    int sl = rr_make_frec(m, n, rn, i, j, di, dj, aij_s * si * sj, si, sj, skip, nr);
-    rec_next[sl] = nr;
-  }
-}
-
-MPJ_DEV void cp_async8(void* smem, const void* gmem) {
-  unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gmem));
-}
-MPJ_DEV void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
-MPJ_DEV void cp_async_wait_1() { asm volatile("cp.async.wait_group 1;\n" ::); }
-MPJ_DEV void cp_async_wait_0() { asm volatile("cp.async.wait_group 0;\n" ::); }
-
-// Index lists of a tile: rows x_a (i < TS) and y_a (i >= TS) of the slots
-// a0 .. a0+TS-1 of round r; -1 marks a slot beyond m/2 or an index >= n.
-MPJ_DEV int tile_index(int m, int n, int r, int a0, int i) {
-  int a = a0 + (i % TS);
-  if (a >= m / 2) return -1;
-  int x, y;
-  rr_slot(m, r, a, x, y);
-  int v = (i < TS) ? x : y;
-  return v < n ? v : -1;
-}
-
-// Queue the loads of a tile into Tb (column-major, Tb[j][i] = A(R[i], C[j]));
-// R, C: the tile's row and column index lists (-1 = no such index).
-MPJ_DEV void tile_load(const double* __restrict__ A, int lda, const int* R, const int* C, double (*Tb)[2 * TS + 1]) {
-  const int i = threadIdx.x % (2 * TS), jg = threadIdx.x / (2 * TS);
-  const int Ri = R[i];
-#pragma unroll
-  for (int k = 0; k < (2 * TS * 2 * TS) / 256; ++k) {
-    const int j = jg + k * (256 / (2 * TS));
-    const int Cj = C[j];
-    if (Ri >= 0 && Cj >= 0)
-      cp_async8(&Tb[j][i], A + (size_t)Cj * lda + Ri);
-    else
-      Tb[j][i] = 0.0;
-  }
-  cp_async_commit();
-}
-
-// One round on A (scaled form) + next round's records + this round's V
-// multipliers.  Persistent CTAs walk the lower-triangular TS x TS-slot tiles
-// (2TS x 2TS entries); each tile is loaded into shared memory with cp.async
-// while the previous one is computed, updated in place (thread (la, lb) owns
-// the 2x2 block of slots a = a0 + la, b = b0 + lb) and written back together
-// with its mirror, both coalesced.  Index lists are built once per tile.
+// One round on A (scaled form) + next round's records + this round's V multipliers.
 __global__ void __launch_bounds__(256) rr_step64(double* __restrict__ A, int lda, int n, int m, int r, double skip,
                                                  const FRec* __restrict__ rec, FRec* __restrict__ rec_next,
                                                  const double2* __restrict__ dcur, double2* __restrict__ dnext,
-                                                 double2* __restrict__ hist_row, int n_atiles) {
-  __shared__ double Tb[2][2 * TS][2 * TS + 1];
-  __shared__ int RC[2][2][2 * TS];  // [buffer][rows, cols][i]
+                                                 double2* __restrict__ hist_row) {
   const int half = m / 2;
   const int rn = (r + 1 == m - 1) ? 0 : r + 1;  // next round (wraps into the next sweep)
-  const int la = threadIdx.x % TS, lb = threadIdx.x / TS;
-  int t = blockIdx.x;
-  if (t >= n_atiles) return;
-  auto build_lists = [&](int tt, int buf) {
-    if (threadIdx.x < 4 * TS) {
-      int ti2, tj2;
-      tri_tile(tt, ti2, tj2);
-      const int which = threadIdx.x / (2 * TS), i = threadIdx.x % (2 * TS);
-      RC[buf][which][i] = tile_index(m, n, r, (which ? tj2 : ti2) * TS, i);
-    }
-  };
-  build_lists(t, 0);
-  __syncthreads();
-  tile_load(A, lda, RC[0][0], RC[0][1], Tb[0]);
-  for (int it = 0; t < n_atiles; ++it, t += gridDim.x) {
-    const int cur = it & 1;
-    int ti, tj;
-    tri_tile(t, ti, tj);
-    const int tn = t + gridDim.x;
-    if (tn < n_atiles) {
-      build_lists(tn, cur ^ 1);
-      __syncthreads();
-      tile_load(A, lda, RC[cur ^ 1][0], RC[cur ^ 1][1], Tb[cur ^ 1]);
-      cp_async_wait_1();
+  int ti, tj;
+  tri_tile(blockIdx.x, ti, tj);
+  const int a = ti * TS + (threadIdx.x % TS);
+  const int b = tj * TS + (threadIdx.x / TS);
+  if (a >= half || b >= half || a < b) return;
+  int xa, ya;
+  rr_slot(m, r, a, xa, ya);
+  const FRec ra = rec[a];
+  const bool rota = frec_rotated(ra);
+  const bool vxa = xa < n, vya = ya < n;
+  if (a == b) {
+    const double cm1 = rota ? frec_cm1(ra) : 0.0;
+    double2 sx = vxa ? dd_scale(dcur[xa], cm1) : make_double2(1.0, 0.0);
+    double2 sy = vya ? dd_scale(dcur[ya], cm1) : make_double2(1.0, 0.0);
+    if (vxa) dnext[xa] = sx;
+    if (vya) dnext[ya] = sy;
+    hist_row[a] = make_double2(ra.mx, ra.my);
+    double axy_s;  // scaled coupling after the round
+    if (rota) {
+      A[(size_t)xa * lda + xa] = ra.dx;
+      A[(size_t)ya * lda + ya] = ra.dy;
+      A[(size_t)ya * lda + xa] = 0.0;
+      A[(size_t)xa * lda + ya] = 0.0;
+      axy_s = 0.0;
     } else {
-      cp_async_wait_0();
+      axy_s = (vxa && vya) ? A[(size_t)ya * lda + xa] : 0.0;
     }
-    __syncthreads();
-    double (*T)[2 * TS + 1] = Tb[cur];
-    const int* R = RC[cur][0];
-    const int* C = RC[cur][1];
-    const int a = ti * TS + la, b = tj * TS + lb;
-    bool changed = false;
-    if (a < half && b < half && (ti != tj || a >= b)) {
-      const int xa = R[la], ya = R[TS + la], xb = C[lb], yb = C[TS + lb];  // -1: no such index
-      const FRec ra = rec[a];
-      const bool rota = frec_rotated(ra);
-      const bool vxa = xa >= 0, vya = ya >= 0;
-      if (a == b) {
-        const double cm1 = rota ? ra.cm1 : 0.0;
-        double2 sx = vxa ? dd_scale(dcur[xa], cm1) : make_double2(1.0, 0.0);
-        double2 sy = vya ? dd_scale(dcur[ya], cm1) : make_double2(1.0, 0.0);
-        if (vxa) dnext[xa] = sx;
-        if (vya) dnext[ya] = sy;
-        hist_row[a] = make_double2(ra.mx, ra.my);
-        double axy_s = T[TS + la][la];  // entry (x_a, y_a), scaled
-        if (rota) {
-          T[la][la] = ra.dx;
-          T[TS + la][TS + la] = ra.dy;
-          T[TS + la][la] = 0.0;
-          T[la][TS + la] = 0.0;
-          axy_s = 0.0;
-          changed = true;
-        }
-        // the unpaired index of round rn when n is odd: slot 0 of round rn
-        // pairs rn with the dummy index m - 1 = n
-        if ((n & 1) && (xa == rn || ya == rn)) {
-          FRec z;
-          z.mx = 0.0;
-          z.my = 0.0;
-          z.cm1 = 0.0;
-          z.dx = (xa == rn) ? ra.dx : ra.dy;
-          z.dy = 0.0;
-          rec_next[0] = z;
-        }
-        // m == 2: the same pair again in the next sweep
-        if (vxa && vya && rr_partner(m, rn, xa) == ya) {
-          FRec nr;
-          int sl = rr_make_frec(m, n, rn, xa, ya, ra.dx, ra.dy, axy_s * sx.x * sy.x, sx.x, sy.x, skip, nr);
-          rec_next[sl] = nr;
-        }
-      } else {
-        const FRec rb = rec[b];
-        const bool rotb = frec_rotated(rb);
-        double vxx = T[lb][la], vxy = T[TS + lb][la], vyx = T[lb][TS + la], vyy = T[TS + lb][TS + la];
-        if (rota) {  // rows x_a, y_a
-          double t0 = fma(-ra.mx, vyx, vxx), t1 = fma(ra.my, vxx, vyx);
-          double t2 = fma(-ra.mx, vyy, vxy), t3 = fma(ra.my, vxy, vyy);
-          vxx = t0;
-          vyx = t1;
-          vxy = t2;
-          vyy = t3;
-        }
-        if (rotb) {  // columns x_b, y_b
-          double t0 = fma(-rb.mx, vxy, vxx), t1 = fma(rb.my, vxx, vxy);
-          double t2 = fma(-rb.mx, vyy, vyx), t3 = fma(rb.my, vyx, vyy);
-          vxx = t0;
-          vxy = t1;
-          vyx = t2;
-          vyy = t3;
-        }
-        if (rota || rotb) {
-          changed = true;
-          T[lb][la] = vxx;
-          T[TS + lb][la] = vxy;
-          T[lb][TS + la] = vyx;
-          T[TS + lb][TS + la] = vyy;
-          if (ti == tj) {  // diagonal tile: keep its mirror half in step
-            T[la][lb] = vxx;
-            T[la][TS + lb] = vxy;
-            T[TS + la][lb] = vyx;
-            T[TS + la][TS + lb] = vyy;
-          }
-        }
-        const int jx = vxa ? rr_partner(m, rn, xa) : -1;
-        const int jy = vya ? rr_partner(m, rn, ya) : -1;
-        const bool nx = jx >= 0 && jx < n && (jx == xb || jx == yb);
-        const bool ny = jy >= 0 && jy < n && (jy == xb || jy == yb);
-        if (nx || ny)
-          next_records(m, n, rn, skip, xa, ya, xb, yb, jx, jy, nx, ny, ra, rb, rota, rotb, vxx, vxy, vyx, vyy, dcur,
-                       rec_next);
-      }
+    // the unpaired index of round rn when n is odd (slot 0 pairs it with the dummy)
+    if ((n & 1) && (xa == rn || ya == rn)) {
+      FRec z;
+      z.mx = 0.0;
+      z.my = 0.0;
+      z.cm1 = 0.0;
+      z.dx = (xa == rn) ? ra.dx : ra.dy;
+      z.dy = 0.0;
+      rec_next[0] = z;
     }
-    const bool any = __syncthreads_or(changed);
-    if (any) {
-      // tile: A(R[i], C[j]) = T[j][i], coalesced over i
-      const int i = threadIdx.x % (2 * TS), jg = threadIdx.x / (2 * TS);
-      const int Ri = R[i];
+    // m == 2: the same pair again in the next sweep
+    if (vxa && vya && rr_partner(m, rn, xa) == ya) {
+      FRec nr;
+      int sl = rr_make_frec(m, n, rn, xa, ya, ra.dx, ra.dy, axy_s * sx.x * sy.x, sx.x, sy.x, skip, nr);
+      rec_next[sl] = nr;
+    }
+    return;
+  }
+  int xb, yb;
+  rr_slot(m, r, b, xb, yb);
+  const FRec rb = rec[b];
+  const bool rotb = frec_rotated(rb);
+  const bool vxb = xb < n, vyb = yb < n;
+  // next-round pairs hosted by this block: (x_a or y_a) with (x_b or y_b)
+  int jx = vxa ? rr_partner(m, rn, xa) : -1;
+  int jy = vya ? rr_partner(m, rn, ya) : -1;
+  bool nx = jx >= 0 && jx < n && (jx == xb || jx == yb);
+  bool ny = jy >= 0 && jy < n && (jy == xb || jy == yb);
+  if (!rota && !rotb && !nx && !ny) return;
+  size_t cxb = (size_t)xb * lda, cyb = (size_t)yb * lda;
+  double vxx = (vxa && vxb) ? A[cxb + xa] : 0.0;
+  double vxy = (vxa && vyb) ? A[cyb + xa] : 0.0;
+  double vyx = (vya && vxb) ? A[cxb + ya] : 0.0;
+  double vyy = (vya && vyb) ? A[cyb + ya] : 0.0;
+  if (rota) {  // rows x_a, y_a
+    double t0 = fma(-ra.mx, vyx, vxx), t1 = fma(ra.my, vxx, vyx);
+    double t2 = fma(-ra.mx, vyy, vxy), t3 = fma(ra.my, vxy, vyy);
+    vxx = t0;
+    vyx = t1;
+    vxy = t2;
+    vyy = t3;
+  }
+  if (rotb) {  // columns x_b, y_b
+    double t0 = fma(-rb.mx, vxy, vxx), t1 = fma(rb.my, vxx, vxy);
+    double t2 = fma(-rb.mx, vyy, vyx), t3 = fma(rb.my, vyx, vyy);
+    vxx = t0;
+    vxy = t1;
+    vyx = t2;
+    vyy = t3;
+  }
+  if (rota || rotb) {
+    if (vxa && vxb) {
+      A[cxb + xa] = vxx;
+      A[(size_t)xa * lda + xb] = vxx;
+    }
+    if (vxa && vyb) {
+      A[cyb + xa] = vxy;
+      A[(size_t)xa * lda + yb] = vxy;
+    }
+    if (vya && vxb) {
+      A[cxb + ya] = vyx;
+      A[(size_t)ya * lda + xb] = vyx;
+    }
+    if (vya && vyb) {
+      A[cyb + ya] = vyy;
+      A[(size_t)ya * lda + yb] = vyy;
+    }
+  }
+  if (nx || ny) {
+    const double cma = rota ? frec_cm1(ra) : 0.0, cmb = rotb ? frec_cm1(rb) : 0.0;
 #pragma unroll
-      for (int k = 0; k < (2 * TS * 2 * TS) / 256; ++k) {
-        const int j = jg + k * (256 / (2 * TS));
-        const int Cj = C[j];
-        if (Ri >= 0 && Cj >= 0) A[(size_t)Cj * lda + Ri] = T[j][i];
-      }
-      if (ti != tj) {
-        // mirror: A(C[j], R[i]) = T[j][i], coalesced over j
-        const int j = threadIdx.x % (2 * TS), ig = threadIdx.x / (2 * TS);
-        const int Cj = C[j];
-#pragma unroll
-        for (int k = 0; k < (2 * TS * 2 * TS) / 256; ++k) {
-          const int i2 = ig + k * (256 / (2 * TS));
-          const int Ri2 = R[i2];
-          if (Ri2 >= 0 && Cj >= 0) A[(size_t)Ri2 * lda + Cj] = T[j][i2];
-        }
-      }
+    for (int side = 0; side < 2; ++side) {
+      if (side == 0 && !nx) continue;
+      if (side == 1 && !ny) continue;
+      int i = side ? ya : xa;
+      int j = side ? jy : jx;
+      double di = side ? ra.dy : ra.dx;
+      double dj = (j == xb) ? rb.dx : rb.dy;
+      double aij_s = side ? ((j == xb) ? vyx : vyy) : ((j == xb) ? vxx : vxy);
+      double si = dd_scale(dcur[i], cma).x;
+      double sj = dd_scale(dcur[j], cmb).x;
+      FRec nr;
+      int sl = rr_make_frec(m, n, rn, i, j, di, dj, aij_s * si * sj, si, sj, skip, nr);
+      rec_next[sl] = nr;
     }
-    __syncthreads();  // T and the lists are refilled two iterations later
   }
 }
 
@@ -593,11 +502,6 @@ int mpj_jacobi64_run(int n, double* A, int lda, double* V, int ldv, double tol, 
   if (ordering == MPJ_ORDER_ROUND_ROBIN) {
     const int nt = (half + TS - 1) / TS;
     const int n_atiles = nt * (nt + 1) / 2;  // lower-triangular TS x TS-slot tiles
-    int dev = 0, sms = 0, per_sm = 0;
-    MPJ_CUDA_TRY(cudaGetDevice(&dev));
-    MPJ_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    MPJ_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, rr_step64, 256, 0));
-    const int step_grid = n_atiles < sms * (per_sm > 0 ? per_sm : 1) ? n_atiles : sms * (per_sm > 0 ? per_sm : 1);
     const int fgrid = (int)(((size_t)n * n + 255) / 256 > 4096 ? 4096 : ((size_t)n * n + 255) / 256);
     int k = 0;  // buffer parity of records and scales
     bool need_init = true;
@@ -614,8 +518,8 @@ int mpj_jacobi64_run(int n, double* A, int lda, double* V, int ldv, double tol, 
       }
       int pending = 0, since_fold = 0;
       for (int r = 0; r < m - 1; ++r) {
-        rr_step64<<<step_grid, 256, 0, s>>>(A, lda, n, m, r, skip, rec[k], rec[k ^ 1], dsc[k], dsc[k ^ 1],
-                                            hist + (size_t)pending * half, n_atiles);
+        rr_step64<<<n_atiles, 256, 0, s>>>(A, lda, n, m, r, skip, rec[k], rec[k ^ 1], dsc[k], dsc[k ^ 1],
+                                           hist + (size_t)pending * half);
         mpj_count_launch();
         k ^= 1;
         ++pending;

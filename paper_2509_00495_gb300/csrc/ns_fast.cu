@@ -3,12 +3,13 @@
 // A Newton-Schulz step (Sec. 4.3.4) X <- X (3I - X^T X)/2 equals
 // X <- X + X E / 2 with E = I - X^T X.  The library forms X^T X in FP64 (its
 // error decides the orthogonality reached) and E = I - X^T X exactly enough
-// in FP64; when max|E| <= 2^-30 the product X E contributes at most ~2^-30
-// and an FP32 evaluation of it (relative error ~2^-22) is below the FP64
-// rounding of X itself, so it runs on the FP32 pipe (about 60x the FP64
-// rate on this GPU) instead of the FP64 one.  In the mixed solver this is the
-// second Newton-Schulz step (||E|| ~ (n u_l)^2) and any polish step; the first
-// step, with ||E|| ~ n u_l, stays in FP64.
+// in FP64.  An FP32 evaluation of X E errs per entry by about
+// sqrt(n) u_l max|E| (entries of X are O(1/sqrt n)); when
+// max|E| <= 2^-31 / sqrt(n) that is below u_d / 4, so the product runs on the
+// FP32 pipe (about 60x the FP64 rate on this GPU) instead of the FP64 one.
+// This holds for a polish step on an already orthogonal Q (||E|| ~ n u_d);
+// the solver's own Newton-Schulz steps (||E|| ~ n u_l, then ~ (n u_l)^2) stay
+// in FP64.
 #include "common.cuh"
 #include "ns_fast.cuh"
 
@@ -130,7 +131,7 @@ int mpj_ns_fp32_correction(int n, const double* X, double* M, double* Y, void* w
   MPJ_CUDA_TRY(cudaMemcpyAsync(&h, dmax, sizeof(double), cudaMemcpyDeviceToHost, s));
   MPJ_CUDA_TRY(cudaStreamSynchronize(s));
   if (max_e) *max_e = h;
-  if (!(h <= 0x1p-30)) return 1;  // too large for an FP32 correction; M now holds E
+  if (!(h <= 0x1p-31 / sqrt((double)n))) return 1;  // too large for FP32; M now holds E
   dim3 grid((n + SB - 1) / SB, (n + SB - 1) / SB);
   sgemm_nn<<<grid, 256, 0, s>>>(X32, E32, C32, n);
   mpj_count_launch();

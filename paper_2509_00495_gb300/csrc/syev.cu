@@ -409,9 +409,15 @@ int mpj_syev_ex(int n, const double* A, int lda, double* W, double* Q, int ldq, 
       Ac = M;
       V = Y;
     }
-    // stage 4: FP64 sweeps from V = I
-    set_identity<<<blocks_for((size_t)n * n), 256, 0, s>>>(V, n, n);
-    mpj_count_launch();
+    // stage 4: FP64 sweeps.  Plain: V from I.  Mixed: the rotations are applied
+    // to Q_d's columns directly (Q = Q_d V by associativity), which saves the
+    // final n x n x n product.
+    if (o.method == MPJ_METHOD_PLAIN) {
+      set_identity<<<blocks_for((size_t)n * n), 256, 0, s>>>(V, n, n);
+      mpj_count_launch();
+    } else {
+      V = Qd;
+    }
     {
       int r4 = mpj_jacobi64_run(n, Ac, n, V, n, tol, o.ordering, o.max_sweeps64, &sweeps64, &offf, &offc, scratch,
                                 mpj_jacobi64_scratch_bytes(n), s);
@@ -422,25 +428,14 @@ int mpj_syev_ex(int n, const double* A, int lda, double* W, double* Q, int ldq, 
       if (r4 == MPJ_NOT_CONVERGED) st = MPJ_NOT_CONVERGED;
     }
     tm.mark(4);
-    // stage 5: W = diag(A_cond), sorted; Q = Q_d V with V's columns permuted
+    // stage 5: W = diag(A_cond), sorted; Q = V (= Q_d V for the mixed method) with columns permuted
     {
       rank_diag<<<(n + 255) / 256, 256, 256 * sizeof(double), s>>>(Ac, n, n, o.sort, sm.rank, sm.w);
       mpj_count_launch();
       double* Vp = (double*)S1;  // the stage-1 area is free now
-      if (o.method == MPJ_METHOD_PLAIN) {
-        permute_cols<<<dim3((n + 255) / 256 > 16 ? 16 : (n + 255) / 256, n), 256, 0, s>>>(V, n, Q, ldq, n, sm.rank,
-                                                                                            sm.w, W);
-        mpj_count_launch();
-      } else {
-        permute_cols<<<dim3((n + 255) / 256 > 16 ? 16 : (n + 255) / 256, n), 256, 0, s>>>(V, n, Vp, n, n, sm.rank,
-                                                                                            sm.w, W);
-        mpj_count_launch();
-        if (mpj_gemm64(false, false, n, n, n, 1.0, Qd, n, Vp, n, 0.0, nullptr, n, Q, ldq, 0, s) != cudaSuccess) {
-          mpj_set_cuda_error(cudaGetLastError(), "final product", __LINE__);
-          st = MPJ_ECUDA;
-          goto done;
-        }
-      }
+      permute_cols<<<dim3((n + 255) / 256 > 16 ? 16 : (n + 255) / 256, n), 256, 0, s>>>(V, n, Q, ldq, n, sm.rank,
+                                                                                          sm.w, W);
+      mpj_count_launch();
       if (o.polish) {
         // one more Newton-Schulz step on Q (not in the paper)
         double* T = (o.method == MPJ_METHOD_PLAIN) ? X : Vp;

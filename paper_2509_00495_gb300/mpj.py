@@ -96,6 +96,8 @@ def lib():
         L.mpj_dgemm.argtypes = [ctypes.c_char, ctypes.c_char, _i, _i, _i, _d, _vp, _i, _vp, _i, _d, _vp, _i, _vp]
         if hasattr(L, "mpj_syev_batched"):
             L.mpj_syev_batched.argtypes = [_i, _ip, _vp, _vp, _vp, _d, _ip, _vp]
+            L.mpj_batched_group_size.argtypes = [_i, _ip]
+            L.mpj_release_plans.argtypes = []
         if hasattr(L, "mpj_syev_backward"):
             L.mpj_syev_backward.argtypes = [_i, _i, _vp, _vp, _i, _vp, _vp, _i, _vp, _i, _vp]
         _lib = L
@@ -252,6 +254,35 @@ def dgemm(transa: str, transb: str, alpha: float, A: torch.Tensor, B: torch.Tens
 
 
 # ------------------------------------------------------------------ batched
+class BatchedSolver:
+    """Repeated mpj_syev_batched calls on fixed device buffers (the planned,
+    graph-replayed path): inputs are copied into the solver's own matrices,
+    so every call after the first replays the same CUDA graph."""
+
+    def __init__(self, sizes, device="cuda"):
+        self.sizes = [int(n) for n in sizes]
+        self.A = [torch.empty(n, n, dtype=torch.float64, device=device) for n in self.sizes]
+        self.W = [torch.empty(n, dtype=torch.float64, device=device) for n in self.sizes]
+        self.Qt = [torch.empty(n, n, dtype=torch.float64, device=device) for n in self.sizes]
+        self.pa = torch.tensor([a.data_ptr() for a in self.A], dtype=torch.int64, device=device)
+        self.pw = torch.tensor([w.data_ptr() for w in self.W], dtype=torch.int64, device=device)
+        self.pq = torch.tensor([q.data_ptr() for q in self.Qt], dtype=torch.int64, device=device)
+        self.ns = (ctypes.c_int * len(self.sizes))(*self.sizes)
+
+    def solve(self, mats=None, tol: float = 0.0):
+        if mats is not None:
+            for dst, src in zip(self.A, mats):
+                dst.copy_(src)
+        sweeps = (ctypes.c_int * len(self.sizes))()
+        st = lib().mpj_syev_batched(len(self.sizes), self.ns, _ptr(self.pa), _ptr(self.pw), _ptr(self.pq), tol,
+                                    sweeps, _stream())
+        _check(st, "mpj_syev_batched")
+        return self.W, [q.T for q in self.Qt], list(sweeps), st
+
+    def group_size(self) -> int:
+        return int(lib().mpj_batched_group_size(len(self.sizes), self.ns))
+
+
 def syev_batched(mats: list[torch.Tensor], tol: float = 0.0):
     """mpj_syev_batched over a list of symmetric CUDA float64 matrices (n_i <= 256).
     Returns (list of W, list of Q, sweeps per matrix, status)."""

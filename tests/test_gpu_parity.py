@@ -404,3 +404,53 @@ def test_two_pass_geo_4096_properties():
     assert np.abs(host(r.W) - np.sort(lam)).max() <= 1e-12
     be, orF = _gpu_triple(A_t, r.W, r.Q)
     assert be <= 4 and orF <= 4, (be, orF)
+
+
+@pytest.mark.parametrize("group", ["256", "512", "1024"])
+def test_batched_each_group_size(group, monkeypatch):
+    """Every thread-group size the autotuner can pick gives oracle-exact results."""
+    monkeypatch.setenv("MPJ_BATCHED_GROUP", group)
+    rng = np.random.default_rng(int(group))
+    sizes = [3, 17, 64, 130, 256, 40 + int(group) // 256]  # a distinct size list -> a fresh plan
+    mats = []
+    for n in sizes:
+        g = rng.standard_normal((n, n)) / np.sqrt(n)
+        mats.append((g + g.T) / 2)
+    Ws, Qs, sweeps, st = mpj().syev_batched([dev(a) for a in mats])
+    assert st == 0
+    for a, W, Q in zip(mats, Ws, Qs):
+        W, Q = host(W), host(Q)
+        Wr, _, _ = oracle.syev_mixed(a, ordering32=oracle.ROUND_ROBIN, ordering64=oracle.ROUND_ROBIN)
+        assert np.abs(W - Wr).max() <= 1e-12 * max(np.linalg.norm(a, 2), 1e-300)
+        be, orF = triple(a, W, Q)
+        assert be <= 4 and orF <= 4
+
+
+def test_batched_graph_replay_and_autotune():
+    """Repeated solves on fixed buffers replay the planned graph; new data, same plan."""
+    m = mpj()
+    rng = np.random.default_rng(77)
+    sizes = list(rng.integers(8, 257, size=24))
+    solver = m.BatchedSolver(sizes)
+    for trial in range(3):
+        mats = []
+        for n in sizes:
+            g = rng.standard_normal((n, n)) / np.sqrt(n)
+            mats.append((g + g.T) / 2)
+        Ws, Qs, sweeps, st = solver.solve([dev(a) for a in mats])
+        assert st == 0
+        for a, W, Q in zip(mats, Ws, Qs):
+            wr = np.linalg.eigvalsh(a)
+            assert np.abs(host(W) - wr).max() <= 1e-12 * np.linalg.norm(a, 2)
+            be, orF = triple(a, host(W), host(Q))
+            assert be <= 4 and orF <= 4
+    assert solver.group_size() in (0, 256, 512, 1024)
+
+
+def test_batched_rejects_nonfinite():
+    m = mpj()
+    a = np.eye(5)
+    a[1, 2] = a[2, 1] = np.inf
+    with pytest.raises(m.MPJError) as e:
+        m.syev_batched([dev(a), dev(np.eye(3))])
+    assert e.value.status == m.MPJ_ENONFINITE
