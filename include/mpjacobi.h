@@ -67,6 +67,9 @@ typedef struct {
   int polish;        /* 1: one more FP64 Newton-Schulz step on the final Q (not in the paper) */
   int sort;          /* 1 (default): W ascending, Q's columns permuted to match              */
   int check_symmetry;/* 1: fail with MPJ_ENOTSYM unless A is exactly symmetric               */
+  int threshold;     /* FP64 sweeps also skip pairs with |a_pq| <= tol / n (threshold Jacobi, the
+                        paper's future work): 1 on, 0 off, -1 (default) on for the round-robin
+                        ordering and off for cyclic-by-row.  Cannot stop the sweeps early.      */
   int precond_passes;/* mixed method: 1 (default) = Algorithm 9; 2 = stages 1-3 applied again to
                         A_cond (FP32 Jacobi on fl32(A_cond), Newton-Schulz, Q_d2^T A_cond Q_d2,
                         Q_d = Q_d1 Q_d2) before the FP64 sweeps -- not in the paper            */

@@ -69,7 +69,7 @@ _d = ctypes.c_double
 class _Opts(ctypes.Structure):
     _fields_ = [("tol", _d), ("tol32", _d), ("skip_tol", _d), ("skip_tol32", _d),
                 ("max_sweeps64", _i), ("max_sweeps32", _i), ("ns_steps", _i),
-                ("ordering32", _i), ("ordering64", _i), ("polish", _i), ("sort", _i)]
+                ("ordering32", _i), ("ordering64", _i), ("polish", _i), ("sort", _i), ("threshold", _i)]
 
 
 class _Info(ctypes.Structure):
@@ -90,7 +90,7 @@ def _declare(L):
     L.orc_round_robin_pair.argtypes = [_i, _i, _i, _ip, _ip, _ip]
     L.orc_block_pair.argtypes = [_i, _i, _i, _i, _i, _ip, _ip]
     L.orc_block_pair.restype = _i
-    L.orc_jacobi_d.argtypes = [_i, _dp, _i, _dp, _i, _i, _d, _d, _i, _i, _ip, _llp, _dp]
+    L.orc_jacobi_d.argtypes = [_i, _dp, _i, _dp, _i, _i, _d, _d, _i, _i, _ip, _llp, _dp, _d]
     L.orc_jacobi_d.restype = _i
     L.orc_jacobi_f.argtypes = [_i, _fp, _i, _fp, _i, _i, _d, ctypes.c_float, _i, _ip, _llp, _dp]
     L.orc_jacobi_f.restype = _i
@@ -141,9 +141,9 @@ def _info(ci: _Info) -> Info:
 
 
 def _opts(n, tol=0.0, tol32=0.0, skip_tol=0.0, skip_tol32=0.0, max_sweeps64=0, max_sweeps32=0, ns_steps=0,
-          ordering32=CYCLIC, ordering64=CYCLIC, polish=False, sort=True) -> _Opts:
+          ordering32=CYCLIC, ordering64=CYCLIC, polish=False, sort=True, threshold=False) -> _Opts:
     return _Opts(tol, tol32, skip_tol, skip_tol32, max_sweeps64, max_sweeps32, ns_steps, ordering32, ordering64,
-                 int(polish), int(sort))
+                 int(polish), int(sort), int(threshold))
 
 
 # ---------------------------------------------------------------- primitives
@@ -214,7 +214,7 @@ def block_schedule(n: int):
 
 
 def jacobi(A, V=None, *, ordering=CYCLIC, tol=0.0, skip_tol=U_D, max_sweeps=30, paper_mode=False,
-           dtype=np.float64):
+           dtype=np.float64, skip_abs=0.0):
     """Cyclic Jacobi sweeps (Algorithm 4) on a copy of A; returns (A_final, V, sweeps, rotations, off, capped).
 
     dtype float64 runs the FP64 loop, float32 the FP32 loop (stage 1)."""
@@ -230,7 +230,7 @@ def jacobi(A, V=None, *, ordering=CYCLIC, tol=0.0, skip_tol=U_D, max_sweeps=30, 
         a = _f64(A)
         v = _f64(np.eye(n) if V is None else V)
         capped = L.orc_jacobi_d(n, _ptr(a), n, _ptr(v), n, ordering, tol, skip_tol, max_sweeps, int(paper_mode),
-                                ctypes.byref(sw), ctypes.byref(rot), ctypes.byref(of))
+                                ctypes.byref(sw), ctypes.byref(rot), ctypes.byref(of), skip_abs)
     return a, v, sw.value, rot.value, of.value, bool(capped)
 
 

@@ -230,7 +230,9 @@ void orc_sample_rotations(int n, void* A, int lda, void* V, int ldv, long long n
 
 /* Cyclic Jacobi, Algorithm 4, FP64.
  *  - skip rule: pair (p,q) is rotated iff |a_pq| > skip_tol * sqrt(|a_pp a_qq|)
- *    (Algorithm 4's test; skip_tol = 2^-53 in the paper's experiments);
+ *    (Algorithm 4's test; skip_tol = 2^-53 in the paper's experiments) and,
+ *    for the threshold variant (Sec. 6 future work: threshold Jacobi),
+ *    |a_pq| > skip_abs (skip_abs = 0 disables it);
  *  - stopping: when paper_mode = 0, stop as soon as off(A) <= tol, tested
  *    before the first sweep and after each sweep (the reading of the stopping
  *    rule used by this library); when paper_mode = 1, stop after a sweep with
@@ -239,7 +241,8 @@ void orc_sample_rotations(int n, void* A, int lda, void* V, int ldv, long long n
  * V must hold the starting matrix (the identity for a plain solve).
  * Returns 1 when the loop ended because of the cap (off > tol), else 0.     */
 int orc_jacobi_d(int n, double* A, int lda, double* V, int ldv, int ordering, double tol, double skip_tol,
-                 int max_sweeps, int paper_mode, int* sweeps_out, long long* rotations_out, double* off_out) {
+                 int max_sweeps, int paper_mode, int* sweeps_out, long long* rotations_out, double* off_out,
+                 double skip_abs) {
   int sweeps = 0;
   long long rot = 0;
   int capped = 0;
@@ -256,7 +259,7 @@ int orc_jacobi_d(int n, double* A, int lda, double* V, int ldv, int ordering, do
       for (int p = 0; p < n - 1; ++p)
         for (int q = p + 1; q < n; ++q) {
           double apq = AT(A, lda, p, q);
-          if (fabs(apq) > skip_tol * sqrt(fabs(AT(A, lda, p, p) * AT(A, lda, q, q)))) {
+          if (fabs(apq) > skip_tol * sqrt(fabs(AT(A, lda, p, p) * AT(A, lda, q, q))) && fabs(apq) > skip_abs) {
             double c, s;
             orc_jacobi_pair_d(AT(A, lda, p, p), AT(A, lda, q, q), apq, &c, &s);
             rotate_d(n, A, lda, V, ldv, p, q, c, s);
@@ -273,7 +276,7 @@ int orc_jacobi_d(int n, double* A, int lda, double* V, int ldv, int ordering, do
               int p, q;
               if (!orc_block_pair(n, R, P, rho, i, &p, &q)) continue;
               double apq = AT(A, lda, p, q);
-              if (fabs(apq) > skip_tol * sqrt(fabs(AT(A, lda, p, p) * AT(A, lda, q, q)))) {
+              if (fabs(apq) > skip_tol * sqrt(fabs(AT(A, lda, p, p) * AT(A, lda, q, q))) && fabs(apq) > skip_abs) {
                 double c, s;
                 orc_jacobi_pair_d(AT(A, lda, p, p), AT(A, lda, q, q), apq, &c, &s);
                 rotate_d(n, A, lda, V, ldv, p, q, c, s);
@@ -287,7 +290,7 @@ int orc_jacobi_d(int n, double* A, int lda, double* V, int ldv, int ordering, do
           int p, q;
           if (!rr_pair(n, r, i, &p, &q)) continue;
           double apq = AT(A, lda, p, q);
-          if (fabs(apq) > skip_tol * sqrt(fabs(AT(A, lda, p, p) * AT(A, lda, q, q)))) {
+          if (fabs(apq) > skip_tol * sqrt(fabs(AT(A, lda, p, p) * AT(A, lda, q, q))) && fabs(apq) > skip_abs) {
             double c, s;
             orc_jacobi_pair_d(AT(A, lda, p, p), AT(A, lda, q, q), apq, &c, &s);
             rotate_d(n, A, lda, V, ldv, p, q, c, s);
@@ -465,6 +468,7 @@ typedef struct {
   int ordering64;
   int polish;       /* 1: one more Newton-Schulz step on the final Q             */
   int sort;         /* 1: sort W ascending, permute Q's columns to match        */
+  int threshold;    /* 1: FP64 sweeps also skip pairs with |a_pq| <= tol / n     */
 } orc_opts;
 
 typedef struct {
@@ -563,7 +567,7 @@ int orc_syev_mixed(int n, const double* A, int lda, double* W, double* Q, int ld
   for (int j = 0; j < n; ++j)
     for (int i = 0; i < n; ++i) AT(V, n, i, j) = (i == j) ? 1.0 : 0.0;
   int capped = orc_jacobi_d(n, Ac, n, V, n, d.ordering64, d.tol, d.skip_tol, d.max_sweeps64, 0, &info->sweeps64,
-                            &info->rotations64, &info->off_final);
+                            &info->rotations64, &info->off_final, d.threshold ? d.tol / n : 0.0);
   info->capped64 = capped;
   for (int j = 0; j < n; ++j) W[j] = AT(Ac, n, j, j);
   orc_gemm_nn_d(n, n, n, X, n, V, n, Q, ldq);
@@ -591,7 +595,7 @@ int orc_syev_plain(int n, const double* A, int lda, double* W, double* Q, int ld
     }
   info->off_cond = orc_off_d(n, Ac, n);
   int capped = orc_jacobi_d(n, Ac, n, Q, ldq, d.ordering64, d.tol, d.skip_tol, d.max_sweeps64, 0, &info->sweeps64,
-                            &info->rotations64, &info->off_final);
+                            &info->rotations64, &info->off_final, d.threshold ? d.tol / n : 0.0);
   info->capped64 = capped;
   for (int j = 0; j < n; ++j) W[j] = AT(Ac, n, j, j);
   if (d.polish) orc_newton_schulz_d(n, Q, ldq, 1);

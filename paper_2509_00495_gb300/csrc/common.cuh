@@ -39,11 +39,11 @@ struct RotRec {
 };
 
 // Algorithm 2 with the skip test of Algorithm 4: rotate iff
-// |a_pq| > skip * sqrt(|a_pp a_qq|).  Outputs t, c - 1, s (for the (p,q)
-// order) and the rotated flag.
+// |a_pq| > skip * sqrt(|a_pp a_qq|) and (threshold variant) |a_pq| > skip_abs.
+// Outputs t, c - 1, s (for the (p,q) order) and the rotated flag.
 template <typename T>
-MPJ_DEV bool jacobi_pair(T app, T aqq, T apq, T skip, T& t, T& cm1, T& s) {
-  if (!(fabs(apq) > skip * sqrt(fabs(app * aqq)))) {
+MPJ_DEV bool jacobi_pair(T app, T aqq, T apq, T skip, T& t, T& cm1, T& s, T skip_abs = T(0)) {
+  if (!(fabs(apq) > skip * sqrt(fabs(app * aqq)) && fabs(apq) > skip_abs)) {
     t = T(0);
     cm1 = T(0);
     s = T(0);

@@ -67,13 +67,13 @@ MPJ_DEV double2 dd_scale(double2 d, double cm1) {
 // Record of pair (i, j) of round r from true diagonals di, dj, true coupling
 // aij and the scales si, sj the round will see.  Returns the slot.
 MPJ_DEV int rr_make_frec(int m, int n, int r, int i, int j, double di, double dj, double aij, double si, double sj,
-                         double skip, FRec& rec) {
+                         double skip, FRec& rec, double skip_abs) {
   int slot, iy;
   rr_slot_of(m, r, i, slot, iy);
   int p = i < j ? i : j, q = i < j ? j : i;
   double app = (p == i) ? di : dj, aqq = (p == i) ? dj : di;
   double t, cm1, s;
-  bool rot = (q < n) && jacobi_pair<double>(app, aqq, aij, skip, t, cm1, s);
+  bool rot = (q < n) && jacobi_pair<double>(app, aqq, aij, skip, t, cm1, s, skip_abs);
   double np = app, nq = aqq;
   if (rot) {
     np = app - t * aij;
@@ -92,7 +92,7 @@ MPJ_DEV int rr_make_frec(int m, int n, int r, int i, int j, double di, double dj
 
 // Records of round r from A's true entries when all scales are 1.
 __global__ void rr_init_frec(const double* __restrict__ A, int lda, int n, int m, int r, double skip,
-                             FRec* __restrict__ rec) {
+                             double skip_abs, FRec* __restrict__ rec) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= m / 2) return;
   int x, y;
@@ -101,7 +101,7 @@ __global__ void rr_init_frec(const double* __restrict__ A, int lda, int n, int m
   double dy = y < n ? A[(size_t)y * lda + y] : 0.0;
   double axy = (x < n && y < n) ? A[(size_t)y * lda + x] : 0.0;
   FRec fr;
-  rr_make_frec(m, n, r, x, y, dx, dy, axy, 1.0, 1.0, skip, fr);
+  rr_make_frec(m, n, r, x, y, dx, dy, axy, 1.0, 1.0, skip, fr, skip_abs);
   rec[i] = fr;
 }
 
@@ -121,7 +121,8 @@ __device__ __forceinline__ void tri_tile(int t, int& ti, int& tj) {
 
 // One round on A (scaled form) + next round's records + this round's V multipliers.
 __global__ void __launch_bounds__(256) rr_step64(double* __restrict__ A, int lda, int n, int m, int r, double skip,
-                                                 const FRec* __restrict__ rec, FRec* __restrict__ rec_next,
+                                                 double skip_abs, const FRec* __restrict__ rec,
+                                                 FRec* __restrict__ rec_next,
                                                  const double2* __restrict__ dcur, double2* __restrict__ dnext,
                                                  double2* __restrict__ hist_row) {
   const int half = m / 2;
@@ -166,7 +167,7 @@ __global__ void __launch_bounds__(256) rr_step64(double* __restrict__ A, int lda
     // m == 2: the same pair again in the next sweep
     if (vxa && vya && rr_partner(m, rn, xa) == ya) {
       FRec nr;
-      int sl = rr_make_frec(m, n, rn, xa, ya, ra.dx, ra.dy, axy_s * sx.x * sy.x, sx.x, sy.x, skip, nr);
+      int sl = rr_make_frec(m, n, rn, xa, ya, ra.dx, ra.dy, axy_s * sx.x * sy.x, sx.x, sy.x, skip, nr, skip_abs);
       rec_next[sl] = nr;
     }
     return;
@@ -235,7 +236,7 @@ __global__ void __launch_bounds__(256) rr_step64(double* __restrict__ A, int lda
       double si = dd_scale(dcur[i], cma).x;
       double sj = dd_scale(dcur[j], cmb).x;
       FRec nr;
-      int sl = rr_make_frec(m, n, rn, i, j, di, dj, aij_s * si * sj, si, sj, skip, nr);
+      int sl = rr_make_frec(m, n, rn, i, j, di, dj, aij_s * si * sj, si, sj, skip, nr, skip_abs);
       rec_next[sl] = nr;
     }
   }
@@ -366,7 +367,8 @@ __global__ void check_symmetric(const double* __restrict__ A, int lda, int n, un
 
 // ---- cyclic-by-row, one CTA per matrix (the paper's ordering and update) ----
 __global__ void __launch_bounds__(1024) cyclic_sweep64(double* __restrict__ A, int lda, double* __restrict__ V,
-                                                       int ldv, int n, double skip, int* __restrict__ rotated) {
+                                                       int ldv, int n, double skip, double skip_abs,
+                                                       int* __restrict__ rotated) {
   __shared__ double cs[2];
   __shared__ int go;
   int any = 0;
@@ -375,7 +377,7 @@ __global__ void __launch_bounds__(1024) cyclic_sweep64(double* __restrict__ A, i
       if (threadIdx.x == 0) {
         double app = A[(size_t)p * lda + p], aqq = A[(size_t)q * lda + q], apq = A[(size_t)q * lda + p];
         go = 0;
-        if (fabs(apq) > skip * sqrt(fabs(app * aqq))) {
+        if (fabs(apq) > skip * sqrt(fabs(app * aqq)) && fabs(apq) > skip_abs) {
           // Algorithm 2, stable form (Appendix A approach 2)
           double tau = (aqq - app) / (2.0 * apq);
           double t = tau >= 0.0 ? 1.0 / (tau + sqrt(1.0 + tau * tau)) : 1.0 / (tau - sqrt(1.0 + tau * tau));
@@ -466,7 +468,7 @@ size_t mpj_jacobi64_scratch_bytes(int n) { return mpj_jacobi64_scratch_bytes_rv(
 
 int mpj_jacobi64_run(int n, double* A, int lda, double* V, int ldv, double tol, int ordering, int max_sweeps,
                      int* sweeps_out, double* off_out, double* off_initial, void* scratch, size_t scratch_bytes,
-                     cudaStream_t s) {
+                     cudaStream_t s, double skip_abs) {
   const double skip = 0x1p-53;
   const int m = n + (n & 1);
   const int half = m / 2;
@@ -513,12 +515,12 @@ int mpj_jacobi64_run(int n, double* A, int lda, double* V, int ldv, double tol, 
       if (need_init) {
         d_reset<<<(n + 255) / 256, 256, 0, s>>>(dsc[k], n);
         mpj_count_launch();
-        rr_init_frec<<<(half + 127) / 128, 128, 0, s>>>(A, lda, n, m, 0, skip, rec[k]);
+        rr_init_frec<<<(half + 127) / 128, 128, 0, s>>>(A, lda, n, m, 0, skip, skip_abs, rec[k]);
         mpj_count_launch();
       }
       int pending = 0, since_fold = 0;
       for (int r = 0; r < m - 1; ++r) {
-        rr_step64<<<n_atiles, 256, 0, s>>>(A, lda, n, m, r, skip, rec[k], rec[k ^ 1], dsc[k], dsc[k ^ 1],
+        rr_step64<<<n_atiles, 256, 0, s>>>(A, lda, n, m, r, skip, skip_abs, rec[k], rec[k ^ 1], dsc[k], dsc[k ^ 1],
                                            hist + (size_t)pending * half);
         mpj_count_launch();
         k ^= 1;
@@ -537,7 +539,7 @@ int mpj_jacobi64_run(int n, double* A, int lda, double* V, int ldv, double tol, 
           if (!last) {  // records of round r+1 were built for the old scales
             d_reset<<<(n + 255) / 256, 256, 0, s>>>(dsc[k], n);
             mpj_count_launch();
-            rr_init_frec<<<(half + 127) / 128, 128, 0, s>>>(A, lda, n, m, r + 1, skip, rec[k]);
+            rr_init_frec<<<(half + 127) / 128, 128, 0, s>>>(A, lda, n, m, r + 1, skip, skip_abs, rec[k]);
             mpj_count_launch();
           }
         }
@@ -556,7 +558,7 @@ int mpj_jacobi64_run(int n, double* A, int lda, double* V, int ldv, double tol, 
         status = MPJ_NOT_CONVERGED;
         break;
       }
-      cyclic_sweep64<<<1, 1024, 0, s>>>(A, lda, V, ldv, n, skip, iscal);
+      cyclic_sweep64<<<1, 1024, 0, s>>>(A, lda, V, ldv, n, skip, skip_abs, iscal);
       mpj_count_launch();
       MPJ_CUDA_TRY(cudaGetLastError());
       int rotated = 0;

@@ -230,6 +230,7 @@ void mpj_opts_default(mpj_opts* o) {
   o->ordering = MPJ_ORDER_ROUND_ROBIN;
   o->method = MPJ_METHOD_MIXED;
   o->sort = 1;
+  o->threshold = -1;
 }
 
 const char* mpj_status_str(int st) {
@@ -419,8 +420,9 @@ int mpj_syev_ex(int n, const double* A, int lda, double* W, double* Q, int ldq, 
       V = Qd;
     }
     {
+      const bool thr = o.threshold > 0 || (o.threshold < 0 && o.ordering == MPJ_ORDER_ROUND_ROBIN);
       int r4 = mpj_jacobi64_run(n, Ac, n, V, n, tol, o.ordering, o.max_sweeps64, &sweeps64, &offf, &offc, scratch,
-                                mpj_jacobi64_scratch_bytes(n), s);
+                                mpj_jacobi64_scratch_bytes(n), s, thr ? tol / n : 0.0);
       if (r4 < 0) {
         st = r4;
         goto done;

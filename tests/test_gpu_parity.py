@@ -153,7 +153,8 @@ def test_syev_mixed_vs_oracle(n):
     A, lam = inputs.geo_matrix(n, 1e3, seed=11 * n) if n > 1 else (np.array([[-0.7]]), np.array([-0.7]))
     r = mpj().syev_ex(dev(A))
     W, Q = host(r.W), host(r.Q)
-    Wr, Qr, info = oracle.syev_mixed(A, ordering32=oracle.BLOCK_ROUND_ROBIN, ordering64=oracle.ROUND_ROBIN)
+    Wr, Qr, info = oracle.syev_mixed(A, ordering32=oracle.BLOCK_ROUND_ROBIN, ordering64=oracle.ROUND_ROBIN,
+                                     threshold=True)
     nA = np.linalg.norm(A, 2)
     assert r.status == 0
     assert np.all(np.diff(W) >= 0)
@@ -170,7 +171,7 @@ def test_syev_plain_vs_oracle(n):
     A, lam = inputs.geo_matrix(n, 1e3, seed=13 * n)
     r = mpj().syev_ex(dev(A), method="plain")
     W, Q = host(r.W), host(r.Q)
-    Wr, Qr, info = oracle.syev_plain(A, ordering64=oracle.ROUND_ROBIN)
+    Wr, Qr, info = oracle.syev_plain(A, ordering64=oracle.ROUND_ROBIN, threshold=True)
     nA = np.linalg.norm(A, 2)
     assert np.abs(W - Wr).max() <= 1e-12 * nA
     assert abs(r.info["sweeps64"] - info.sweeps64) <= 1
@@ -185,6 +186,21 @@ def test_syev_cyclic_fp64_stage_vs_oracle():
     Wr, Qr, info = oracle.syev_mixed(A, ordering32=oracle.BLOCK_ROUND_ROBIN, ordering64=oracle.CYCLIC)
     assert abs(r.info["sweeps64"] - info.sweeps64) <= 1
     assert np.abs(host(r.W) - Wr).max() <= 1e-12 * np.linalg.norm(A, 2)
+
+
+@pytest.mark.parametrize("threshold", [0, 1])
+def test_threshold_option_vs_oracle(threshold):
+    """The threshold variant (skip |a_pq| <= tol/n) on and off, against the oracle
+    with the same rule: same sweeps (+-1), same eigenvalues, same accuracy."""
+    n = 130
+    A, lam = inputs.geo_matrix(n, 1e6, seed=5)
+    r = mpj().syev_ex(dev(A), threshold=threshold)
+    Wr, _, info = oracle.syev_mixed(A, ordering32=oracle.BLOCK_ROUND_ROBIN, ordering64=oracle.ROUND_ROBIN,
+                                    threshold=bool(threshold))
+    assert abs(r.info["sweeps64"] - info.sweeps64) <= 1
+    assert np.abs(host(r.W) - Wr).max() <= 1e-12 * np.linalg.norm(A, 2)
+    be, orF = triple(A, host(r.W), host(r.Q))
+    assert be <= 4 and orF <= 4
 
 
 def test_paper_sweep_claims_small_cases():

@@ -29,8 +29,9 @@ MUTATIONS = {
     "gemm_tn_transposed": ("for (int l = 0; l < k; ++l) s += AT(A, lda, l, i) * AT(B, ldb, l, j);",
                            "for (int l = 0; l < k; ++l) s += AT(A, lda, i, l) * AT(B, ldb, l, j);"),
     "rr_pair_offset": ("b = ((r - i) % (m - 1) + (m - 1)) % (m - 1);", "b = ((r - i + 1) % (m - 1) + (m - 1)) % (m - 1);"),
-    "skip_rule_inverted": ("if (fabs(apq) > skip_tol * sqrt(fabs(AT(A, lda, p, p) * AT(A, lda, q, q)))) {",
-                           "if (fabs(apq) < skip_tol * sqrt(fabs(AT(A, lda, p, p) * AT(A, lda, q, q)))) {"),
+    "skip_rule_inverted": ("if (fabs(apq) > skip_tol * sqrt(fabs(AT(A, lda, p, p) * AT(A, lda, q, q))) && fabs(apq) > skip_abs) {",
+                           "if (fabs(apq) < skip_tol * sqrt(fabs(AT(A, lda, p, p) * AT(A, lda, q, q))) && fabs(apq) > skip_abs) {"),
+    "threshold_inverted": ("&& fabs(apq) > skip_abs) {", "&& fabs(apq) >= skip_abs * 0.0 + 1e300 * (skip_abs > 0)) {"),
     "backward_gap_sign": ("double gap = W[j] - W[i];", "double gap = W[i] - W[j];"),
     "backward_no_diag": ("g = dW ? dW[i] : 0.0;", "g = 0.0;"),
     "precondition_untransposed": ("orc_gemm_tn_d(n, n, n, Qd, ldq, W, n, Ac, ldc);", "orc_gemm_nn_d(n, n, n, Qd, ldq, W, n, Ac, ldc);"),

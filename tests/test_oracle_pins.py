@@ -445,3 +445,24 @@ def test_block_ordering_jacobi_against_eigh(n):
     a32, v32, sw32, _, of32, cap32 = oracle.jacobi(A, ordering=oracle.BLOCK_ROUND_ROBIN, tol=n * U_L * np.linalg.norm(A),
                                                    skip_tol=U_L, dtype=np.float32)
     assert not cap32 and of32 <= n * U_L * np.linalg.norm(A)
+
+
+# ---------------------------------------------------------------- threshold variant (Sec. 6 future work)
+@pytest.mark.parametrize("ordering", [oracle.CYCLIC, oracle.ROUND_ROBIN])
+def test_threshold_variant_same_result_fewer_rotations(ordering):
+    """Skipping pairs with |a_pq| <= tol/n cannot stop the sweeps early
+    (all such entries together give off(A) < tol) and leaves the result within
+    the stopping tolerance; it only saves rotations of negligible entries."""
+    n = 60
+    A, lam = inputs.geo_matrix(n, 1e5, seed=31)
+    tol = n * U_D * np.linalg.norm(A)
+    a0, v0, sw0, rot0, of0, cap0 = oracle.jacobi(A, ordering=ordering, tol=tol)
+    a1, v1, sw1, rot1, of1, cap1 = oracle.jacobi(A, ordering=ordering, tol=tol, skip_abs=tol / n)
+    assert not cap0 and not cap1 and of1 <= tol
+    assert rot1 < rot0
+    assert np.abs(np.sort(np.diag(a1)) - np.sort(lam)).max() <= 4 * n * U_D
+    assert np.linalg.norm(A @ v1 - v1 * np.diag(a1), 2) <= 4 * n * U_D * np.linalg.norm(A, 2)
+    W, Q, info = oracle.syev_mixed(A, ordering32=ordering, ordering64=ordering, threshold=True)
+    Wn, Qn, infon = oracle.syev_mixed(A, ordering32=ordering, ordering64=ordering)
+    assert info.rotations64 < infon.rotations64
+    assert np.abs(W - Wn).max() <= 1e-13
