@@ -29,6 +29,9 @@
 //
 // off(A) (Sec. 3.1, direct form) is reduced after every sweep with a fixed
 // reduction order, so repeated runs are bitwise identical.
+#include <memory>
+#include <cstdlib>
+
 #include "common.cuh"
 #include "jacobi64.cuh"
 
@@ -174,16 +177,16 @@ __global__ void __launch_bounds__(256) rr_step64(double* __restrict__ A, int lda
   }
   int xb, yb;
   rr_slot(m, r, b, xb, yb);
+  const bool vxb = xb < n, vyb = yb < n;
+  size_t cxb = (size_t)xb * lda, cyb = (size_t)yb * lda;
   const FRec rb = rec[b];
   const bool rotb = frec_rotated(rb);
-  const bool vxb = xb < n, vyb = yb < n;
   // next-round pairs hosted by this block: (x_a or y_a) with (x_b or y_b)
   int jx = vxa ? rr_partner(m, rn, xa) : -1;
   int jy = vya ? rr_partner(m, rn, ya) : -1;
   bool nx = jx >= 0 && jx < n && (jx == xb || jx == yb);
   bool ny = jy >= 0 && jy < n && (jy == xb || jy == yb);
   if (!rota && !rotb && !nx && !ny) return;
-  size_t cxb = (size_t)xb * lda, cyb = (size_t)yb * lda;
   double vxx = (vxa && vxb) ? A[cxb + xa] : 0.0;
   double vxy = (vxa && vyb) ? A[cyb + xa] : 0.0;
   double vyx = (vya && vxb) ? A[cxb + ya] : 0.0;
@@ -464,11 +467,45 @@ size_t mpj_jacobi64_scratch_bytes_rv(int n, int rv) {
   return scratch_fixed(n) + (size_t)rv * (m / 2) * sizeof(double2);
 }
 
-size_t mpj_jacobi64_scratch_bytes(int n) { return mpj_jacobi64_scratch_bytes_rv(n, RV_MAX); }
+// Room for two halves of RV_MAX rounds each: the rotation kernels fill one
+// half while the batched V update of the other half runs on a side stream.
+size_t mpj_jacobi64_scratch_bytes(int n) { return mpj_jacobi64_scratch_bytes_rv(n, 2 * RV_MAX); }
+
+namespace {
+// Side stream and events for overlapping the V updates with the rotation
+// rounds; released when the solve returns.
+struct SideStream {
+  cudaStream_t sv = nullptr;
+  cudaEvent_t ready = nullptr, done[2] = {nullptr, nullptr};
+  bool ok = false;
+  SideStream() {
+    ok = cudaStreamCreateWithFlags(&sv, cudaStreamNonBlocking) == cudaSuccess &&
+         cudaEventCreateWithFlags(&ready, cudaEventDisableTiming) == cudaSuccess &&
+         cudaEventCreateWithFlags(&done[0], cudaEventDisableTiming) == cudaSuccess &&
+         cudaEventCreateWithFlags(&done[1], cudaEventDisableTiming) == cudaSuccess;
+    if (!ok) (void)cudaGetLastError();
+  }
+  ~SideStream() {
+    if (done[1]) cudaEventDestroy(done[1]);
+    if (done[0]) cudaEventDestroy(done[0]);
+    if (ready) cudaEventDestroy(ready);
+    if (sv) cudaStreamDestroy(sv);
+  }
+};
+
+bool overlap_enabled(int n) {
+  static int env = -1;
+  if (env < 0) {
+    const char* e = getenv("MPJ_JACOBI_OVERLAP");
+    env = (e && e[0] == '0') ? 0 : 1;
+  }
+  return env == 1 && n >= 256;
+}
+}  // namespace
 
 int mpj_jacobi64_run(int n, double* A, int lda, double* V, int ldv, double tol, int ordering, int max_sweeps,
                      int* sweeps_out, double* off_out, double* off_initial, void* scratch, size_t scratch_bytes,
-                     cudaStream_t s, double skip_abs) {
+                     cudaStream_t s, double skip_abs, bool side_stream) {
   const double skip = 0x1p-53;
   const int m = n + (n & 1);
   const int half = m / 2;
@@ -489,9 +526,12 @@ int mpj_jacobi64_run(int n, double* A, int lda, double* V, int ldv, double tol, 
   int* iscal = (int*)(dscal + 2);
   off_b += align256(RED_CTAS * sizeof(double) + 4 * sizeof(double) + 64);
   double2* hist = (double2*)(base + off_b);
+  if (mpj_jacobi64_scratch_bytes_rv(n, 1) > scratch_bytes) return MPJ_EWORKSPACE;
+  // rounds of history that fit; with the side stream two halves of rv rounds
+  const size_t cap = (scratch_bytes - scratch_fixed(n)) / ((size_t)half * sizeof(double2));
+  bool overlap = side_stream && ordering == MPJ_ORDER_ROUND_ROBIN && overlap_enabled(n) && cap >= 16;
   int rv = RV_MAX;
-  while (rv > 1 && mpj_jacobi64_scratch_bytes_rv(n, rv) > scratch_bytes) rv >>= 1;
-  if (mpj_jacobi64_scratch_bytes_rv(n, rv) > scratch_bytes) return MPJ_EWORKSPACE;
+  while (rv > 1 && (size_t)rv * (overlap ? 2 : 1) > cap) rv >>= 1;
 
   double off2 = 0.0;
   MPJ_CUDA_TRY(mpj_sumsq(A, lda, n, true, partial, dscal, nullptr, s));
@@ -507,6 +547,14 @@ int mpj_jacobi64_run(int n, double* A, int lda, double* V, int ldv, double tol, 
     const int fgrid = (int)(((size_t)n * n + 255) / 256 > 4096 ? 4096 : ((size_t)n * n + 255) / 256);
     int k = 0;  // buffer parity of records and scales
     bool need_init = true;
+    std::unique_ptr<SideStream> side;
+    if (overlap) {
+      side.reset(new SideStream());
+      if (!side->ok) overlap = false;
+    }
+    int hb = 0;                          // history half being filled
+    bool used[2] = {false, false};       // a V update may still read that half
+    double2* hcur = hist;
     while (off > tol && n > 1) {
       if (sweeps >= max_sweeps) {
         status = MPJ_NOT_CONVERGED;
@@ -520,8 +568,10 @@ int mpj_jacobi64_run(int n, double* A, int lda, double* V, int ldv, double tol, 
       }
       int pending = 0, since_fold = 0;
       for (int r = 0; r < m - 1; ++r) {
+        if (overlap && pending == 0 && used[hb])  // the V update reading this half must be done
+          MPJ_CUDA_TRY(cudaStreamWaitEvent(s, side->done[hb], 0));
         rr_step64<<<n_atiles, 256, 0, s>>>(A, lda, n, m, r, skip, skip_abs, rec[k], rec[k ^ 1], dsc[k], dsc[k ^ 1],
-                                           hist + (size_t)pending * half);
+                                           hcur + (size_t)pending * half);
         mpj_count_launch();
         k ^= 1;
         ++pending;
@@ -529,7 +579,18 @@ int mpj_jacobi64_run(int n, double* A, int lda, double* V, int ldv, double tol, 
         const bool last = (r == m - 2);
         const bool fold = last || since_fold == RS;
         if (pending == rv || fold) {
-          MPJ_CUDA_TRY(v_apply(V, ldv, n, m, r - pending + 1, pending, hist, s));
+          if (overlap) {
+            MPJ_CUDA_TRY(cudaEventRecord(side->ready, s));
+            MPJ_CUDA_TRY(cudaStreamWaitEvent(side->sv, side->ready, 0));
+            MPJ_CUDA_TRY(v_apply(V, ldv, n, m, r - pending + 1, pending, hcur, side->sv));
+            MPJ_CUDA_TRY(cudaEventRecord(side->done[hb], side->sv));
+            used[hb] = true;
+            if (fold) MPJ_CUDA_TRY(cudaStreamWaitEvent(s, side->done[hb], 0));  // V is rescaled next
+            hb ^= 1;
+            hcur = hist + (size_t)hb * rv * half;
+          } else {
+            MPJ_CUDA_TRY(v_apply(V, ldv, n, m, r - pending + 1, pending, hist, s));
+          }
           pending = 0;
         }
         if (fold) {
@@ -639,7 +700,7 @@ extern "C" int mpj_jacobi64_noalloc(int n, double* A, int lda, double* V, int ld
     tol = (double)n * 0x1p-53 * sqrt(norm2);
   }
   st = mpj_jacobi64_run(n, A, lda, V, ldv, tol, ordering, max_sweeps > 0 ? max_sweeps : 30, sweeps, off_final, nullptr,
-                        w, (size_t)MPJ_NOALLOC_SCRATCH_BYTES, s);
+                        w, (size_t)MPJ_NOALLOC_SCRATCH_BYTES, s, 0.0, /*side_stream=*/false);
   cudaError_t e = cudaStreamSynchronize(s);
   if (e != cudaSuccess && st >= 0) {
     mpj_set_cuda_error(e, "mpj_jacobi64_noalloc sync", __LINE__);

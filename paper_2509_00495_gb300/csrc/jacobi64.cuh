@@ -11,11 +11,14 @@ size_t mpj_jacobi64_scratch_bytes_rv(int n, int rv);
 // FP64 sweeps in place (see mpjacobi.h, mpj_jacobi64).  Synchronizes `s` once
 // per sweep to read off(A).  `scratch_bytes` bounds the V batching (at least
 // mpj_jacobi64_scratch_bytes_rv(n, 1)).  skip_abs > 0 also skips pairs with
-// |a_pq| <= skip_abs (threshold variant).  Returns MPJ_OK / MPJ_NOT_CONVERGED
-// / MPJ_ECUDA / MPJ_EWORKSPACE.
+// |a_pq| <= skip_abs (threshold variant).  With side_stream (and n >= 256,
+// room for two V batches, MPJ_JACOBI_OVERLAP not "0"), the batched V updates
+// run on a private non-blocking stream, overlapping the next rounds; it is
+// joined back into `s` before every scale fold, so V is complete in `s` order
+// on return.  Returns MPJ_OK / MPJ_NOT_CONVERGED / MPJ_ECUDA / MPJ_EWORKSPACE.
 int mpj_jacobi64_run(int n, double* A, int lda, double* V, int ldv, double tol, int ordering, int max_sweeps,
                      int* sweeps_out, double* off_out, double* off_initial, void* scratch, size_t scratch_bytes,
-                     cudaStream_t s, double skip_abs = 0.0);
+                     cudaStream_t s, double skip_abs = 0.0, bool side_stream = true);
 
 // Sum of squares of A's entries (off_only: off-diagonal entries) into *out,
 // through 256 per-CTA partials summed in a fixed order; sets
