@@ -36,6 +36,10 @@ METRIC = "n=4096 FP64-accurate eig solves/s, mixed vs plain FP64 Jacobi, same GB
 UNIT = "solves/s"
 U_D = 2.0 ** -53
 FP64_PEAK_TFLOPS = 1.25  # nominal GB300 FP64 (152 SMs x 2 FP64 FMA/clk x 2 flop x ~2.07 GHz)
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum, one ncu capture each)
+# of one FP64 round at n = 4096: rr_step64 67.9 + 75.0 MB, plus 1/64 of a 64-round
+# v_apply_rounds launch (136.7 + 78.8 MB).  Valid for these kernel versions only.
+TRAFFIC_PER_ROUND_N4096 = 67.92e6 + 75.01e6 + (136.73e6 + 78.85e6) / 64
 WORKLOAD = "geo4096: one symmetric FP64 matrix n=4096, |lam| geometric in [1e-6,1] (condition 1e6), random signs, Haar eigenvectors, seed 0"
 
 
@@ -314,7 +318,8 @@ def main():
         achieved = flops / avg_launch_s / 1e12
         out["roofline"] = {"kernel": "rr_step64+v_apply_rounds (one round)", "bound": "alu", "achieved": achieved,
                            "peak": FP64_PEAK_TFLOPS,
-                           "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+                           "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
+                           "traffic": TRAFFIC_PER_ROUND_N4096 if n == 4096 else None,
                            "peak_source": "nominal FP64 of the recipe table (not in MEASURED_PEAKS.json)",
                            "algorithmic_flops_per_launch": flops, "avg_launch_ms": avg_launch_s * 1e3,
                            "dominant_stage": dominant,
