@@ -45,9 +45,14 @@ constexpr int RS = 512;       // rounds between scale folds
 // Scaled-rotation record of one slot (see the file comment); mx == my == 0
 // means "not rotated".  cm1 = c - 1 of the rotation (for the scale update),
 // dx, dy: true diagonal entries after the rotation.
-struct FRec {
-  double mx, my, cm1, dx, dy;
+// 48 bytes (padded) so that (mx, my) load as one aligned 16-byte access.
+struct __align__(16) FRec {
+  double mx, my, cm1, dx, dy, pad;
 };
+
+// The multipliers of a record (the only fields every block reads).
+MPJ_DEV double2 frec_m(const FRec* __restrict__ p) { return __ldg(reinterpret_cast<const double2*>(p)); }
+MPJ_DEV bool m_rotated(double2 mm) { return (__double_as_longlong(mm.x) | __double_as_longlong(mm.y)) != 0; }
 
 // Bit test instead of an FP64 compare: on this GPU FP64 compares issue on the
 // same slow FP64 pipe as the FMAs.  "Not rotated" records hold +0.0 exactly.
@@ -90,6 +95,7 @@ MPJ_DEV int rr_make_frec(int m, int n, int r, int i, int j, double di, double dj
   rec.cm1 = rot ? cm1 : 0.0;
   rec.dx = (x == p) ? np : nq;
   rec.dy = (x == p) ? nq : np;
+  rec.pad = 0.0;
   return slot;
 }
 
@@ -122,127 +128,164 @@ __device__ __forceinline__ void tri_tile(int t, int& ti, int& tj) {
   tj = t - r * (r + 1) / 2;
 }
 
+// Inputs of one next-round record, queued in shared memory by the thread whose
+// 2 x 2 block holds the pair's coupling after this round.
+struct HostIn {
+  int i, j;            // pair (i, j) of the next round, i from this block's rows
+  double di, dj, aij;  // true diagonals after this round, scaled coupling
+  double cmi, cmj;     // c - 1 of this round's rotations of i and j (scale update)
+};
+// Queue length per CTA.  Entries come only from the row side of a block: the
+// next-round partner of x_a (and of y_a) lies in exactly one slot, so each of
+// a CTA's 16 row slots queues at most 2 entries: at most 32 per CTA.
+constexpr int HMAX = 2 * TS;
+
+MPJ_DEV void build_next_rec(const HostIn& h, int m, int n, int rn, double skip, double skip_abs,
+                            const double2* __restrict__ dcur, FRec* __restrict__ rec_next) {
+  double si = dd_scale(dcur[h.i], h.cmi).x;
+  double sj = dd_scale(dcur[h.j], h.cmj).x;
+  FRec nr;
+  int sl = rr_make_frec(m, n, rn, h.i, h.j, h.di, h.dj, h.aij * si * sj, si, sj, skip, nr, skip_abs);
+  rec_next[sl] = nr;
+}
+
 // One round on A (scaled form) + next round's records + this round's V multipliers.
-__global__ void __launch_bounds__(256) rr_step64(double* __restrict__ A, int lda, int n, int m, int r, double skip,
+// Each thread owns one 2 x 2 block (rows x_a, y_a; columns x_b, y_b) of the lower
+// slot triangle.  The n/2 records of the next round need a square root and
+// divisions each; their inputs are queued in shared memory and built by the
+// CTA's first warp with all lanes busy, instead of by one lane of many warps
+// (FP64 instructions issue at 1/64 of the FP32 rate on this GPU).
+__global__ void __launch_bounds__(256, 5) rr_step64(double* __restrict__ A, int lda, int n, int m, int r, double skip,
                                                  double skip_abs, const FRec* __restrict__ rec,
                                                  FRec* __restrict__ rec_next,
                                                  const double2* __restrict__ dcur, double2* __restrict__ dnext,
                                                  double2* __restrict__ hist_row) {
+  __shared__ HostIn hq[HMAX];
+  __shared__ int hcount;
   const int half = m / 2;
   const int rn = (r + 1 == m - 1) ? 0 : r + 1;  // next round (wraps into the next sweep)
   int ti, tj;
   tri_tile(blockIdx.x, ti, tj);
   const int a = ti * TS + (threadIdx.x % TS);
   const int b = tj * TS + (threadIdx.x / TS);
-  if (a >= half || b >= half || a < b) return;
-  int xa, ya;
-  rr_slot(m, r, a, xa, ya);
-  const FRec ra = rec[a];
-  const bool rota = frec_rotated(ra);
-  const bool vxa = xa < n, vya = ya < n;
-  if (a == b) {
-    const double cm1 = rota ? frec_cm1(ra) : 0.0;
-    double2 sx = vxa ? dd_scale(dcur[xa], cm1) : make_double2(1.0, 0.0);
-    double2 sy = vya ? dd_scale(dcur[ya], cm1) : make_double2(1.0, 0.0);
-    if (vxa) dnext[xa] = sx;
-    if (vya) dnext[ya] = sy;
-    hist_row[a] = make_double2(ra.mx, ra.my);
-    double axy_s;  // scaled coupling after the round
-    if (rota) {
-      A[(size_t)xa * lda + xa] = ra.dx;
-      A[(size_t)ya * lda + ya] = ra.dy;
-      A[(size_t)ya * lda + xa] = 0.0;
-      A[(size_t)xa * lda + ya] = 0.0;
-      axy_s = 0.0;
+  if (threadIdx.x == 0) hcount = 0;
+  __syncthreads();
+  if (a < half && b < half && a >= b) {
+    int xa, ya;
+    rr_slot(m, r, a, xa, ya);
+    const FRec* pa = rec + a;
+    const double2 ma = frec_m(pa);
+    const bool rota = m_rotated(ma);
+    const bool vxa = xa < n, vya = ya < n;
+    if (a == b) {
+      const FRec ra = *pa;
+      const double cm1 = rota ? frec_cm1(ra) : 0.0;
+      double2 sx = vxa ? dd_scale(dcur[xa], cm1) : make_double2(1.0, 0.0);
+      double2 sy = vya ? dd_scale(dcur[ya], cm1) : make_double2(1.0, 0.0);
+      if (vxa) dnext[xa] = sx;
+      if (vya) dnext[ya] = sy;
+      hist_row[a] = make_double2(ra.mx, ra.my);
+      double axy_s;  // scaled coupling after the round
+      if (rota) {
+        A[(size_t)xa * lda + xa] = ra.dx;
+        A[(size_t)ya * lda + ya] = ra.dy;
+        A[(size_t)ya * lda + xa] = 0.0;
+        A[(size_t)xa * lda + ya] = 0.0;
+        axy_s = 0.0;
+      } else {
+        axy_s = (vxa && vya) ? A[(size_t)ya * lda + xa] : 0.0;
+      }
+      // the unpaired index of round rn when n is odd (slot 0 pairs it with the dummy)
+      if ((n & 1) && (xa == rn || ya == rn)) {
+        FRec z;
+        z.mx = 0.0;
+        z.my = 0.0;
+        z.cm1 = 0.0;
+        z.dx = (xa == rn) ? ra.dx : ra.dy;
+        z.dy = 0.0;
+        z.pad = 0.0;
+        rec_next[0] = z;
+      }
+      // m == 2: the same pair again in the next sweep
+      if (vxa && vya && rr_partner(m, rn, xa) == ya) {
+        FRec nr;
+        int sl = rr_make_frec(m, n, rn, xa, ya, ra.dx, ra.dy, axy_s * sx.x * sy.x, sx.x, sy.x, skip, nr, skip_abs);
+        rec_next[sl] = nr;
+      }
     } else {
-      axy_s = (vxa && vya) ? A[(size_t)ya * lda + xa] : 0.0;
-    }
-    // the unpaired index of round rn when n is odd (slot 0 pairs it with the dummy)
-    if ((n & 1) && (xa == rn || ya == rn)) {
-      FRec z;
-      z.mx = 0.0;
-      z.my = 0.0;
-      z.cm1 = 0.0;
-      z.dx = (xa == rn) ? ra.dx : ra.dy;
-      z.dy = 0.0;
-      rec_next[0] = z;
-    }
-    // m == 2: the same pair again in the next sweep
-    if (vxa && vya && rr_partner(m, rn, xa) == ya) {
-      FRec nr;
-      int sl = rr_make_frec(m, n, rn, xa, ya, ra.dx, ra.dy, axy_s * sx.x * sy.x, sx.x, sy.x, skip, nr, skip_abs);
-      rec_next[sl] = nr;
-    }
-    return;
-  }
-  int xb, yb;
-  rr_slot(m, r, b, xb, yb);
-  const bool vxb = xb < n, vyb = yb < n;
-  size_t cxb = (size_t)xb * lda, cyb = (size_t)yb * lda;
-  const FRec rb = rec[b];
-  const bool rotb = frec_rotated(rb);
-  // next-round pairs hosted by this block: (x_a or y_a) with (x_b or y_b)
-  int jx = vxa ? rr_partner(m, rn, xa) : -1;
-  int jy = vya ? rr_partner(m, rn, ya) : -1;
-  bool nx = jx >= 0 && jx < n && (jx == xb || jx == yb);
-  bool ny = jy >= 0 && jy < n && (jy == xb || jy == yb);
-  if (!rota && !rotb && !nx && !ny) return;
-  double vxx = (vxa && vxb) ? A[cxb + xa] : 0.0;
-  double vxy = (vxa && vyb) ? A[cyb + xa] : 0.0;
-  double vyx = (vya && vxb) ? A[cxb + ya] : 0.0;
-  double vyy = (vya && vyb) ? A[cyb + ya] : 0.0;
-  if (rota) {  // rows x_a, y_a
-    double t0 = fma(-ra.mx, vyx, vxx), t1 = fma(ra.my, vxx, vyx);
-    double t2 = fma(-ra.mx, vyy, vxy), t3 = fma(ra.my, vxy, vyy);
-    vxx = t0;
-    vyx = t1;
-    vxy = t2;
-    vyy = t3;
-  }
-  if (rotb) {  // columns x_b, y_b
-    double t0 = fma(-rb.mx, vxy, vxx), t1 = fma(rb.my, vxx, vxy);
-    double t2 = fma(-rb.mx, vyy, vyx), t3 = fma(rb.my, vyx, vyy);
-    vxx = t0;
-    vxy = t1;
-    vyx = t2;
-    vyy = t3;
-  }
-  if (rota || rotb) {
-    if (vxa && vxb) {
-      A[cxb + xa] = vxx;
-      A[(size_t)xa * lda + xb] = vxx;
-    }
-    if (vxa && vyb) {
-      A[cyb + xa] = vxy;
-      A[(size_t)xa * lda + yb] = vxy;
-    }
-    if (vya && vxb) {
-      A[cxb + ya] = vyx;
-      A[(size_t)ya * lda + xb] = vyx;
-    }
-    if (vya && vyb) {
-      A[cyb + ya] = vyy;
-      A[(size_t)ya * lda + yb] = vyy;
-    }
-  }
-  if (nx || ny) {
-    const double cma = rota ? frec_cm1(ra) : 0.0, cmb = rotb ? frec_cm1(rb) : 0.0;
+      int xb, yb;
+      rr_slot(m, r, b, xb, yb);
+      const FRec* pb = rec + b;
+      const double2 mb = frec_m(pb);
+      const bool rotb = m_rotated(mb);
+      const bool vxb = xb < n, vyb = yb < n;
+      // next-round pairs hosted by this block: (x_a or y_a) with (x_b or y_b)
+      int jx = vxa ? rr_partner(m, rn, xa) : -1;
+      int jy = vya ? rr_partner(m, rn, ya) : -1;
+      bool nx = jx >= 0 && jx < n && (jx == xb || jx == yb);
+      bool ny = jy >= 0 && jy < n && (jy == xb || jy == yb);
+      if (rota || rotb || nx || ny) {
+        size_t cxb = (size_t)xb * lda, cyb = (size_t)yb * lda;
+        double vxx = (vxa && vxb) ? A[cxb + xa] : 0.0;
+        double vxy = (vxa && vyb) ? A[cyb + xa] : 0.0;
+        double vyx = (vya && vxb) ? A[cxb + ya] : 0.0;
+        double vyy = (vya && vyb) ? A[cyb + ya] : 0.0;
+        if (rota) {  // rows x_a, y_a
+          double t0 = fma(-ma.x, vyx, vxx), t1 = fma(ma.y, vxx, vyx);
+          double t2 = fma(-ma.x, vyy, vxy), t3 = fma(ma.y, vxy, vyy);
+          vxx = t0;
+          vyx = t1;
+          vxy = t2;
+          vyy = t3;
+        }
+        if (rotb) {  // columns x_b, y_b
+          double t0 = fma(-mb.x, vxy, vxx), t1 = fma(mb.y, vxx, vxy);
+          double t2 = fma(-mb.x, vyy, vyx), t3 = fma(mb.y, vyx, vyy);
+          vxx = t0;
+          vxy = t1;
+          vyx = t2;
+          vyy = t3;
+        }
+        if (rota || rotb) {
+          if (vxa && vxb) {
+            A[cxb + xa] = vxx;
+            A[(size_t)xa * lda + xb] = vxx;
+          }
+          if (vxa && vyb) {
+            A[cyb + xa] = vxy;
+            A[(size_t)xa * lda + yb] = vxy;
+          }
+          if (vya && vxb) {
+            A[cxb + ya] = vyx;
+            A[(size_t)ya * lda + xb] = vyx;
+          }
+          if (vya && vyb) {
+            A[cyb + ya] = vyy;
+            A[(size_t)ya * lda + yb] = vyy;
+          }
+        }
 #pragma unroll
-    for (int side = 0; side < 2; ++side) {
-      if (side == 0 && !nx) continue;
-      if (side == 1 && !ny) continue;
-      int i = side ? ya : xa;
-      int j = side ? jy : jx;
-      double di = side ? ra.dy : ra.dx;
-      double dj = (j == xb) ? rb.dx : rb.dy;
-      double aij_s = side ? ((j == xb) ? vyx : vyy) : ((j == xb) ? vxx : vxy);
-      double si = dd_scale(dcur[i], cma).x;
-      double sj = dd_scale(dcur[j], cmb).x;
-      FRec nr;
-      int sl = rr_make_frec(m, n, rn, i, j, di, dj, aij_s * si * sj, si, sj, skip, nr, skip_abs);
-      rec_next[sl] = nr;
+        for (int side = 0; side < 2; ++side) {
+          if (side == 0 && !nx) continue;
+          if (side == 1 && !ny) continue;
+          HostIn h;
+          h.i = side ? ya : xa;
+          h.j = side ? jy : jx;
+          h.di = side ? pa->dy : pa->dx;
+          h.dj = (h.j == xb) ? pb->dx : pb->dy;
+          h.aij = side ? ((h.j == xb) ? vyx : vyy) : ((h.j == xb) ? vxx : vxy);
+          h.cmi = rota ? pa->cm1 : 0.0;
+          h.cmj = rotb ? pb->cm1 : 0.0;
+          int slot = atomicAdd(&hcount, 1);
+          if (slot < HMAX) hq[slot] = h;  // always true (see HMAX)
+        }
+      }
     }
   }
+  __syncthreads();
+  const int cnt = hcount < HMAX ? hcount : HMAX;
+  if (threadIdx.x < 32)
+    for (int k = threadIdx.x; k < cnt; k += 32) build_next_rec(hq[k], m, n, rn, skip, skip_abs, dcur, rec_next);
 }
 
 // Apply rounds r0 .. r0+nr-1 of the history to a chunk of ROWS consecutive
