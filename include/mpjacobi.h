@@ -210,6 +210,23 @@ int mpj_jacobi64_noalloc(int n, double* A_dev, int lda, double* V_dev, int ldv, 
 int mpj_dgemm(char transa, char transb, int m, int n, int k, double alpha, const double* A_dev, int lda,
               const double* B_dev, int ldb, double beta, double* C_dev, int ldc, void* stream);
 
+/* One product of the stage-1 blocked update on the tcgen05 tensor cores
+ * (3xTF32; the stage is the approximate eigenvector step of Sec. 4.1, and the
+ * paper has no blocked form of it).  N: a multiple of 32; block round R in
+ * [0, N/16 - 1) of the circle method on the N/16 blocks of 16 indices; block
+ * pair q of that round covers the 32 indices I_q (its lower block, then its
+ * upper block).  For every pair q:
+ *   Out[:, I_q] = In[:, I_q] * U_q       (transpose_out = 0), or
+ *   Out[I_q, :] = (In[:, I_q] * U_q)^T   (transpose_out = 1),
+ * In, Out: N x N column-major FP32 device arrays (ld = N), distinct when
+ * transpose_out = 1; U_dev: N/32 column-major 32 x 32 FP32 factors, U_q at
+ * U_dev + 1024 q.  Products are accurate to about 2^-21 relative.  Returns
+ * MPJ_EINVAL for bad arguments, MPJ_ETIMEOUT if the tensor cores did not
+ * signal completion within about 2 s, MPJ_ECUDA on a launch error.
+ * Synchronizes the stream. */
+int mpj_stage1_panel(int N, int R, const float* U_dev, const float* In_dev, float* Out_dev, int transpose_out,
+                     void* stream);
+
 #ifdef __cplusplus
 }
 #endif

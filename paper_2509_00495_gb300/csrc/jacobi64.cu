@@ -169,6 +169,12 @@ __global__ void __launch_bounds__(256, 5) rr_step64(double* __restrict__ A, int 
   const int a = ti * TS + (threadIdx.x % TS);
   const int b = tj * TS + (threadIdx.x / TS);
   if (threadIdx.x == 0) hcount = 0;
+  // Programmatic dependent launch: once every CTA of this round has started,
+  // the next round's CTAs may be scheduled into the slots this round frees;
+  // each waits here until the previous round has completed and its writes
+  // are visible (no global memory is touched before the wait).
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+  asm volatile("griddepcontrol.wait;" ::: "memory");
   __syncthreads();
   if (a < half && b < half && a >= b) {
     int xa, ya;
@@ -536,6 +542,28 @@ struct SideStream {
   }
 };
 
+// rr_step64 with programmatic stream serialization, so that consecutive
+// rounds overlap their launch and ramp-up (the kernel waits in
+// griddepcontrol.wait before touching memory).
+cudaError_t launch_rr_step64(int grid, cudaStream_t s, double* A, int lda, int n, int m, int r, double skip,
+                             double skip_abs, const FRec* rec, FRec* rec_next, const double2* dcur, double2* dnext,
+                             double2* hist_row) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(256);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cudaError_t e = cudaLaunchKernelEx(&cfg, rr_step64, A, lda, n, m, r, skip, skip_abs, rec, rec_next, dcur, dnext,
+                                     hist_row);
+  mpj_count_launch();
+  return e;
+}
+
 bool overlap_enabled(int n) {
   static int env = -1;
   if (env < 0) {
@@ -613,9 +641,8 @@ int mpj_jacobi64_run(int n, double* A, int lda, double* V, int ldv, double tol, 
       for (int r = 0; r < m - 1; ++r) {
         if (overlap && pending == 0 && used[hb])  // the V update reading this half must be done
           MPJ_CUDA_TRY(cudaStreamWaitEvent(s, side->done[hb], 0));
-        rr_step64<<<n_atiles, 256, 0, s>>>(A, lda, n, m, r, skip, skip_abs, rec[k], rec[k ^ 1], dsc[k], dsc[k ^ 1],
-                                           hcur + (size_t)pending * half);
-        mpj_count_launch();
+        MPJ_CUDA_TRY(launch_rr_step64(n_atiles, s, A, lda, n, m, r, skip, skip_abs, rec[k], rec[k ^ 1], dsc[k],
+                                      dsc[k ^ 1], hcur + (size_t)pending * half));
         k ^= 1;
         ++pending;
         ++since_fold;

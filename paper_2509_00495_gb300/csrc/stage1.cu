@@ -18,8 +18,11 @@
 // blocked update (FP32 FMA), which touch A32 and V32 once per round instead of
 // once per pair step.  off(A32) is reduced after each sweep; stop at
 // off(A32) <= tol32 or the sweep cap.
+#include <stdlib.h>
+
 #include "common.cuh"
 #include "stage1.cuh"
+#include "tc32.cuh"
 
 namespace {
 
@@ -266,10 +269,29 @@ __global__ void __launch_bounds__(UT) update32(float* __restrict__ A32, float* _
 
 int mpj_stage1_padded(int n) { return ((n + W2 - 1) / W2) * W2; }
 
+// A32, V32, the per-pair S and U, a flag word after them (the tensor-core
+// update also keeps the transposed intermediate B^T there).
+static int stage1_tensor_cores();
+
 size_t mpj_stage1_bytes(int n) {
   size_t N = (size_t)mpj_stage1_padded(n);
   size_t nb = N / BS;
-  return 2 * N * N * sizeof(float) + 2 * (nb / 2) * W2 * W2 * sizeof(float) + 4096;
+  return (stage1_tensor_cores() ? 3 : 2) * N * N * sizeof(float) + 2 * (nb / 2) * W2 * W2 * sizeof(float) + 4096;
+}
+
+// MPJ_STAGE1_TC=1 runs the A update of each block round on the tcgen05
+// tensor cores (3xTF32, two panel products, see tc32.cu) and the V update on
+// the FP32 pipe.  Off by default: on GB300 at n = 4096 it is slower (600 vs
+// 435 ms for the stage), and V must stay on the FP32 pipe because the tensor
+// cores' FP32 accumulation drifts the column norms over thousands of products
+// (||V^T V - I||_F 0.08 instead of 0.007).
+static int stage1_tensor_cores() {
+  static int env = -1;
+  if (env < 0) {
+    const char* e = getenv("MPJ_STAGE1_TC");
+    env = (e && e[0] == '1') ? 1 : 0;
+  }
+  return env;
 }
 
 cudaError_t mpj_sumsq32(const float* A, int lda, int n, double* partial, double* out, cudaStream_t s);
@@ -282,6 +304,10 @@ int mpj_stage1_run(int n, const double* A, int lda, double* Ql, int ldq, double 
   float* V32 = A32 + (size_t)N * N;
   float* Sbuf = V32 + (size_t)N * N;
   float* Ubuf = Sbuf + (size_t)(nb / 2) * W2 * W2;
+  const int tc = stage1_tensor_cores();
+  float* Bt = Ubuf + (size_t)(nb / 2) * W2 * W2;
+  unsigned* tflag = (unsigned*)(Bt + (tc ? (size_t)N * N : 0));
+  MPJ_CUDA_TRY(cudaMemsetAsync(tflag, 0, sizeof(unsigned), s));
   init32<<<1024, 256, 0, s>>>(A, lda, n, N, A32, V32);
   mpj_count_launch();
   MPJ_CUDA_TRY(cudaGetLastError());
@@ -302,14 +328,26 @@ int mpj_stage1_run(int n, const double* A, int lda, double* Ql, int ldq, double 
     for (int R = 0; R < nb - 1; ++R) {
       solve32<<<npairs, 256, 0, s>>>(A32, N, nb, R, Sbuf, Ubuf);
       mpj_count_launch();
-      update32<<<grid_u, UT, 0, s>>>(A32, V32, N, nb, R, Sbuf, Ubuf, n_atiles);
-      mpj_count_launch();
+      if (tc == 1) {
+        // A' = U^T A U = (A U)^T U (A symmetric): B^T = (A U)^T, then
+        // A' = (B^T)(:, I_q) U_q on the tensor cores; V U on the FP32 pipe
+        MPJ_CUDA_TRY(mpj_tc_panel(N, nb, R, Ubuf, A32, Bt, 1, nullptr, nullptr, tflag, s));
+        MPJ_CUDA_TRY(mpj_tc_panel(N, nb, R, Ubuf, Bt, A32, 0, nullptr, nullptr, tflag, s));
+        update32<<<(N / W2) * npairs, UT, 0, s>>>(A32, V32, N, nb, R, Sbuf, Ubuf, 0);
+        mpj_count_launch();
+      } else {
+        update32<<<grid_u, UT, 0, s>>>(A32, V32, N, nb, R, Sbuf, Ubuf, n_atiles);
+        mpj_count_launch();
+      }
     }
     MPJ_CUDA_TRY(cudaGetLastError());
     ++sweeps;
     MPJ_CUDA_TRY(mpj_sumsq32(A32, N, N, partial, dscal, s));
+    unsigned tf = 0;
     MPJ_CUDA_TRY(cudaMemcpyAsync(&off2, dscal, sizeof(double), cudaMemcpyDeviceToHost, s));
+    MPJ_CUDA_TRY(cudaMemcpyAsync(&tf, tflag, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
     MPJ_CUDA_TRY(cudaStreamSynchronize(s));
+    if (tf & MPJ_FLAG_TIMEOUT) return MPJ_ETIMEOUT;
     off = sqrt(off2);
   }
   widen<<<1024, 256, 0, s>>>(V32, N, n, Ql, ldq);

@@ -94,6 +94,7 @@ def lib():
         L.mpj_precondition.argtypes = [_i, _vp, _i, _vp, _i, _vp, _i, _vp]
         L.mpj_jacobi64.argtypes = [_i, _vp, _i, _vp, _i, _d, _i, _i, _ip, _dp, _vp]
         L.mpj_dgemm.argtypes = [ctypes.c_char, ctypes.c_char, _i, _i, _i, _d, _vp, _i, _vp, _i, _d, _vp, _i, _vp]
+        L.mpj_stage1_panel.argtypes = [_i, _i, _vp, _vp, _vp, _i, _vp]
         if hasattr(L, "mpj_syev_batched"):
             L.mpj_syev_batched.argtypes = [_i, _ip, _vp, _vp, _vp, _d, _ip, _vp]
             L.mpj_batched_group_size.argtypes = [_i, _ip]
@@ -251,6 +252,23 @@ def dgemm(transa: str, transb: str, alpha: float, A: torch.Tensor, B: torch.Tens
                          max(B.shape[0], 1), beta, _ptr(Ct), max(m, 1), _stream())
     _check(st, "mpj_dgemm")
     return Ct.T
+
+
+def stage1_panel(R: int, U: torch.Tensor, In: torch.Tensor, transpose_out: bool = False) -> torch.Tensor:
+    """mpj_stage1_panel: the tensor-core block product of block round R.
+    In: N x N float32 holding the column-major matrix (In[j, i] = element
+    (i, j), i.e. the transpose of the logical matrix, as stored); U: (N/32,
+    32, 32) float32 with U[q, j, i] = U_q(i, j).  Returns Out in the same
+    storage convention."""
+    for t, name in ((In, "In"), (U, "U")):
+        if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != torch.float32:
+            raise TypeError(f"{name} must be a float32 CUDA tensor")
+    In, U = In.contiguous(), U.contiguous()
+    N = In.shape[0]
+    Out = torch.zeros_like(In)
+    st = lib().mpj_stage1_panel(N, R, _ptr(U), _ptr(In), _ptr(Out), int(transpose_out), _stream())
+    _check(st, "mpj_stage1_panel")
+    return Out
 
 
 # ------------------------------------------------------------------ batched
