@@ -71,7 +71,9 @@ __global__ void __launch_bounds__(256) solve32(const float* __restrict__ A32, in
   int I, J;
   block_pair(nb, R, slot, I, J);
   const int tid = threadIdx.x;
-  for (int e = tid; e < W2 * W2; e += 256) {
+  #pragma unroll
+  for (int it = 0; it < W2 * W2 / 256; ++it) {
+    const int e = tid + it * 256;
     int li = e % W2, lj = e / W2;
     S[li][lj] = A32[(size_t)gidx(I, J, lj) * N + gidx(I, J, li)];
     U[li][lj] = (li == lj) ? 1.0f : 0.0f;
@@ -139,7 +141,9 @@ __global__ void __launch_bounds__(256) solve32(const float* __restrict__ A32, in
   }
   float* So = Sbuf + (size_t)slot * W2 * W2;
   float* Uo = Ubuf + (size_t)slot * W2 * W2;
-  for (int e = tid; e < W2 * W2; e += 256) {
+  #pragma unroll
+  for (int it = 0; it < W2 * W2 / 256; ++it) {
+    const int e = tid + it * 256;
     int li = e % W2, lj = e / W2;
     So[e] = S[li][lj];
     Uo[e] = U[li][lj];
@@ -181,7 +185,8 @@ MPJ_DEV void tile_mm(const float (*Lt)[LD4], const float (*R)[LD4], float acc[4]
   }
 }
 
-__global__ void __launch_bounds__(UT) update32(float* __restrict__ A32, float* __restrict__ V32, int N, int nb, int R,
+// all tile loads unrolled (48 in flight per thread): 127 registers, 8 CTAs/SM
+__global__ void __launch_bounds__(UT, 8) update32(float* __restrict__ A32, float* __restrict__ V32, int N, int nb, int R,
                                                const float* __restrict__ Sbuf, const float* __restrict__ Ubuf,
                                                int n_atiles) {
   // three 32 x 32 buffers (13.5 KB): the tile (later X^T), U_P, U_Q
@@ -201,7 +206,9 @@ __global__ void __launch_bounds__(UT) update32(float* __restrict__ A32, float* _
     block_pair(nb, R, Q, IQ, JQ);
     if (P == Q) {
       const float* Sp = Sbuf + (size_t)P * W2 * W2;
-      for (int e = tid; e < W2 * W2; e += UT) {
+      #pragma unroll
+      for (int it = 0; it < W2 * W2 / UT; ++it) {
+        const int e = tid + it * UT;
         int li = e % W2, lj = e / W2;
         A32[(size_t)gidx(IP, JP, lj) * N + gidx(IP, JP, li)] = Sp[e];
       }
@@ -209,7 +216,9 @@ __global__ void __launch_bounds__(UT) update32(float* __restrict__ A32, float* _
     }
     const float* Up = Ubuf + (size_t)P * W2 * W2;  // column-major 32 x 32: Up[li + 32 lj] = U_P(li, lj)
     const float* Uq = Ubuf + (size_t)Q * W2 * W2;
-    for (int e = tid; e < W2 * W2; e += UT) {
+    #pragma unroll
+    for (int it = 0; it < W2 * W2 / UT; ++it) {
+      const int e = tid + it * UT;
       int li = e % W2, lj = e / W2;
       T[li][lj] = A32[(size_t)gidx(IQ, JQ, lj) * N + gidx(IP, JP, li)];
       UP[li][lj] = Up[e];
@@ -232,7 +241,9 @@ __global__ void __launch_bounds__(UT) update32(float* __restrict__ A32, float* _
 #pragma unroll
       for (int b = 0; b < 4; ++b) T[i4 + a][j4 + b] = acc[a][b];
     __syncthreads();
-    for (int e = tid; e < W2 * W2; e += UT) {
+    #pragma unroll
+    for (int it = 0; it < W2 * W2 / UT; ++it) {
+      const int e = tid + it * UT;
       int li = e % W2, lj = e / W2;
       A32[(size_t)gidx(IQ, JQ, lj) * N + gidx(IP, JP, li)] = T[li][lj];
       // mirror: entry (cols(Q)[li], rows(P)[lj]) = T[lj][li]
@@ -247,7 +258,9 @@ __global__ void __launch_bounds__(UT) update32(float* __restrict__ A32, float* _
   int IQ, JQ;
   block_pair(nb, R, Q, IQ, JQ);
   const float* Uq = Ubuf + (size_t)Q * W2 * W2;
-  for (int e = tid; e < W2 * W2; e += UT) {
+  #pragma unroll
+  for (int it = 0; it < W2 * W2 / UT; ++it) {
+    const int e = tid + it * UT;
     int li = e % W2, lj = e / W2;
     UP[lj][li] = V32[(size_t)gidx(IQ, JQ, lj) * N + rc * W2 + li];  // UP holds the chunk transposed
     UQ[li][lj] = Uq[e];
@@ -259,7 +272,9 @@ __global__ void __launch_bounds__(UT) update32(float* __restrict__ A32, float* _
 #pragma unroll
     for (int b = 0; b < 4; ++b) T[i4 + a][j4 + b] = acc[a][b];
   __syncthreads();
-  for (int e = tid; e < W2 * W2; e += UT) {
+  #pragma unroll
+  for (int it = 0; it < W2 * W2 / UT; ++it) {
+    const int e = tid + it * UT;
     int li = e % W2, lj = e / W2;
     V32[(size_t)gidx(IQ, JQ, lj) * N + rc * W2 + li] = T[li][lj];
   }
