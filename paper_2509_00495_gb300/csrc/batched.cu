@@ -10,7 +10,8 @@
 //      off(A32) <= n 2^-24 ||A||_F (cap max32), Q_l = double(V32);
 //   2. Newton-Schulz X <- 1.5 X - 0.5 X (X^T X), ns_steps times (FP64 DMMA);
 //   3. A_cond = X^T (A X) (FP64 DMMA, lower tiles mirrored);
-//   4. FP64 round-robin Jacobi on A_cond from V = I until off <= tol (cap max64);
+//   4. FP64 round-robin Jacobi on A_cond from V = I until off <= tol (cap max64),
+//      also skipping pairs with |a_pq| <= tol/n (threshold Jacobi);
 //   5. W = sorted diag, Q = X V (columns permuted), written to the caller.
 // Groups synchronize with named barriers (bar.sync id, G), so small matrices
 // share an SM.  The round-robin ordering, the rotation records and the
@@ -92,6 +93,7 @@ MPJ_DEV void grp_gemm(const Grp& g, int n, double alpha, const double* A, const 
     if (sym && ti < tj) continue;
     int m0 = ti * 16, n0 = tj * 16;
     double acc[2][2][2] = {{{0, 0}, {0, 0}}, {{0, 0}, {0, 0}}};
+#pragma unroll 8
     for (int k = 0; k < n; k += 4) {
       int kk = k + tig;
       double af[2], bf[2];
@@ -128,9 +130,10 @@ MPJ_DEV void grp_gemm(const Grp& g, int n, double alpha, const double* A, const 
 }
 
 // One round-robin Jacobi sweep at group level on a symmetric n x n matrix A
-// (ld n) with vectors V (ld n).  rec: m/2 records in shared memory.
+// (ld n) with vectors V (ld n).  rec: m/2 records in shared memory.  Pairs
+// with |a_pq| <= skip sqrt|a_pp a_qq| or |a_pq| <= skip_abs are skipped.
 template <typename T>
-MPJ_DEV void grp_rr_sweep(const Grp& g, int n, T* A, T* V, RotRec<T>* rec, T skip) {
+MPJ_DEV void grp_rr_sweep(const Grp& g, int n, T* A, T* V, RotRec<T>* rec, T skip, T skip_abs) {
   const int m = n + (n & 1), h = m / 2;
   for (int r = 0; r < m - 1; ++r) {
     for (int i = g.t; i < h; i += g.n) {
@@ -140,10 +143,11 @@ MPJ_DEV void grp_rr_sweep(const Grp& g, int n, T* A, T* V, RotRec<T>* rec, T ski
       T dy = y < n ? A[(size_t)y * n + y] : T(0);
       T axy = (x < n && y < n) ? A[(size_t)y * n + x] : T(0);
       RotRec<T> rr;
-      rr_make_rec<T>(m, n, r, x, y, dx, dy, axy, skip, rr);
+      rr_make_rec<T>(m, n, r, x, y, dx, dy, axy, skip, rr, skip_abs);
       rec[i] = rr;
     }
     gsync(g);
+#pragma unroll 4
     for (int e = g.t; e < h * h; e += g.n) {
       int a = e % h, b = e / h;
       if (a < b) continue;
@@ -182,6 +186,7 @@ MPJ_DEV void grp_rr_sweep(const Grp& g, int n, T* A, T* V, RotRec<T>* rec, T ski
       if (vya && vxb) A[(size_t)xb * n + ya] = A[(size_t)ya * n + xb] = vyx;
       if (vya && vyb) A[(size_t)yb * n + ya] = A[(size_t)ya * n + yb] = vyy;
     }
+#pragma unroll 4
     for (int e = g.t; e < n * h; e += g.n) {
       int row = e % n, b = e / n;
       RotRec<T> rb = rec[b];
@@ -272,7 +277,7 @@ __global__ void __launch_bounds__(NTH, 1)
     for (int sw = 0; sw < max32; ++sw) {
       double off2 = grp_off2<float>(g, n, B.A32, red[g.id]);
       if (!(off2 > tol32 * tol32)) break;
-      grp_rr_sweep<float>(g, n, B.A32, B.V32, rec32[g.id], 0x1p-24f);
+      grp_rr_sweep<float>(g, n, B.A32, B.V32, rec32[g.id], 0x1p-24f, 0.0f);
     }
     for (int e = tid; e < n * n; e += G) B.X[e] = (double)B.V32[e];
     gsync(g);
@@ -301,7 +306,7 @@ __global__ void __launch_bounds__(NTH, 1)
         if (tid == 0) atomicOr(flags, MPJ_FLAG_TIMEOUT);  // cap reached: reported as not converged
         break;
       }
-      grp_rr_sweep<double>(g, n, B.M, V, rec64[g.id], 0x1p-53);
+      grp_rr_sweep<double>(g, n, B.M, V, rec64[g.id], 0x1p-53, tol / n);  // threshold variant
       ++sweeps;
     }
     // 5. sort, permute, Q = X Vp

@@ -119,13 +119,14 @@ MPJ_DEV void rr_slot_of(int m, int r, int idx, int& slot, int& is_y) {
 // diagonal entries di = a_ii, dj = a_jj and the coupling aij.  Returns the
 // slot index.  n is the true size (indices >= n are dummies).
 template <typename T>
-MPJ_DEV int rr_make_rec(int m, int n, int r, int i, int j, T di, T dj, T aij, T skip, RotRec<T>& rec) {
+MPJ_DEV int rr_make_rec(int m, int n, int r, int i, int j, T di, T dj, T aij, T skip, RotRec<T>& rec,
+                        T skip_abs = T(0)) {
   int slot, iy;
   rr_slot_of(m, r, i, slot, iy);
   int p = i < j ? i : j, q = i < j ? j : i;
   T app = (p == i) ? di : dj, aqq = (p == i) ? dj : di;
   T t, cm1, s;
-  bool rot = (q < n) && jacobi_pair<T>(app, aqq, aij, skip, t, cm1, s);
+  bool rot = (q < n) && jacobi_pair<T>(app, aqq, aij, skip, t, cm1, s, skip_abs);
   T np = app, nq = aqq;
   if (rot) {
     np = app - t * aij;

@@ -323,7 +323,8 @@ def test_batched_vs_oracle_sample():
     for a, W, Q, sw in zip(mats, Ws, Qs, sweeps):
         n = a.shape[0]
         W, Q = host(W), host(Q)
-        Wr, Qr, info = oracle.syev_mixed(a, ordering32=oracle.ROUND_ROBIN, ordering64=oracle.ROUND_ROBIN)
+        Wr, Qr, info = oracle.syev_mixed(a, ordering32=oracle.ROUND_ROBIN, ordering64=oracle.ROUND_ROBIN,
+                                         threshold=True)
         nA = max(np.linalg.norm(a, 2), 1e-300)
         assert np.abs(W - Wr).max() <= 1e-12 * nA
         be, orF = triple(a, W, Q)
