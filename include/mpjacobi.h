@@ -216,16 +216,17 @@ int mpj_dgemm(char transa, char transb, int m, int n, int k, double alpha, const
  * [0, N/16 - 1) of the circle method on the N/16 blocks of 16 indices; block
  * pair q of that round covers the 32 indices I_q (its lower block, then its
  * upper block).  For every pair q:
- *   Out[:, I_q] = In[:, I_q] * U_q       (transpose_out = 0), or
- *   Out[I_q, :] = (In[:, I_q] * U_q)^T   (transpose_out = 1),
+ *   Out[:, I_q] = In[:, I_q] * U_q       (mode bit 0 clear), or
+ *   Out[I_q, :] = (In[:, I_q] * U_q)^T   (mode bit 0 set),
  * In, Out: N x N column-major FP32 device arrays (ld = N), distinct when
- * transpose_out = 1; U_dev: N/32 column-major 32 x 32 FP32 factors, U_q at
- * U_dev + 1024 q.  Products are accurate to about 2^-21 relative.  Returns
- * MPJ_EINVAL for bad arguments, MPJ_ETIMEOUT if the tensor cores did not
- * signal completion within about 2 s, MPJ_ECUDA on a launch error.
- * Synchronizes the stream. */
-int mpj_stage1_panel(int N, int R, const float* U_dev, const float* In_dev, float* Out_dev, int transpose_out,
-                     void* stream);
+ * transposing; U_dev: N/32 column-major 32 x 32 FP32 factors, U_q at
+ * U_dev + 1024 q.  Products are accurate to about 2^-21 relative.  Mode bit 1
+ * (failure-detection test, N <= 256 only) issues no tensor-core work, so the
+ * completion wait runs out: the call then returns MPJ_ETIMEOUT after about
+ * 4 s with Out untouched and the device usable.  Returns MPJ_EINVAL for bad
+ * arguments, MPJ_ETIMEOUT if the tensor cores did not signal completion within
+ * about 2 s, MPJ_ECUDA on a launch error.  Synchronizes the stream. */
+int mpj_stage1_panel(int N, int R, const float* U_dev, const float* In_dev, float* Out_dev, int mode, void* stream);
 
 #ifdef __cplusplus
 }

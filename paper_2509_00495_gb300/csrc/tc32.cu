@@ -115,7 +115,8 @@ MPJ_DEV bool mbar_wait_bounded(uint32_t mbar, uint32_t parity) {
 
 __global__ void __launch_bounds__(TPB) tc_panel_kernel(int N, int nb, int R, const float* __restrict__ Ubuf,
                                                        const float* In, float* Out, int transpose_out,
-                                                       const float* In2, float* Out2, unsigned* flags) {
+                                                       const float* In2, float* Out2, unsigned* flags,
+                                                       int no_commit) {
   extern __shared__ __align__(1024) float sm[];
   float* xh = sm;                          // [QPC][X_FLOATS]
   float* xl = xh + QPC * X_FLOATS;         // [QPC][X_FLOATS]
@@ -192,7 +193,7 @@ __global__ void __launch_bounds__(TPB) tc_panel_kernel(int N, int nb, int R, con
   const uint32_t tmem = *tmem_slot;
   const uint32_t mb = smem_u32(mbar);
 
-  if (tid == 0) {
+  if (tid == 0 && !no_commit) {  // no_commit: failure-detection test, nothing is issued
     constexpr uint32_t idesc = idesc_tf32(TM, KQ);
     for (int qi = 0; qi < nq; ++qi) {
       const uint32_t d = tmem + (uint32_t)(qi * KQ);
@@ -254,27 +255,29 @@ __global__ void __launch_bounds__(TPB) tc_panel_kernel(int N, int nb, int R, con
 }  // namespace
 
 cudaError_t mpj_tc_panel(int N, int nb, int R, const float* Ubuf, const float* In, float* Out, int transpose_out,
-                         const float* In2, float* Out2, unsigned* flags, cudaStream_t s) {
+                         const float* In2, float* Out2, unsigned* flags, cudaStream_t s, int no_commit) {
   if (N <= 0 || N % 32 || nb != N / 16 || !Ubuf || !In || !Out) return cudaErrorInvalidValue;
   if (transpose_out && In == Out) return cudaErrorInvalidValue;
   cudaError_t e = cudaFuncSetAttribute(tc_panel_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES);
   if (e != cudaSuccess) return e;
   const int npairs = nb / 2;
   dim3 grid((N + TM - 1) / TM, (npairs + QPC - 1) / QPC, (In2 && Out2) ? 2 : 1);
-  tc_panel_kernel<<<grid, TPB, SMEM_BYTES, s>>>(N, nb, R, Ubuf, In, Out, transpose_out, In2, Out2, flags);
+  tc_panel_kernel<<<grid, TPB, SMEM_BYTES, s>>>(N, nb, R, Ubuf, In, Out, transpose_out, In2, Out2, flags, no_commit);
   mpj_count_launch();
   return cudaGetLastError();
 }
 
-extern "C" int mpj_stage1_panel(int N, int R, const float* U, const float* In, float* Out, int transpose_out,
+extern "C" int mpj_stage1_panel(int N, int R, const float* U, const float* In, float* Out, int mode,
                                 void* stream) {
-  if (N < 32 || N % 32 || R < 0 || R >= N / 16 - 1 || !U || !In || !Out) return MPJ_EINVAL;
+  const int transpose_out = mode & 1, no_commit = (mode >> 1) & 1;
+  if (N < 32 || N % 32 || R < 0 || R >= N / 16 - 1 || !U || !In || !Out || (mode & ~3)) return MPJ_EINVAL;
+  if (no_commit && N > 256) return MPJ_EINVAL;  // the test form runs one small wave only
   if (transpose_out && In == Out) return MPJ_EINVAL;
   cudaStream_t s = (cudaStream_t)stream;
   unsigned* flag = nullptr;
   cudaError_t e = cudaMallocAsync((void**)&flag, sizeof(unsigned), s);
   if (e == cudaSuccess) e = cudaMemsetAsync(flag, 0, sizeof(unsigned), s);
-  if (e == cudaSuccess) e = mpj_tc_panel(N, N / 16, R, U, In, Out, transpose_out, nullptr, nullptr, flag, s);
+  if (e == cudaSuccess) e = mpj_tc_panel(N, N / 16, R, U, In, Out, transpose_out, nullptr, nullptr, flag, s, no_commit);
   unsigned h = 0;
   if (e == cudaSuccess) e = cudaMemcpyAsync(&h, flag, sizeof(unsigned), cudaMemcpyDeviceToHost, s);
   if (flag) cudaFreeAsync(flag, s);

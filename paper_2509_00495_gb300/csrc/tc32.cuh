@@ -15,5 +15,8 @@
 // tile before writing it).  The products run as 3xTF32 (hi*hi + hi*lo +
 // lo*hi) on tcgen05.mma with the accumulators in tensor memory.  Timeouts of
 // the completion wait set MPJ_FLAG_TIMEOUT in *flags.
+// no_commit (tests only) issues no MMA and no commit, so every CTA's bounded
+// wait runs out: the kernel sets MPJ_FLAG_TIMEOUT, frees its tensor memory and
+// returns without touching Out.
 cudaError_t mpj_tc_panel(int N, int nb, int R, const float* Ubuf, const float* In, float* Out, int transpose_out,
-                         const float* In2, float* Out2, unsigned* flags, cudaStream_t s);
+                         const float* In2, float* Out2, unsigned* flags, cudaStream_t s, int no_commit = 0);

@@ -254,7 +254,8 @@ def dgemm(transa: str, transb: str, alpha: float, A: torch.Tensor, B: torch.Tens
     return Ct.T
 
 
-def stage1_panel(R: int, U: torch.Tensor, In: torch.Tensor, transpose_out: bool = False) -> torch.Tensor:
+def stage1_panel(R: int, U: torch.Tensor, In: torch.Tensor, transpose_out: bool = False,
+                 _test_no_commit: bool = False) -> torch.Tensor:
     """mpj_stage1_panel: the tensor-core block product of block round R.
     In: N x N float32 holding the column-major matrix (In[j, i] = element
     (i, j), i.e. the transpose of the logical matrix, as stored); U: (N/32,
@@ -266,7 +267,8 @@ def stage1_panel(R: int, U: torch.Tensor, In: torch.Tensor, transpose_out: bool 
     In, U = In.contiguous(), U.contiguous()
     N = In.shape[0]
     Out = torch.zeros_like(In)
-    st = lib().mpj_stage1_panel(N, R, _ptr(U), _ptr(In), _ptr(Out), int(transpose_out), _stream())
+    mode = int(transpose_out) | (2 if _test_no_commit else 0)
+    st = lib().mpj_stage1_panel(N, R, _ptr(U), _ptr(In), _ptr(Out), mode, _stream())
     _check(st, "mpj_stage1_panel")
     return Out
 

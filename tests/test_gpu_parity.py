@@ -508,3 +508,20 @@ def test_stage1_panel_tensor_cores(N, R):
     assert np.abs(out - ref).max() <= 2.0 ** -19 * scale
     outT = mpj().stage1_panel(R, Ud, Xd, transpose_out=True).cpu().numpy().T
     assert np.abs(outT - ref.T).max() <= 2.0 ** -19 * scale
+
+
+@pytest.mark.gpu
+def test_stage1_panel_timeout_is_reported():
+    """Failure detection without a fault: with no tensor-core work issued, the
+    kernel's bounded completion wait runs out, MPJ_ETIMEOUT comes back, the
+    output is untouched and the next call works."""
+    m = mpj()
+    N = 64
+    rng = np.random.default_rng(0)
+    X = torch.from_numpy(rng.standard_normal((N, N)).astype(np.float32)).cuda()
+    U = torch.from_numpy(np.stack([np.eye(32, dtype=np.float32)] * (N // 32))).cuda()
+    with pytest.raises(RuntimeError, match="MPJ_ETIMEOUT"):
+        m.stage1_panel(0, U, X, _test_no_commit=True)
+    out = m.stage1_panel(0, U, X)  # identity factors: the product is X itself
+    torch.cuda.synchronize()
+    assert torch.allclose(out, X, rtol=2.0 ** -19, atol=0)
