@@ -17,8 +17,11 @@
 // share an SM.  The round-robin ordering, the rotation records and the
 // 2x2-block update are those of common.cuh; one round is one barrier-separated
 // phase of the group.  The group's matrices live in a per-group slice of
-// global workspace.  FP64 is the bound: GB300 issues about 2 FP64 FMA per clock
-// per SM, so the batch costs its total FP64 work over 152 SMs.
+// global workspace, except the stage-1 matrices: A32 lives in shared memory
+// for n <= about 236 / 164 / 112 (G = 1024 / 512 / 256), V32 too for
+// n <= about 167 / 116 / 79.  FP64 work sets the floor: GB300 issues about
+// 2 FP64 FMA per clock per SM, so the batch costs at least its total FP64
+// work over 152 SMs; barrier-separated rounds add latency on top.
 //
 // Planning and replay: the first call for a given batch (sizes, pointer
 // arrays, tolerance) allocates the workspace, sorts the queue, picks G (timed
@@ -224,8 +227,12 @@ __global__ void __launch_bounds__(NTH, 1)
     batched_syev(const int* __restrict__ order, const int* __restrict__ nvec, const double* const* __restrict__ Aptr,
                  double* const* __restrict__ Wptr, double* const* __restrict__ Qptr, int batch, double tol_in,
                  int max32, int max64, int ns_steps, char* __restrict__ work, size_t per_group,
-                 int* __restrict__ counter, int* __restrict__ sweeps_out, unsigned* __restrict__ flags) {
+                 int* __restrict__ counter, int* __restrict__ sweeps_out, unsigned* __restrict__ flags,
+                 int region) {
   constexpr int NG = NTH / G;
+  // stage 1 keeps A32 (and V32 when both fit) in this group's `region` floats
+  // of shared memory
+  extern __shared__ __align__(16) float dsm1[];
   __shared__ double red[NG][33];
   __shared__ RotRec<double> rec64[NG][NMAX / 2 + 1];
   __shared__ RotRec<float> rec32[NG][NMAX / 2 + 1];
@@ -268,18 +275,22 @@ __global__ void __launch_bounds__(NTH, 1)
     double normA = sqrt(group_sum(g, s, red[g.id]));
     double tol = tol_in > 0 ? tol_in : (double)n * 0x1p-53 * normA;
     double tol32 = (double)n * 0x1p-24 * normA;
-    // 1. stage 1 (FP32 round-robin)
+    // 1. stage 1 (FP32 round-robin), in shared memory where it fits
+    float* reg = dsm1 + (size_t)g.id * region;
+    const int nn = n * n;
+    float* A32 = nn <= region ? reg : B.A32;
+    float* V32 = 2 * nn <= region ? reg + nn : B.V32;
     for (int e = tid; e < n * n; e += G) {
-      B.A32[e] = (float)A[e];
-      B.V32[e] = (e % n == e / n) ? 1.0f : 0.0f;
+      A32[e] = (float)A[e];
+      V32[e] = (e % n == e / n) ? 1.0f : 0.0f;
     }
     gsync(g);
     for (int sw = 0; sw < max32; ++sw) {
-      double off2 = grp_off2<float>(g, n, B.A32, red[g.id]);
+      double off2 = grp_off2<float>(g, n, A32, red[g.id]);
       if (!(off2 > tol32 * tol32)) break;
-      grp_rr_sweep<float>(g, n, B.A32, B.V32, rec32[g.id], 0x1p-24f, 0.0f);
+      grp_rr_sweep<float>(g, n, A32, V32, rec32[g.id], 0x1p-24f, 0.0f);
     }
-    for (int e = tid; e < n * n; e += G) B.X[e] = (double)B.V32[e];
+    for (int e = tid; e < n * n; e += G) B.X[e] = (double)V32[e];
     gsync(g);
     // 2. Newton-Schulz
     double* X = B.X;
@@ -334,7 +345,26 @@ __global__ void __launch_bounds__(NTH, 1)
 
 // ---------------------------------------------------------------- host side
 typedef void (*KernelFn)(const int*, const int*, const double* const*, double* const*, double* const*, int, double,
-                         int, int, int, char*, size_t, int*, int*, unsigned*);
+                         int, int, int, char*, size_t, int*, int*, unsigned*, int);
+
+// Shared memory for the stage-1 matrices: all the opt-in shared memory next to
+// the kernel's static part, split evenly among the groups of a CTA.
+cudaError_t stage1_smem(KernelFn k, int G, int* region, size_t* dyn) {
+  int dev = 0, optin = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  cudaFuncAttributes fa;
+  if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, k);
+  if (e != cudaSuccess) return e;
+  const int ng = NTH / G;
+  long budget = (long)optin - (long)fa.sharedSizeBytes - 1024;
+  long per = budget > 0 ? budget / (ng * (long)sizeof(float)) : 0;
+  per &= ~3L;  // keep each region 16-byte aligned
+  if (per > 2L * NMAX * NMAX) per = 2L * NMAX * NMAX;
+  *region = (int)per;
+  *dyn = (size_t)ng * per * sizeof(float);
+  return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)*dyn);
+}
 
 KernelFn kernel_for(int G) {
   if (G == 256) return batched_syev<256>;
@@ -450,9 +480,13 @@ cudaError_t enqueue(const Plan* p, const Layout& L, const double* const* A, doub
   unsigned* d_flags = (unsigned*)(d_counter + 1);
   cudaError_t e = cudaMemsetAsync(d_counter, 0, 2 * sizeof(int), s);
   if (e != cudaSuccess) return e;
-  kernel_for(G)<<<p->grid, NTH, 0, s>>>((const int*)(base + L.order), (const int*)(base + L.nvec), A, W, Q, p->batch,
-                                        p->tol, 15, 30, 2, base, group_bytes(), d_counter, (int*)(base + L.sweeps),
-                                        d_flags);
+  int region = 0;
+  size_t dyn = 0;
+  e = stage1_smem(kernel_for(G), G, &region, &dyn);
+  if (e != cudaSuccess) return e;
+  kernel_for(G)<<<p->grid, NTH, dyn, s>>>((const int*)(base + L.order), (const int*)(base + L.nvec), A, W, Q, p->batch,
+                                          p->tol, 15, 30, 2, base, group_bytes(), d_counter, (int*)(base + L.sweeps),
+                                          d_flags, region);
   if (count) mpj_count_launch();
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
