@@ -522,12 +522,16 @@ size_t mpj_jacobi64_scratch_bytes(int n) { return mpj_jacobi64_scratch_bytes_rv(
 
 namespace {
 // Side stream and events for overlapping the V updates with the rotation
-// rounds; released when the solve returns.
+// rounds; released when the solve returns.  On every exit (also an early
+// error return) the owner stream is first made to wait for the side stream,
+// so stream-ordered reuse or freeing of the scratch stays after the last V
+// update.
 struct SideStream {
+  cudaStream_t owner = nullptr;
   cudaStream_t sv = nullptr;
   cudaEvent_t ready = nullptr, done[2] = {nullptr, nullptr};
   bool ok = false;
-  SideStream() {
+  explicit SideStream(cudaStream_t s) : owner(s) {
     ok = cudaStreamCreateWithFlags(&sv, cudaStreamNonBlocking) == cudaSuccess &&
          cudaEventCreateWithFlags(&ready, cudaEventDisableTiming) == cudaSuccess &&
          cudaEventCreateWithFlags(&done[0], cudaEventDisableTiming) == cudaSuccess &&
@@ -535,6 +539,7 @@ struct SideStream {
     if (!ok) (void)cudaGetLastError();
   }
   ~SideStream() {
+    if (ok && cudaEventRecord(ready, sv) == cudaSuccess) (void)cudaStreamWaitEvent(owner, ready, 0);
     if (done[1]) cudaEventDestroy(done[1]);
     if (done[0]) cudaEventDestroy(done[0]);
     if (ready) cudaEventDestroy(ready);
@@ -620,7 +625,7 @@ int mpj_jacobi64_run(int n, double* A, int lda, double* V, int ldv, double tol, 
     bool need_init = true;
     std::unique_ptr<SideStream> side;
     if (overlap) {
-      side.reset(new SideStream());
+      side.reset(new SideStream(s));
       if (!side->ok) overlap = false;
     }
     int hb = 0;                          // history half being filled

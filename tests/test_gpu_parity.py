@@ -18,6 +18,7 @@ pytestmark = pytest.mark.gpu
 
 import oracle  # noqa: E402
 from paper_2509_00495_gb300 import inputs  # noqa: E402
+from block_sets import block_sets  # noqa: E402
 
 U = 2.0 ** -53
 UL = 2.0 ** -24
@@ -474,22 +475,6 @@ def test_batched_rejects_nonfinite():
 
 
 # ---------------------------------------------------------------- stage-1 tensor-core block product
-def _block_sets(N, R):
-    """Index sets I_q of block round R (circle method on N/16 blocks of 16),
-    written out independently of the library: slot 0 pairs (R, nb-1), slot i
-    pairs (R+i, R-i) mod nb-1; I_q = lower block's 16 indices, then the upper's."""
-    nb = N // 16
-    sets = []
-    for i in range(nb // 2):
-        if i == 0:
-            x, y = R, nb - 1
-        else:
-            x, y = (R + i) % (nb - 1), (R - i) % (nb - 1)
-        lo, hi = min(x, y), max(x, y)
-        sets.append(np.r_[np.arange(16 * lo, 16 * lo + 16), np.arange(16 * hi, 16 * hi + 16)])
-    return sets
-
-
 @pytest.mark.gpu
 @pytest.mark.parametrize("N,R", [(64, 0), (96, 3), (320, 7), (1024, 30)])
 def test_stage1_panel_tensor_cores(N, R):
@@ -499,7 +484,7 @@ def test_stage1_panel_tensor_cores(N, R):
     Uq = np.stack([np.linalg.qr(rng.standard_normal((32, 32)))[0] for _ in range(N // 32)]).astype(np.float32)
     Xd = torch.from_numpy(np.ascontiguousarray(X.T)).cuda()       # column-major storage
     Ud = torch.from_numpy(np.ascontiguousarray(Uq.transpose(0, 2, 1))).cuda()
-    sets = _block_sets(N, R)
+    sets = block_sets(N, R)
     ref = np.zeros((N, N))
     for q, I in enumerate(sets):
         ref[:, I] = X[:, I].astype(np.float64) @ Uq[q].astype(np.float64)

@@ -466,3 +466,17 @@ def test_threshold_variant_same_result_fewer_rotations(ordering):
     Wn, Qn, infon = oracle.syev_mixed(A, ordering32=ordering, ordering64=ordering)
     assert info.rotations64 < infon.rotations64
     assert np.abs(W - Wn).max() <= 1e-13
+
+
+@pytest.mark.parametrize("N", [32, 64, 96, 256])
+def test_block_sets_helper_matches_oracle_schedule(N):
+    """The index sets the tensor-core panel test expects per block pair are the
+    index sets of the oracle's block round-robin schedule."""
+    from block_sets import block_sets
+    sched = oracle.block_schedule(N)
+    for R, rnd in enumerate(sched):
+        sets = block_sets(N, R)
+        assert len(sets) == len(rnd)
+        for P, inner in enumerate(rnd):
+            idx = {i for rho in inner for pq in rho for i in pq}
+            assert idx == set(sets[P].tolist()), (N, R, P)
