@@ -18,8 +18,8 @@
 // 2x2-block update are those of common.cuh; one round is one barrier-separated
 // phase of the group.  The group's matrices live in a per-group slice of
 // global workspace, except the stage-1 matrices: A32 lives in shared memory
-// for n <= about 236 / 164 / 112 (G = 1024 / 512 / 256), V32 too for
-// n <= about 167 / 116 / 79.  FP64 work sets the floor: GB300 issues about
+// for n <= about 233 / 160 / 106 (G = 1024 / 512 / 256), V32 too for
+// n <= about 165 / 113 / 75.  FP64 work sets the floor: GB300 issues about
 // 2 FP64 FMA per clock per SM, so the batch costs at least its total FP64
 // work over 152 SMs; barrier-separated rounds add latency on top.
 //
@@ -205,6 +205,142 @@ MPJ_DEV void grp_rr_sweep(const Grp& g, int n, T* A, T* V, RotRec<T>* rec, T ski
   }
 }
 
+// Record of one slot for the scaled FP64 sweep: multipliers mx, my (zero:
+// not rotated), c - 1 of the rotation, true diagonals after it.
+struct SRec {
+  double mx, my, cm1, dx, dy;
+};
+
+MPJ_DEV bool srec_rotated(const SRec& r) {
+  return (__double_as_longlong(r.mx) | __double_as_longlong(r.my)) != 0;  // bit test, not an FP64 compare
+}
+
+// One round-robin sweep of the FP64 stage with scaled rotations (the scheme
+// of the single-matrix sweeps): off the diagonal A = D Ã D and V = Ṽ D with
+// one scale vector d (double-double, in shared memory), so a rotation costs
+// one FMA per entry and side, Ã_x -= mx Ã_y, Ã_y += my Ã_x with
+// mx = τ d_y / d_x, my = τ d_x / d_y, and d_x, d_y take the factor c; the true
+// diagonal stays in A's diagonal entries.  The scales are folded back at the
+// end of the sweep (at most n - 1 <= 255 factors c >= 2^-1/2 per index, so d
+// stays far above the FP64 range limit).  Pairs with |a_pq| <= skip sqrt|a_pp
+// a_qq| or |a_pq| <= skip_abs are skipped (a_pq the true coupling).
+MPJ_DEV void grp_rr_sweep_fast(const Grp& g, int n, double* A, double* V, SRec* rec, double2* d, double skip,
+                               double skip_abs) {
+  const int m = n + (n & 1), h = m / 2;
+  for (int i = g.t; i < n; i += g.n) d[i] = make_double2(1.0, 0.0);
+  gsync(g);
+  for (int r = 0; r < m - 1; ++r) {
+    for (int i = g.t; i < h; i += g.n) {
+      int x, y;
+      rr_slot(m, r, i, x, y);
+      const bool vx = x < n, vy = y < n;
+      SRec rr;
+      rr.mx = 0.0;
+      rr.my = 0.0;
+      rr.cm1 = 0.0;
+      rr.dx = vx ? A[(size_t)x * n + x] : 0.0;
+      rr.dy = vy ? A[(size_t)y * n + y] : 0.0;
+      if (vx && vy) {
+        const double sx = d[x].x, sy = d[y].x;
+        const double axy = A[(size_t)y * n + x] * sx * sy;  // true coupling
+        const bool xp = x < y;
+        const double app = xp ? rr.dx : rr.dy, aqq = xp ? rr.dy : rr.dx;
+        double t, cm1, s;
+        if (jacobi_pair<double>(app, aqq, axy, skip, t, cm1, s, skip_abs)) {
+          const double np = app - t * axy, nq = aqq + t * axy;
+          const double tau = xp ? t : -t;
+          rr.mx = tau * (sy / sx);
+          rr.my = tau * (sx / sy);
+          rr.cm1 = cm1;
+          rr.dx = xp ? np : nq;
+          rr.dy = xp ? nq : np;
+        }
+      }
+      rec[i] = rr;
+    }
+    gsync(g);
+#pragma unroll 4
+    for (int e = g.t; e < h * h; e += g.n) {
+      int a = e % h, b = e / h;
+      if (a < b) continue;
+      const SRec ra = rec[a];
+      const bool rota = srec_rotated(ra);
+      int xa, ya, xb, yb;
+      rr_slot(m, r, a, xa, ya);
+      if (a == b) {
+        if (rota) {
+          A[(size_t)xa * n + xa] = ra.dx;
+          A[(size_t)ya * n + ya] = ra.dy;
+          A[(size_t)ya * n + xa] = 0.0;
+          A[(size_t)xa * n + ya] = 0.0;
+        }
+        continue;
+      }
+      const SRec rb = rec[b];
+      const bool rotb = srec_rotated(rb);
+      if (!rota && !rotb) continue;
+      rr_slot(m, r, b, xb, yb);
+      const bool vxa = xa < n, vya = ya < n, vxb = xb < n, vyb = yb < n;
+      double vxx = (vxa && vxb) ? A[(size_t)xb * n + xa] : 0.0;
+      double vxy = (vxa && vyb) ? A[(size_t)yb * n + xa] : 0.0;
+      double vyx = (vya && vxb) ? A[(size_t)xb * n + ya] : 0.0;
+      double vyy = (vya && vyb) ? A[(size_t)yb * n + ya] : 0.0;
+      if (rota) {  // rows x_a, y_a
+        double t0 = fma(-ra.mx, vyx, vxx), t1 = fma(ra.my, vxx, vyx);
+        double t2 = fma(-ra.mx, vyy, vxy), t3 = fma(ra.my, vxy, vyy);
+        vxx = t0;
+        vyx = t1;
+        vxy = t2;
+        vyy = t3;
+      }
+      if (rotb) {  // columns x_b, y_b
+        double t0 = fma(-rb.mx, vxy, vxx), t1 = fma(rb.my, vxx, vxy);
+        double t2 = fma(-rb.mx, vyy, vyx), t3 = fma(rb.my, vyx, vyy);
+        vxx = t0;
+        vxy = t1;
+        vyx = t2;
+        vyy = t3;
+      }
+      if (vxa && vxb) A[(size_t)xb * n + xa] = A[(size_t)xa * n + xb] = vxx;
+      if (vxa && vyb) A[(size_t)yb * n + xa] = A[(size_t)xa * n + yb] = vxy;
+      if (vya && vxb) A[(size_t)xb * n + ya] = A[(size_t)ya * n + xb] = vyx;
+      if (vya && vyb) A[(size_t)yb * n + ya] = A[(size_t)ya * n + yb] = vyy;
+    }
+#pragma unroll 4
+    for (int e = g.t; e < n * h; e += g.n) {
+      int row = e % n, b = e / n;
+      const SRec rb = rec[b];
+      if (!srec_rotated(rb)) continue;
+      int xb, yb;
+      rr_slot(m, r, b, xb, yb);
+      double vx = V[(size_t)xb * n + row], vy = V[(size_t)yb * n + row];
+      V[(size_t)xb * n + row] = fma(-rb.mx, vy, vx);
+      V[(size_t)yb * n + row] = fma(rb.my, vx, vy);
+    }
+    // scales of the rotated indices (read again only in the next record phase)
+    for (int i = g.t; i < h; i += g.n) {
+      const SRec rr = rec[i];
+      if (!srec_rotated(rr)) continue;
+      int x, y;
+      rr_slot(m, r, i, x, y);
+      d[x] = dd_scale(d[x], rr.cm1);
+      d[y] = dd_scale(d[y], rr.cm1);
+    }
+    gsync(g);
+  }
+  // fold the scales back: A_ij = Ã_ij d_i d_j off the diagonal, V_ij = Ṽ_ij d_j
+  for (int e = g.t; e < n * n; e += g.n) {
+    int i = e % n, j = e / n;
+    const double sj = d[j].x + d[j].y;
+    if (i != j) {
+      const double si = d[i].x + d[i].y;
+      A[e] = (A[e] * si) * sj;
+    }
+    V[e] *= sj;
+  }
+  gsync(g);
+}
+
 template <typename T>
 MPJ_DEV double grp_off2(const Grp& g, int n, const T* A, double* red) {
   double s = 0.0;
@@ -234,7 +370,8 @@ __global__ void __launch_bounds__(NTH, 1)
   // of shared memory
   extern __shared__ __align__(16) float dsm1[];
   __shared__ double red[NG][33];
-  __shared__ RotRec<double> rec64[NG][NMAX / 2 + 1];
+  __shared__ SRec rec64[NG][NMAX / 2 + 1];
+  __shared__ double2 dsc[NG][NMAX];
   __shared__ RotRec<float> rec32[NG][NMAX / 2 + 1];
   __shared__ int job[NG];
   __shared__ int rank_sh[NG][NMAX];
@@ -317,7 +454,7 @@ __global__ void __launch_bounds__(NTH, 1)
         if (tid == 0) atomicOr(flags, MPJ_FLAG_TIMEOUT);  // cap reached: reported as not converged
         break;
       }
-      grp_rr_sweep<double>(g, n, B.M, V, rec64[g.id], 0x1p-53, tol / n);  // threshold variant
+      grp_rr_sweep_fast(g, n, B.M, V, rec64[g.id], dsc[g.id], 0x1p-53, tol / n);  // threshold variant
       ++sweeps;
     }
     // 5. sort, permute, Q = X Vp

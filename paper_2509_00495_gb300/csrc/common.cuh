@@ -59,6 +59,16 @@ MPJ_DEV bool jacobi_pair(T app, T aqq, T apq, T skip, T& t, T& cm1, T& s, T skip
   return true;
 }
 
+// Scale factor update of the scaled ("fast") rotations: d' = d (1 + cm1),
+// d = d.x + d.y in double-double (Fast2Sum renormalization, |cm1| < 0.3), so
+// that factors c = 1 + cm1 that round to 1 in FP64 still shrink d exactly.
+MPJ_DEV double2 dd_scale(double2 d, double cm1) {
+  double sum = fma(cm1, d.x, fma(cm1, d.y, d.y));
+  double hi = d.x + sum;
+  double lo = sum - (hi - d.x);
+  return make_double2(hi, lo);
+}
+
 // Apply a rotation record to a pair of values (rows or columns x, y).
 template <typename T>
 MPJ_DEV void rot_apply(T cm1, T sig, T& vx, T& vy) {

@@ -64,13 +64,6 @@ MPJ_DEV bool frec_rotated(const FRec& r) {
 // the record so the per-entry path never evaluates sqrt or a division).
 MPJ_DEV double frec_cm1(const FRec& r) { return r.cm1; }
 
-// d' = d (1 + cm1) in double-double (Fast2Sum renormalization, |cm1| < 0.3).
-MPJ_DEV double2 dd_scale(double2 d, double cm1) {
-  double sum = fma(cm1, d.x, fma(cm1, d.y, d.y));
-  double hi = d.x + sum;
-  double lo = sum - (hi - d.x);
-  return make_double2(hi, lo);
-}
 
 // Record of pair (i, j) of round r from true diagonals di, dj, true coupling
 // aij and the scales si, sj the round will see.  Returns the slot.
