@@ -189,7 +189,7 @@ MPJ_DEV void grp_rr_sweep(const Grp& g, int n, T* A, T* V, RotRec<T>* rec, T ski
       if (vya && vxb) A[(size_t)xb * n + ya] = A[(size_t)ya * n + xb] = vyx;
       if (vya && vyb) A[(size_t)yb * n + ya] = A[(size_t)ya * n + yb] = vyy;
     }
-#pragma unroll 4
+#pragma unroll 8
     for (int e = g.t; e < n * h; e += g.n) {
       int row = e % n, b = e / n;
       RotRec<T> rb = rec[b];
