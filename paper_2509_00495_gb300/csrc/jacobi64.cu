@@ -142,33 +142,13 @@ MPJ_DEV void build_next_rec(const HostIn& h, int m, int n, int rn, double skip, 
   rec_next[sl] = nr;
 }
 
-// One round on A (scaled form) + next round's records + this round's V multipliers.
-// Each thread owns one 2 x 2 block (rows x_a, y_a; columns x_b, y_b) of the lower
-// slot triangle.  The n/2 records of the next round need a square root and
-// divisions each; their inputs are queued in shared memory and built by the
-// CTA's first warp with all lanes busy, instead of by one lane of many warps
-// (FP64 instructions issue at 1/64 of the FP32 rate on this GPU).
-__global__ void __launch_bounds__(256, 5) rr_step64(double* __restrict__ A, int lda, int n, int m, int r, double skip,
-                                                 double skip_abs, const FRec* __restrict__ rec,
-                                                 FRec* __restrict__ rec_next,
-                                                 const double2* __restrict__ dcur, double2* __restrict__ dnext,
-                                                 double2* __restrict__ hist_row) {
-  __shared__ HostIn hq[HMAX];
-  __shared__ int hcount;
-  const int half = m / 2;
-  const int rn = (r + 1 == m - 1) ? 0 : r + 1;  // next round (wraps into the next sweep)
-  int ti, tj;
-  tri_tile(blockIdx.x, ti, tj);
-  const int a = ti * TS + (threadIdx.x % TS);
-  const int b = tj * TS + (threadIdx.x / TS);
-  if (threadIdx.x == 0) hcount = 0;
-  // Programmatic dependent launch: once every CTA of this round has started,
-  // the next round's CTAs may be scheduled into the slots this round frees;
-  // each waits here until the previous round has completed and its writes
-  // are visible (no global memory is touched before the wait).
-  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-  asm volatile("griddepcontrol.wait;" ::: "memory");
-  __syncthreads();
+// One 2 x 2 block (rows x_a, y_a; columns x_b, y_b) of a round, with the
+// diagonal blocks' scale and record work; next-round record inputs hosted by
+// the block go to the CTA's shared-memory queue.
+MPJ_DEV void rr_block(int a, int b, double* __restrict__ A, int lda, int n, int m, int r, int rn, int half,
+                      double skip, double skip_abs, const FRec* __restrict__ rec, FRec* __restrict__ rec_next,
+                      const double2* __restrict__ dcur, double2* __restrict__ dnext, double2* __restrict__ hist_row,
+                      HostIn* hq, int* hcount) {
   if (a < half && b < half && a >= b) {
     int xa, ya;
     rr_slot(m, r, a, xa, ya);
@@ -275,9 +255,144 @@ __global__ void __launch_bounds__(256, 5) rr_step64(double* __restrict__ A, int 
           h.aij = side ? ((h.j == xb) ? vyx : vyy) : ((h.j == xb) ? vxx : vxy);
           h.cmi = rota ? pa->cm1 : 0.0;
           h.cmj = rotb ? pb->cm1 : 0.0;
-          int slot = atomicAdd(&hcount, 1);
+          int slot = atomicAdd(hcount, 1);
           if (slot < HMAX) hq[slot] = h;  // always true (see HMAX)
         }
+      }
+    }
+  }
+}
+
+
+// One round on A (scaled form) + next round's records + this round's V
+// multipliers.  A CTA of 128 threads takes a 16 x 16 tile of the lower slot
+// triangle; each thread owns two 2 x 2 blocks (row slots a and a + 8, column
+// slot b).  Off-diagonal tiles load both blocks' four entries before any
+// arithmetic or store (eight loads in flight per thread); diagonal tiles take
+// the general per-block path.  The n/2 records of the next round need a
+// square root and divisions each; their inputs are queued in shared memory
+// and built by the CTA's first warp with all lanes busy, instead of by one
+// lane of many warps (FP64 instructions issue at 1/64 of the FP32 rate on
+// this GPU).  80 registers, 6 CTAs per SM.
+__global__ void __launch_bounds__(128, 6) rr_step64(double* __restrict__ A, int lda, int n, int m, int r,
+                                                      double skip, double skip_abs, const FRec* __restrict__ rec,
+                                                      FRec* __restrict__ rec_next,
+                                                      const double2* __restrict__ dcur, double2* __restrict__ dnext,
+                                                      double2* __restrict__ hist_row) {
+  __shared__ HostIn hq[HMAX];
+  __shared__ int hcount;
+  const int half = m / 2;
+  const int rn = (r + 1 == m - 1) ? 0 : r + 1;
+  int ti, tj;
+  tri_tile(blockIdx.x, ti, tj);
+  const int b = tj * TS + (threadIdx.x >> 3);
+  const int a0 = ti * TS + (threadIdx.x & 7);
+  if (threadIdx.x == 0) hcount = 0;
+  // Programmatic dependent launch: once every CTA of this round has started,
+  // the next round's CTAs may be scheduled into the slots this round frees;
+  // each waits here until the previous round has completed and its writes
+  // are visible (no global memory is touched before the wait).
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  __syncthreads();
+  if (ti == tj) {
+#pragma unroll 1
+    for (int k = 0; k < 2; ++k)
+      rr_block(a0 + 8 * k, b, A, lda, n, m, r, rn, half, skip, skip_abs, rec, rec_next, dcur, dnext, hist_row, hq,
+               &hcount);
+  } else if (b < half) {  // a > b for both blocks
+    int xb, yb;
+    rr_slot(m, r, b, xb, yb);
+    const FRec* pb = rec + b;
+    const double2 mb = frec_m(pb);
+    const bool rotb = m_rotated(mb);
+    const bool vxb = xb < n, vyb = yb < n;
+    const size_t cxb = (size_t)xb * lda, cyb = (size_t)yb * lda;
+    int xa[2], ya[2], jx[2], jy[2];
+    bool need[2], rota[2], nx[2], ny[2], vxa[2], vya[2];
+    double2 ma[2];
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      const int a = a0 + 8 * k;
+      need[k] = false;
+      rota[k] = nx[k] = ny[k] = vxa[k] = vya[k] = false;
+      xa[k] = ya[k] = jx[k] = jy[k] = 0;
+      ma[k] = make_double2(0.0, 0.0);
+      if (a < half) {
+        rr_slot(m, r, a, xa[k], ya[k]);
+        ma[k] = frec_m(rec + a);
+        rota[k] = m_rotated(ma[k]);
+        vxa[k] = xa[k] < n;
+        vya[k] = ya[k] < n;
+        jx[k] = vxa[k] ? rr_partner(m, rn, xa[k]) : -1;
+        jy[k] = vya[k] ? rr_partner(m, rn, ya[k]) : -1;
+        nx[k] = jx[k] >= 0 && jx[k] < n && (jx[k] == xb || jx[k] == yb);
+        ny[k] = jy[k] >= 0 && jy[k] < n && (jy[k] == xb || jy[k] == yb);
+        need[k] = rota[k] || rotb || nx[k] || ny[k];
+      }
+    }
+    double v[2][4];
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      v[k][0] = (need[k] && vxa[k] && vxb) ? A[cxb + xa[k]] : 0.0;
+      v[k][1] = (need[k] && vxa[k] && vyb) ? A[cyb + xa[k]] : 0.0;
+      v[k][2] = (need[k] && vya[k] && vxb) ? A[cxb + ya[k]] : 0.0;
+      v[k][3] = (need[k] && vya[k] && vyb) ? A[cyb + ya[k]] : 0.0;
+    }
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      if (!need[k]) continue;
+      double vxx = v[k][0], vxy = v[k][1], vyx = v[k][2], vyy = v[k][3];
+      if (rota[k]) {
+        double t0 = fma(-ma[k].x, vyx, vxx), t1 = fma(ma[k].y, vxx, vyx);
+        double t2 = fma(-ma[k].x, vyy, vxy), t3 = fma(ma[k].y, vxy, vyy);
+        vxx = t0;
+        vyx = t1;
+        vxy = t2;
+        vyy = t3;
+      }
+      if (rotb) {
+        double t0 = fma(-mb.x, vxy, vxx), t1 = fma(mb.y, vxx, vxy);
+        double t2 = fma(-mb.x, vyy, vyx), t3 = fma(mb.y, vyx, vyy);
+        vxx = t0;
+        vxy = t1;
+        vyx = t2;
+        vyy = t3;
+      }
+      const int xk = xa[k], yk = ya[k];
+      if (rota[k] || rotb) {
+        if (vxa[k] && vxb) {
+          A[cxb + xk] = vxx;
+          A[(size_t)xk * lda + xb] = vxx;
+        }
+        if (vxa[k] && vyb) {
+          A[cyb + xk] = vxy;
+          A[(size_t)xk * lda + yb] = vxy;
+        }
+        if (vya[k] && vxb) {
+          A[cxb + yk] = vyx;
+          A[(size_t)yk * lda + xb] = vyx;
+        }
+        if (vya[k] && vyb) {
+          A[cyb + yk] = vyy;
+          A[(size_t)yk * lda + yb] = vyy;
+        }
+      }
+      const FRec* pa = rec + a0 + 8 * k;
+#pragma unroll
+      for (int side = 0; side < 2; ++side) {
+        if (side == 0 && !nx[k]) continue;
+        if (side == 1 && !ny[k]) continue;
+        HostIn h;
+        h.i = side ? yk : xk;
+        h.j = side ? jy[k] : jx[k];
+        h.di = side ? pa->dy : pa->dx;
+        h.dj = (h.j == xb) ? pb->dx : pb->dy;
+        h.aij = side ? ((h.j == xb) ? vyx : vyy) : ((h.j == xb) ? vxx : vxy);
+        h.cmi = rota[k] ? pa->cm1 : 0.0;
+        h.cmj = rotb ? pb->cm1 : 0.0;
+        int slot = atomicAdd(&hcount, 1);
+        if (slot < HMAX) hq[slot] = h;  // always true (see HMAX)
       }
     }
   }
@@ -548,7 +663,7 @@ cudaError_t launch_rr_step64(int grid, cudaStream_t s, double* A, int lda, int n
                              double2* hist_row) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(grid);
-  cfg.blockDim = dim3(256);
+  cfg.blockDim = dim3(128);
   cfg.dynamicSmemBytes = 0;
   cfg.stream = s;
   cudaLaunchAttribute attr[1];
@@ -556,8 +671,8 @@ cudaError_t launch_rr_step64(int grid, cudaStream_t s, double* A, int lda, int n
   attr[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  cudaError_t e = cudaLaunchKernelEx(&cfg, rr_step64, A, lda, n, m, r, skip, skip_abs, rec, rec_next, dcur, dnext,
-                                     hist_row);
+  cudaError_t e =
+      cudaLaunchKernelEx(&cfg, rr_step64, A, lda, n, m, r, skip, skip_abs, rec, rec_next, dcur, dnext, hist_row);
   mpj_count_launch();
   return e;
 }
