@@ -37,9 +37,9 @@ UNIT = "solves/s"
 U_D = 2.0 ** -53
 FP64_PEAK_TFLOPS = 1.25  # nominal GB300 FP64 (152 SMs x 2 FP64 FMA/clk x 2 flop x ~2.07 GHz)
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum, one ncu capture each)
-# of one FP64 round at n = 4096: rr_step64 68.0 + 75.4 MB, plus 1/64 of a 64-round
+# of one FP64 round at n = 4096: rr_step64 67.8 + 78.2 MB, plus 1/64 of a 64-round
 # v_apply_rounds launch (137.0 + 79.2 MB).  Valid for these kernel versions only.
-TRAFFIC_PER_ROUND_N4096 = 67.96e6 + 75.44e6 + (136.99e6 + 79.17e6) / 64
+TRAFFIC_PER_ROUND_N4096 = 67.84e6 + 78.23e6 + (136.99e6 + 79.17e6) / 64
 WORKLOAD = "geo4096: one symmetric FP64 matrix n=4096, |lam| geometric in [1e-6,1] (condition 1e6), random signs, Haar eigenvectors, seed 0"
 
 
