@@ -13,7 +13,8 @@
  *   3. A_cond = Q_d^T A Q_d in FP64 (Alg. 9 step 3),
  *   4. FP64 Jacobi sweeps on A_cond from V = I until off(A_cond) <= tol
  *      (Alg. 4, with the round-robin or the cyclic-by-row ordering),
- *   5. W = diag(A_cond), Q = Q_d V.
+ *   5. W = diag(A_cond), Q = Q_d V (formed by rotating the columns of Q_d
+ *      directly, the same product by associativity).
  * The plain method is step 4 applied to A itself (the paper's jacobi_eig).
  *
  * Conventions for every entry point:
@@ -28,7 +29,16 @@
  *     device (non-finite input, sweep cap) are reported through mpj_info after
  *     the call returns (the solve entry points synchronize `stream`);
  *   - no entry point traps or asserts on the device; every device-side wait
- *     has an iteration limit.
+ *     has an iteration or clock limit.
+ *
+ * Environment switches (read once per process):
+ *   MPJ_JACOBI_OVERLAP=0  keep the batched V updates of the round-robin FP64
+ *                         sweeps on `stream` (by default they run on a
+ *                         private side stream joined back into `stream`);
+ *   MPJ_STAGE1_TC=1       run the stage-1 A update on the tcgen05 tensor
+ *                         cores (3xTF32; slower on GB300, off by default);
+ *   MPJ_AUTOTUNE_CACHE=f  file that keeps the batched group-size choices;
+ *   MPJ_BATCHED_GROUP=g   fix the batched group size (256, 512 or 1024).
  */
 #ifndef MPJACOBI_H
 #define MPJACOBI_H
@@ -188,7 +198,7 @@ int mpj_jacobi64(int n, double* A_dev, int lda, double* V_dev, int ldv, double t
  * calls are not allowed at that point.  Same arguments, behaviour and results
  * as mpj_jacobi64, but the sweep's scratch (rotation records, scale vectors,
  * reduction partials and a batch of rotation multipliers for V: about
- * (72 + 8 r) n bytes with r rounds per V batch, r = 64 down to 1 as n grows)
+ * (80 + 8 r) n bytes with r rounds per V batch, r = 64 down to 1 as n grows)
  * lives in one fixed array of MPJ_NOALLOC_SCRATCH_BYTES bytes in device
  * memory, reserved in every GPU that loads the library until the process
  * exits; no cudaMalloc, cudaFree or
