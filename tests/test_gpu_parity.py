@@ -510,3 +510,34 @@ def test_stage1_panel_timeout_is_reported():
     out = m.stage1_panel(0, U, X)  # identity factors: the product is X itself
     torch.cuda.synchronize()
     assert torch.allclose(out, X, rtol=2.0 ** -19, atol=0)
+
+
+_OVERLAP_SCRIPT = r"""
+import sys, numpy as np, torch
+sys.path.insert(0, sys.argv[1])
+from paper_2509_00495_gb300 import inputs, mpj
+A, lam = inputs.geo_matrix(300, 1e4, seed=7)
+r = mpj.syev_ex(torch.from_numpy(A).cuda())
+torch.cuda.synchronize()
+np.save(sys.argv[2], np.concatenate([r.W.cpu().numpy()[None, :], r.Q.cpu().numpy()]))
+"""
+
+
+@pytest.mark.gpu
+def test_side_stream_overlap_is_bitwise_neutral(tmp_path):
+    """The batched V updates give the same bits on the private side stream as
+    on the caller's stream (n = 300 >= 256 turns the overlap on); a difference
+    would flag a race between the rotation rounds and the V updates."""
+    import os
+    import subprocess
+    import sys as _sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    script = tmp_path / "run.py"
+    script.write_text(_OVERLAP_SCRIPT)
+    outs = []
+    for flag in ("1", "0"):
+        out = tmp_path / f"wq{flag}.npy"
+        env = dict(os.environ, MPJ_JACOBI_OVERLAP=flag)
+        subprocess.run([_sys.executable, str(script), root, str(out)], check=True, env=env, timeout=300)
+        outs.append(np.load(out))
+    assert np.array_equal(outs[0], outs[1])
