@@ -50,15 +50,13 @@ struct __align__(16) FRec {
   double mx, my, cm1, dx, dy, pad;
 };
 
-// The multipliers of a record (the only fields every block reads).
+// The multipliers of a record (the only fields every block reads), and the
+// rotated test as a bit test instead of an FP64 compare: on this GPU FP64
+// compares issue on the same slow FP64 pipe as the FMAs.  "Not rotated"
+// records hold +0.0 exactly.
 MPJ_DEV double2 frec_m(const FRec* __restrict__ p) { return __ldg(reinterpret_cast<const double2*>(p)); }
 MPJ_DEV bool m_rotated(double2 mm) { return (__double_as_longlong(mm.x) | __double_as_longlong(mm.y)) != 0; }
 
-// Bit test instead of an FP64 compare: on this GPU FP64 compares issue on the
-// same slow FP64 pipe as the FMAs.  "Not rotated" records hold +0.0 exactly.
-MPJ_DEV bool frec_rotated(const FRec& r) {
-  return (__double_as_longlong(r.mx) | __double_as_longlong(r.my)) != 0;
-}
 
 // c - 1 of a record, computed once per slot when the record is built (kept in
 // the record so the per-entry path never evaluates sqrt or a division).

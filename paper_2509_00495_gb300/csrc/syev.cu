@@ -386,8 +386,8 @@ int mpj_syev_ex(int n, const double* A, int lda, double* W, double* Q, int ldq, 
         if ((st = ns_steps_run(n, &X2, Z, &Y2, o.ns_steps, (char*)S1 + al((size_t)n * n * sizeof(double)), s)) !=
             MPJ_OK)
           goto done;
-        // A_cond2 = Q_d2^T (A_cond Q_d2): T = A_cond Q_d2 into Z, then into M (A_cond is consumed)
-        double* T = (X2 == Ql2) ? (double*)S1 : Ql2;
+        // A_cond2 = Q_d2^T (A_cond Q_d2): A_cond Q_d2 into Z, then Q_d2^T Z into M (A_cond is
+        // consumed); then Q_d = Q_d1 Q_d2 into Z
         if (mpj_gemm64(false, false, n, n, n, 1.0, M, n, X2, n, 0.0, nullptr, n, Z, n, 0, s) != cudaSuccess ||
             mpj_gemm64(true, false, n, n, n, 1.0, X2, n, Z, n, 0.0, nullptr, n, M, n, 1, s) != cudaSuccess ||
             mpj_gemm64(false, false, n, n, n, 1.0, Xp, n, X2, n, 0.0, nullptr, n, Z, n, 0, s) != cudaSuccess) {
@@ -395,7 +395,6 @@ int mpj_syev_ex(int n, const double* A, int lda, double* W, double* Q, int ldq, 
           st = MPJ_ECUDA;
           goto done;
         }
-        (void)T;
         Qd = Z;   // Q_d = Q_d1 Q_d2
         Ac = M;
         V = Xp;   // Q_d1 is folded into Z
