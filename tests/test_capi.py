@@ -66,3 +66,46 @@ def test_binding_refuses_cpu_tensors(libpath):
     from paper_2509_00495_gb300 import mpj
     with pytest.raises(TypeError):
         mpj.syev(torch.eye(3, dtype=torch.float64))
+
+
+def test_more_host_side_argument_checks(libpath):
+    """Entry points added later reject bad arguments on the host as well."""
+    from paper_2509_00495_gb300 import mpj
+    L = mpj.lib()
+    p = ctypes.c_void_p(256)
+    # stage-1 panel: N a multiple of 32, R in range, known mode bits, test mode only for N <= 256
+    assert L.mpj_stage1_panel(48, 0, p, p, p, 0, None) == mpj.MPJ_EINVAL
+    assert L.mpj_stage1_panel(64, 3, p, p, p, 0, None) == mpj.MPJ_EINVAL
+    assert L.mpj_stage1_panel(64, 0, p, p, p, 4, None) == mpj.MPJ_EINVAL
+    assert L.mpj_stage1_panel(512, 0, p, p, p, 2, None) == mpj.MPJ_EINVAL
+    assert L.mpj_stage1_panel(64, 0, p, p, p, 1, None) == mpj.MPJ_EINVAL  # transposing in place
+    # allocation-free sweeps: too large before any device work
+    big = 8193
+    z = ctypes.c_double(0.0)
+    assert L.mpj_jacobi64_noalloc(big, p, big, p, big, z, 1, 0, None, None, None) == -9  # MPJ_ETOOLARGE
+    assert L.mpj_jacobi64_noalloc(4, p, 4, p, 4, z, 5, 0, None, None, None) == mpj.MPJ_EINVAL
+    # batched: sizes outside [1, 256]
+    n_bad = (ctypes.c_int * 2)(3, 300)
+    assert L.mpj_syev_batched(2, n_bad, p, p, p, 0.0, None, None) == mpj.MPJ_EINVAL
+    assert L.mpj_syev_batched(0, None, None, None, None, 0.0, None, None) == 0
+
+
+def test_bench_reference_arm_contract():
+    """bench.py --impl reference prints one JSON line with the contract's keys
+    (the oracle timed on bounded samples; no GPU involved)."""
+    import json
+    import subprocess
+    import sys
+    out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
+                          "--warmup", "0", "--ref-step-seconds", "0.5"], capture_output=True, text=True,
+                         timeout=600, cwd=ROOT)
+    assert out.returncode == 0, out.stderr[-2000:]
+    lines = [l for l in out.stdout.splitlines() if l.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    for k in ["metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better", "scaling",
+              "dtype", "data", "config", "impl", "cpu_baseline", "e2e"]:
+        assert k in d, k
+    assert d["impl"] == "reference" and d["value"] > 0 and d["higher_is_better"] is True
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
+    assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["value"] == d["value"]
