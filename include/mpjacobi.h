@@ -220,6 +220,21 @@ int mpj_jacobi64_noalloc(int n, double* A_dev, int lda, double* V_dev, int ldv, 
 int mpj_dgemm(char transa, char transb, int m, int n, int k, double alpha, const double* A_dev, int lda,
               const double* B_dev, int ldb, double beta, double* C_dev, int ldc, void* stream);
 
+/* FP64 matrix product on the tcgen05 tensor cores (not in the paper; the
+ * paper's products are FP64): C = alpha op(A) op(B) + beta C with the same
+ * arguments as mpj_dgemm (m, n, k >= 1).  Each row of op(A) and column of
+ * op(B) is split on the grid of its largest exponent into 8 slices of 7 bits
+ * held exactly as bf16; slice products are summed exactly in the tensor cores'
+ * FP32 accumulators over chunks of 256 values of k (all partial sums are
+ * integers below 2^23 in their level's unit) and the chunks in FP64.  The
+ * error is within a small multiple of k 2^-53 max|op(A)(r,:)| max|op(B)(:,c)|
+ * per entry.  Allocates about 16 (m + n) k bytes of scratch with
+ * cudaMallocAsync; synchronizes the stream.  Returns MPJ_EINVAL, MPJ_ENOMEM,
+ * MPJ_ETIMEOUT (the tensor cores did not signal completion within about 2 s)
+ * or MPJ_ECUDA on failure. */
+int mpj_dgemm_tc(char transa, char transb, int m, int n, int k, double alpha, const double* A_dev, int lda,
+                 const double* B_dev, int ldb, double beta, double* C_dev, int ldc, void* stream);
+
 /* One product of the stage-1 blocked update on the tcgen05 tensor cores
  * (3xTF32; the stage is the approximate eigenvector step of Sec. 4.1, and the
  * paper has no blocked form of it).  N: a multiple of 32; block round R in

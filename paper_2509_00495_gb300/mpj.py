@@ -95,6 +95,7 @@ def lib():
         L.mpj_jacobi64.argtypes = [_i, _vp, _i, _vp, _i, _d, _i, _i, _ip, _dp, _vp]
         L.mpj_dgemm.argtypes = [ctypes.c_char, ctypes.c_char, _i, _i, _i, _d, _vp, _i, _vp, _i, _d, _vp, _i, _vp]
         L.mpj_stage1_panel.argtypes = [_i, _i, _vp, _vp, _vp, _i, _vp]
+        L.mpj_dgemm_tc.argtypes = [ctypes.c_char, ctypes.c_char, _i, _i, _i, _d, _vp, _i, _vp, _i, _d, _vp, _i, _vp]
         if hasattr(L, "mpj_syev_batched"):
             L.mpj_syev_batched.argtypes = [_i, _ip, _vp, _vp, _vp, _d, _ip, _vp]
             L.mpj_batched_group_size.argtypes = [_i, _ip]
@@ -251,6 +252,23 @@ def dgemm(transa: str, transb: str, alpha: float, A: torch.Tensor, B: torch.Tens
     st = lib().mpj_dgemm(transa.encode(), transb.encode(), m, n, k, alpha, _ptr(At), max(A.shape[0], 1), _ptr(Bt),
                          max(B.shape[0], 1), beta, _ptr(Ct), max(m, 1), _stream())
     _check(st, "mpj_dgemm")
+    return Ct.T
+
+
+def dgemm_tc(transa: str, transb: str, alpha: float, A: torch.Tensor, B: torch.Tensor, beta: float = 0.0,
+             C: torch.Tensor | None = None) -> torch.Tensor:
+    """mpj_dgemm_tc (FP64 product on the tensor cores from exact bf16 slices),
+    with the numpy-like semantics of dgemm."""
+    A = _dev(A, "A")
+    B = _dev(B, "B")
+    At, Bt = A.T.contiguous(), B.T.contiguous()  # column-major buffers
+    m = A.shape[1] if transa == "T" else A.shape[0]
+    k = A.shape[0] if transa == "T" else A.shape[1]
+    n = B.shape[0] if transb == "T" else B.shape[1]
+    Ct = (torch.zeros(n, m, dtype=torch.float64, device=A.device) if C is None else _dev(C, "C").T.contiguous())
+    st = lib().mpj_dgemm_tc(transa.encode(), transb.encode(), m, n, k, alpha, _ptr(At), max(A.shape[0], 1),
+                            _ptr(Bt), max(B.shape[0], 1), beta, _ptr(Ct), max(m, 1), _stream())
+    _check(st, "mpj_dgemm_tc")
     return Ct.T
 
 

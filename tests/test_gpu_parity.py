@@ -541,3 +541,24 @@ def test_side_stream_overlap_is_bitwise_neutral(tmp_path):
         subprocess.run([_sys.executable, str(script), root, str(out)], check=True, env=env, timeout=300)
         outs.append(np.load(out))
     assert np.array_equal(outs[0], outs[1])
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("m,n,k,ta,tb", [(64, 64, 64, "N", "N"), (130, 70, 300, "N", "N"), (200, 129, 513, "T", "N"),
+                                         (96, 200, 256, "N", "T"), (257, 65, 1000, "T", "T")])
+def test_dgemm_tc_matches_numpy(m, n, k, ta, tb):
+    """The tensor-core FP64 product (exact bf16 slices) within the FP64 product's
+    componentwise error bound, on tiles, ragged edges and every transpose."""
+    rng = np.random.default_rng(m * 5 + n * 11 + k)
+    A = rng.standard_normal((k, m) if ta == "T" else (m, k))
+    B = rng.standard_normal((n, k) if tb == "T" else (k, n))
+    C0 = rng.standard_normal((m, n))
+    opA = A.T if ta == "T" else A
+    opB = B.T if tb == "T" else B
+    got = host(mpj().dgemm_tc(ta, tb, 0.75, dev(A), dev(B), -1.5, dev(C0)))
+    ref = 0.75 * opA @ opB - 1.5 * C0
+    bound = 2 * (k + 2) * U * (0.75 * np.abs(opA) @ np.abs(opB) + 1.5 * np.abs(C0))
+    assert np.all(np.abs(got - ref) <= bound)
+    # and much closer than the bound: an exact-slice product errs by a few units
+    # of the output's last place, not by k of them
+    assert np.abs(got - ref).max() <= 64 * U * (np.abs(opA) @ np.abs(opB)).max()
