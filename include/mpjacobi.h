@@ -183,10 +183,12 @@ int mpj_syev_backward(int batch, int n, const double* W_dev, const double* Q_dev
 int mpj_stage1(int n, const double* A_dev, int lda, double* Ql_dev, int ldq, double tol32, int max_sweeps,
                int* sweeps, double* off32, void* stream);
 
-/* Newton-Schulz in place: X <- X (3I - X^T X)/2, `steps` times (Sec. 4.3.4). */
+/* Newton-Schulz in place: X <- X (3I - X^T X)/2, `steps` times (Sec. 4.3.4);
+ * products as in the solve (tensor cores unless MPJ_GEMM_TC=0). */
 int mpj_newton_schulz(int n, double* X_dev, int ldx, int steps, void* stream);
 
-/* Preconditioning: Ac = Qd^T A Qd (Alg. 9 step 3); Ac is written symmetric. */
+/* Preconditioning: Ac = Qd^T A Qd (Alg. 9 step 3); Ac is written symmetric.
+ * This stage entry point always uses the FP64 DMMA kernel. */
 int mpj_precondition(int n, const double* A_dev, int lda, const double* Qd_dev, int ldq, double* Ac_dev, int ldc,
                      void* stream);
 
