@@ -236,7 +236,7 @@ int mpj_dgemm(char transa, char transb, int m, int n, int k, double alpha, const
  * op(B) is split on the grid of its largest exponent into 8 slices of 7 bits
  * held exactly as bf16; slice products are summed exactly in the tensor cores'
  * FP32 accumulators over chunks of 256 values of k (all partial sums are
- * integers below 2^23 in their level's unit) and the chunks in FP64.  The
+ * integers below 2^24 in their level's unit) and the chunks in FP64.  The
  * error is within a small multiple of k 2^-53 max|op(A)(r,:)| max|op(B)(:,c)|
  * per entry.  Allocates about 16 (m + n) k bytes of scratch with
  * cudaMallocAsync; synchronizes the stream.  Returns MPJ_EINVAL, MPJ_ENOMEM,

@@ -10,9 +10,9 @@
 // same for each column c of op(B) with exponents f_c.  Then
 //   (op(A) op(B))_rc = sum_L 2^(e_r + f_c - 7 L) sum_{i+j=L} sum_k q_i(r,k) q_j(k,c)
 // for levels L = 2..9 (the dropped levels are below 2^-57 relative).  Over a
-// chunk of 256 values of k every level sum is an integer below 2^23, so the
-// tensor cores' FP32 accumulation of the bf16 products is exact whatever its
-// rounding; each chunk's level sums are read back from tensor memory,
+// chunk of 256 values of k every level sum (and every partial sum of it) is
+// an integer below 2^24 (at most 2^23.33 for the top levels), so the tensor
+// cores' FP32 accumulation of the bf16 products is exact whatever its rounding; each chunk's level sums are read back from tensor memory,
 // converted to FP64 exactly and accumulated in FP64.
 //
 // Layout of the slices in global memory: for slice s and a tile of TR rows
