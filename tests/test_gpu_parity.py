@@ -562,3 +562,41 @@ def test_dgemm_tc_matches_numpy(m, n, k, ta, tb):
     # and much closer than the bound: an exact-slice product errs by a few units
     # of the output's last place, not by k of them
     assert np.abs(got - ref).max() <= 64 * U * (np.abs(opA) @ np.abs(opB)).max()
+
+
+_ENGINE_SCRIPT = r"""
+import sys, numpy as np, torch
+sys.path.insert(0, sys.argv[1])
+from paper_2509_00495_gb300 import inputs, mpj
+A, lam = inputs.geo_matrix(300, 1e6, seed=11)
+r = mpj.syev_ex(torch.from_numpy(A).cuda())
+torch.cuda.synchronize()
+assert r.status == 0
+np.save(sys.argv[2], np.concatenate([r.W.cpu().numpy()[None, :], r.Q.cpu().numpy()]))
+"""
+
+
+@pytest.mark.gpu
+def test_gemm_engines_agree(tmp_path):
+    """The FP64 products on the tensor cores (default) and on the DMMA kernel
+    (MPJ_GEMM_TC=0) both give an FP64-accurate solve with the same spectrum."""
+    import os
+    import subprocess
+    import sys as _sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    script = tmp_path / "run.py"
+    script.write_text(_ENGINE_SCRIPT)
+    A, lam = inputs.geo_matrix(300, 1e6, seed=11)
+    res = []
+    for flag in ("1", "0"):
+        out = tmp_path / f"wq{flag}.npy"
+        env = dict(os.environ, MPJ_GEMM_TC=flag)
+        subprocess.run([_sys.executable, str(script), root, str(out)], check=True, env=env, timeout=300)
+        wq = np.load(out)
+        W, Q = wq[0], wq[1:]
+        be, orF = triple(A, W, Q)
+        assert be <= 4 and orF <= 4, (flag, be, orF)
+        res.append(W)
+    nA = np.linalg.norm(A, 2)
+    assert np.abs(res[0] - res[1]).max() <= 1e-12 * nA
+    assert np.abs(res[0] - np.sort(lam)).max() <= 1e-12 * nA
