@@ -36,11 +36,36 @@ METRIC = "n=4096 FP64-accurate eig solves/s, mixed vs plain FP64 Jacobi, same GB
 UNIT = "solves/s"
 U_D = 2.0 ** -53
 FP64_PEAK_TFLOPS = 1.25  # nominal GB300 FP64 (152 SMs x 2 FP64 FMA/clk x 2 flop x ~2.07 GHz)
-# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum, one ncu capture each)
-# of one FP64 round at n = 4096: rr_step64 67.8 + 78.2 MB, plus 1/64 of a 64-round
-# v_apply_rounds launch (137.0 + 79.2 MB).  Valid for these kernel versions only.
-TRAFFIC_PER_ROUND_N4096 = 67.84e6 + 78.23e6 + (136.99e6 + 79.17e6) / 64
+# DRAM bytes of one FP64 round at n = 4096 come from the committed ncu summary
+# of the sweep kernels (a "traffic_bytes_per_round:" line), taken on the kernel
+# versions the summary names; see traffic_per_round().
+TRAFFIC_PROFILE = os.path.join(ROOT, "profiles", "rr_step64_geo4096.md")
+# Sweep counts of the GPU arm on this input (FP32 stage, FP64 sweeps), used by
+# the reference arm only while no full oracle run is recorded.
+GPU_ARM_SWEEPS = (9, 11)
 WORKLOAD = "geo4096: one symmetric FP64 matrix n=4096, |lam| geometric in [1e-6,1] (condition 1e6), random signs, Haar eigenvectors, seed 0"
+
+
+def traffic_per_round() -> float | None:
+    """dram__bytes_read.sum + dram__bytes_write.sum of one round (rr_step64 plus
+    1/64 of a v_apply_rounds launch) from the ncu summary in profiles/."""
+    try:
+        for line in open(TRAFFIC_PROFILE):
+            if line.strip().startswith("traffic_bytes_per_round:"):
+                return float(line.split(":", 1)[1].split()[0])
+    except OSError:
+        return None
+    return None
+
+
+def oracle_record(which: str) -> dict | None:
+    """The oracle's full run on the n = 4096 input (oracle/record_geo4096.py)."""
+    path = os.path.join(ROOT, "oracle", f"geo4096_{which}.json")
+    try:
+        with open(path) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return None
 
 
 # ---------------------------------------------------------------- clocks
@@ -139,6 +164,18 @@ def cpu_baseline_estimate(A: np.ndarray, sweeps32: int, sweeps64: int, budget_s:
             "seconds_per_solve": T, "t_rot32_s": t32, "t_rot64_s": t64, "t_flop_s": tflop}
 
 
+def oracle_sweep_counts(fallback: tuple[int, int] | None = None) -> tuple[int, int, str]:
+    """The oracle's own sweep counts on the n = 4096 input (FP32 cyclic stage,
+    FP64 cyclic sweeps), from its full run recorded by oracle/record_geo4096.py;
+    without that record, `fallback` (labelled as such)."""
+    rec = oracle_record("mixed")
+    if rec is not None:
+        return int(rec["sweeps32"]), int(rec["sweeps64"]), "the oracle's full n=4096 run (oracle/geo4096_mixed.json)"
+    if fallback is None:
+        raise SystemExit("oracle/geo4096_mixed.json missing: run oracle/record_geo4096.py mixed")
+    return fallback[0], fallback[1], "GPU arm's sweep counts (no full oracle run recorded)"
+
+
 def run_reference(args) -> None:
     """--impl reference: the CPU oracle as it stands, timed on the host."""
     rank = int(os.environ.get("RANK", "0"))
@@ -146,8 +183,7 @@ def run_reference(args) -> None:
         return
     from paper_2509_00495_gb300 import inputs
     A, lam = inputs.geo_4096(seed=0)
-    # the GPU arm's sweep counts on this input (measured): stage 1 and FP64 sweeps
-    s32, s64 = args.ref_sweeps32, args.ref_sweeps64
+    s32, s64, _src = oracle_sweep_counts(GPU_ARM_SWEEPS)
     for _ in range(args.warmup):
         cpu_baseline_estimate(A, s32, s64, budget_s=2.0)
     vals, t0 = [], time.perf_counter()
@@ -168,6 +204,30 @@ def run_reference(args) -> None:
     print(json.dumps(line), flush=True)
 
 
+def oracle_full_runs() -> dict:
+    """The oracle run in full: the n = 96 solve of the small geometric case,
+    timed here on one host core, and the recorded full n = 4096 runs."""
+    import oracle
+    from paper_2509_00495_gb300 import inputs
+    A, lam = inputs.small_geo(seed=0)
+    t0 = time.perf_counter()
+    reps = 0
+    while True:
+        W, Q, info = oracle.syev_mixed(A)
+        reps += 1
+        if time.perf_counter() - t0 > 1.0:
+            break
+    t96 = (time.perf_counter() - t0) / reps
+    out = {"n96_mixed": {"seconds_per_solve": t96, "solves_per_s": 1.0 / t96, "sweeps32": info.sweeps32,
+                         "sweeps64": info.sweeps64, "cores": 1}}
+    for which in ("mixed", "plain"):
+        rec = oracle_record(which)
+        if rec is not None:
+            out[f"n4096_{which}_recorded"] = {k: rec[k] for k in ("sweeps32", "sweeps64", "wall_seconds", "machine")
+                                              if k in rec}
+    return out
+
+
 # ---------------------------------------------------------------- GPU arm
 def main():
     ap = argparse.ArgumentParser()
@@ -182,8 +242,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end timing")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--ref-step-seconds", type=float, default=8.0)
-    ap.add_argument("--ref-sweeps32", type=int, default=8)
-    ap.add_argument("--ref-sweeps64", type=int, default=6)
+    ap.add_argument("--plain-solves", type=int, default=3)
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
@@ -319,7 +378,7 @@ def main():
         out["roofline"] = {"kernel": "rr_step64+v_apply_rounds (one round)", "bound": "alu", "achieved": achieved,
                            "peak": FP64_PEAK_TFLOPS,
                            "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
-                           "traffic": TRAFFIC_PER_ROUND_N4096 if n == 4096 else None,
+                           "traffic": traffic_per_round() if n == 4096 else None,
                            "peak_source": "nominal FP64 of the recipe table (not in MEASURED_PEAKS.json)",
                            "algorithmic_flops_per_launch": flops, "avg_launch_ms": avg_launch_s * 1e3,
                            "dominant_stage": dominant,
@@ -334,18 +393,25 @@ def main():
                             "fp64_pipe_peak": FP64_PEAK_TFLOPS, "stages": "newton_schulz + transform"}
 
     if rank == 0 and not args.no_plain:
-        torch.cuda.synchronize()
-        e_a = torch.cuda.Event(enable_timing=True)
-        e_b = torch.cuda.Event(enable_timing=True)
-        e_a.record()
-        rp = mpj.syev_ex(A, workspace=ws, method="plain")
-        e_b.record()
-        e_b.synchronize()
-        ms_plain = e_a.elapsed_time(e_b)
+        # the metric's denominator: plain FP64 Jacobi from V = I on the same input and
+        # sweep kernels, timed like the mixed arm (L2 flushed before each solve), median of 3
+        ms_p = []
+        for _ in range(args.plain_solves):
+            flush.zero_()
+            torch.cuda.synchronize()
+            e_a = torch.cuda.Event(enable_timing=True)
+            e_b = torch.cuda.Event(enable_timing=True)
+            e_a.record()
+            rp = mpj.syev_ex(A, workspace=ws, method="plain")
+            e_b.record()
+            e_b.synchronize()
+            ms_p.append(e_a.elapsed_time(e_b))
+        ms_plain = statistics.median(ms_p)
         with torch.no_grad():
             bep = (torch.linalg.norm(A - (rp.Q * rp.W) @ rp.Q.T) / torch.linalg.norm(A)).item() / (n * U_D)
             orp = torch.linalg.norm(rp.Q.T @ rp.Q - torch.eye(n, dtype=torch.float64, device=dev)).item() / (n * U_D)
-        out["plain"] = {"ms_per_solve": ms_plain, "sweeps64": rp.info["sweeps64"], "status": rp.status,
+        out["plain"] = {"ms_per_solve": ms_plain, "solves": len(ms_p), "ms_all": [round(x, 1) for x in ms_p],
+                        "sweeps64": rp.info["sweeps64"], "status": rp.status,
                         "backward_err_over_nu": bep, "orth_fro_over_nu": orp}
         out["speedup_vs_plain"] = ms_plain / ms_mixed
 
@@ -373,11 +439,31 @@ def main():
                               "backward_err_over_nu": be2, "orth_fro_over_nu": or2}
         if "plain" in out:
             out["mixed_2pass"]["speedup_vs_plain"] = out["plain"]["ms_per_solve"] / min(ms2)
+        # the paper's own ordering (cyclic-by-row, Sec. 3.3) for the FP64 sweeps, one solve
+        ws_c = ws
+        flush.zero_()
+        torch.cuda.synchronize()
+        e_a = torch.cuda.Event(enable_timing=True)
+        e_b = torch.cuda.Event(enable_timing=True)
+        e_a.record()
+        rc = mpj.syev_ex(A, workspace=ws_c, ordering="cyclic")
+        e_b.record()
+        e_b.synchronize()
+        with torch.no_grad():
+            bec = (torch.linalg.norm(A - (rc.Q * rc.W) @ rc.Q.T) / torch.linalg.norm(A)).item() / (n * U_D)
+            orc = torch.linalg.norm(rc.Q.T @ rc.Q - torch.eye(n, dtype=torch.float64, device=dev)).item() / (n * U_D)
+        out["mixed_cyclic"] = {"ms_per_solve": e_a.elapsed_time(e_b), "status": rc.status,
+                               "sweeps": {"stage1_fp32": rc.info["sweeps32"], "fp64": rc.info["sweeps64"]},
+                               "stage_ms": [round(x, 3) for x in rc.info["ms_stage"]],
+                               "backward_err_over_nu": bec, "orth_fro_over_nu": orc,
+                               "ordering": "cyclic-by-row (the paper's), run as wavefronts of pairs with equal p+q"}
         out["extras"] = extras(mpj, torch, dev, inputs)
 
     if rank == 0 and world == 1 and not args.no_cpu:
-        out["cpu_baseline"] = cpu_baseline_estimate(A_np, info["sweeps32"], info["sweeps64"], args.cpu_seconds)
+        s32, s64, _src = oracle_sweep_counts(GPU_ARM_SWEEPS)
+        out["cpu_baseline"] = cpu_baseline_estimate(A_np, s32, s64, args.cpu_seconds)
         out["cpu_baseline"]["note"] = "a baseline, not the target"
+        out["cpu_baseline"]["full_runs"] = oracle_full_runs()
 
     if rank == 0:
         print(json.dumps(out), flush=True)

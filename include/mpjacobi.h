@@ -39,10 +39,8 @@
  *                         cores (3xTF32; slower on GB300, off by default);
  *   MPJ_GEMM_TC=0         run the Newton-Schulz and Q_d^T A Q_d products on
  *                         the FP64 DMMA kernel instead of the tensor cores
- *                         (mpj_dgemm_tc, the default; it takes stream-ordered
- *                         scratch of its own with cudaMallocAsync, also when a
- *                         caller workspace is given, about 16 n^2 bytes per
- *                         operand);
+ *                         (the exact bf16-slice products of mpj_dgemm_tc, the
+ *                         default);
  *   MPJ_AUTOTUNE_CACHE=f  file that keeps the batched group-size choices;
  *   MPJ_BATCHED_GROUP=g   fix the batched group size (256, 512 or 1024).
  */
@@ -118,6 +116,12 @@ const char* mpj_last_cuda_error(void);
  * loaded (all threads).  The difference around a call counts its launches. */
 long long mpj_kernel_launches(void);
 
+/* Diagnostic: number of device (and pinned host) allocations this library has
+ * made since it was loaded (all threads; cudaMalloc, cudaMallocAsync,
+ * cudaMallocHost).  The difference around a call counts its allocations: zero
+ * for mpj_syev_ex with a caller workspace. */
+long long mpj_device_allocations(void);
+
 /* Bytes of device workspace mpj_syev_ex needs for size n under `o` (NULL: defaults). */
 size_t mpj_syev_workspace(int n, const mpj_opts* o);
 
@@ -131,9 +135,13 @@ int mpj_syev(int n, const double* A_dev, int lda, double* W_dev, double* Q_dev, 
 
 /* Same with explicit options, output leading dimension, optional host `info`
  * (may be NULL) and optional caller workspace (work_dev may be NULL: then the
- * library allocates; else work_bytes >= mpj_syev_workspace(n, o)).  The
- * tensor-core products of the mixed method allocate their slice scratch
- * stream-ordered in either case (MPJ_GEMM_TC=0 avoids it). */
+ * library allocates it with cudaMallocAsync and frees it before returning;
+ * else work_bytes >= mpj_syev_workspace(n, o) and the call allocates nothing:
+ * every buffer, including the sliced operands of the tensor-core products,
+ * is carved from work_dev).  Synchronizes `stream` once per sweep (to read
+ * off(A)) and at the end; device-side conditions (a tensor-core completion
+ * wait that ran out: MPJ_ETIMEOUT) are read at the final synchronization.
+ * Returns MPJ_EWORKSPACE if work_bytes is too small. */
 int mpj_syev_ex(int n, const double* A_dev, int lda, double* W_dev, double* Q_dev, int ldq, const mpj_opts* o,
                 mpj_info* info, void* work_dev, size_t work_bytes, void* stream);
 
@@ -187,8 +195,10 @@ int mpj_stage1(int n, const double* A_dev, int lda, double* Ql_dev, int ldq, dou
  * products as in the solve (tensor cores unless MPJ_GEMM_TC=0). */
 int mpj_newton_schulz(int n, double* X_dev, int ldx, int steps, void* stream);
 
-/* Preconditioning: Ac = Qd^T A Qd (Alg. 9 step 3); Ac is written symmetric.
- * This stage entry point always uses the FP64 DMMA kernel. */
+/* Preconditioning: Ac = Qd^T A Qd (Alg. 9 step 3); Ac is written exactly
+ * symmetric (lower triangle mirrored).  Products as in the solve: the
+ * tensor-core exact-slice engine unless MPJ_GEMM_TC=0 selects the FP64 DMMA
+ * kernel.  Allocates its scratch with cudaMallocAsync; synchronizes. */
 int mpj_precondition(int n, const double* A_dev, int lda, const double* Qd_dev, int ldq, double* Ac_dev, int ldc,
                      void* stream);
 
@@ -236,12 +246,14 @@ int mpj_dgemm(char transa, char transb, int m, int n, int k, double alpha, const
  * op(B) is split on the grid of its largest exponent into 8 slices of 7 bits
  * held exactly as bf16; slice products are summed exactly in the tensor cores'
  * FP32 accumulators over chunks of 256 values of k (all partial sums are
- * integers below 2^24 in their level's unit) and the chunks in FP64.  The
- * error is within a small multiple of k 2^-53 max|op(A)(r,:)| max|op(B)(:,c)|
- * per entry.  Allocates about 16 (m + n) k bytes of scratch with
- * cudaMallocAsync; synchronizes the stream.  Returns MPJ_EINVAL, MPJ_ENOMEM,
- * MPJ_ETIMEOUT (the tensor cores did not signal completion within about 2 s)
- * or MPJ_ECUDA on failure. */
+ * integers below 2^24 in their level's unit) and the chunks exactly in 64-bit
+ * integers; the result is rounded once to FP64 and scaled by 2^(e_r + f_c)
+ * in one step (no intermediate underflow).  The error is within a small
+ * multiple of 2^-53 (|op(A)| |op(B)|)_rc plus k 2^-54 max|op(A)(r,:)|
+ * max|op(B)(:,c)| per entry.  Allocates about 16 (m + n) k bytes of scratch
+ * with cudaMallocAsync; synchronizes the stream.  Returns MPJ_EINVAL,
+ * MPJ_ENOMEM, MPJ_ETIMEOUT (the tensor cores did not signal completion within
+ * about 2 s) or MPJ_ECUDA on failure. */
 int mpj_dgemm_tc(char transa, char transb, int m, int n, int k, double alpha, const double* A_dev, int lda,
                  const double* B_dev, int ldb, double beta, double* C_dev, int ldc, void* stream);
 

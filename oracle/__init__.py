@@ -69,13 +69,14 @@ _d = ctypes.c_double
 class _Opts(ctypes.Structure):
     _fields_ = [("tol", _d), ("tol32", _d), ("skip_tol", _d), ("skip_tol32", _d),
                 ("max_sweeps64", _i), ("max_sweeps32", _i), ("ns_steps", _i),
-                ("ordering32", _i), ("ordering64", _i), ("polish", _i), ("sort", _i), ("threshold", _i)]
+                ("ordering32", _i), ("ordering64", _i), ("polish", _i), ("sort", _i), ("threshold", _i),
+                ("precond_passes", _i)]
 
 
 class _Info(ctypes.Structure):
     _fields_ = [("sweeps32", _i), ("sweeps64", _i), ("capped32", _i), ("capped64", _i),
                 ("rotations32", ctypes.c_longlong), ("rotations64", ctypes.c_longlong),
-                ("normA_fro", _d), ("off32", _d), ("off_cond", _d), ("off_final", _d)]
+                ("normA_fro", _d), ("off32", _d), ("off_cond", _d), ("off_final", _d), ("sweeps32_pass2", _i)]
 
 
 def _declare(L):
@@ -133,17 +134,19 @@ class Info:
     off32: float
     off_cond: float
     off_final: float
+    sweeps32_pass2: int = 0
 
 
 def _info(ci: _Info) -> Info:
     return Info(ci.sweeps32, ci.sweeps64, bool(ci.capped32), bool(ci.capped64), ci.rotations32,
-                ci.rotations64, ci.normA_fro, ci.off32, ci.off_cond, ci.off_final)
+                ci.rotations64, ci.normA_fro, ci.off32, ci.off_cond, ci.off_final, ci.sweeps32_pass2)
 
 
 def _opts(n, tol=0.0, tol32=0.0, skip_tol=0.0, skip_tol32=0.0, max_sweeps64=0, max_sweeps32=0, ns_steps=0,
-          ordering32=CYCLIC, ordering64=CYCLIC, polish=False, sort=True, threshold=False) -> _Opts:
+          ordering32=CYCLIC, ordering64=CYCLIC, polish=False, sort=True, threshold=False,
+          precond_passes=1) -> _Opts:
     return _Opts(tol, tol32, skip_tol, skip_tol32, max_sweeps64, max_sweeps32, ns_steps, ordering32, ordering64,
-                 int(polish), int(sort), int(threshold))
+                 int(polish), int(sort), int(threshold), int(precond_passes))
 
 
 # ---------------------------------------------------------------- primitives
@@ -289,7 +292,10 @@ def stage1(A, **kw):
 
 
 def syev_mixed(A, *, return_intermediates=False, **kw):
-    """Algorithm 9 with an FP32 Jacobi stage 1.  Returns (W, Q, Info[, dict of Q_l, Q_d, A_cond])."""
+    """Algorithm 9 with an FP32 Jacobi stage 1.  Returns (W, Q, Info[, dict of Q_l, Q_d, A_cond]).
+
+    precond_passes=2 applies stages 1-3 a second time to A_cond before the
+    FP64 sweeps (not in the paper; see orc_syev_mixed)."""
     a = _f64(A)
     n = a.shape[0]
     W = np.zeros(n)

@@ -469,12 +469,15 @@ typedef struct {
   int polish;       /* 1: one more Newton-Schulz step on the final Q             */
   int sort;         /* 1: sort W ascending, permute Q's columns to match        */
   int threshold;    /* 1: FP64 sweeps also skip pairs with |a_pq| <= tol / n     */
+  int precond_passes; /* 2: Algorithm 9's stages 1-3 applied a second time to
+                         A_cond before the FP64 sweeps (not in the paper)        */
 } orc_opts;
 
 typedef struct {
   int sweeps32, sweeps64, capped32, capped64;
   long long rotations32, rotations64;
   double normA_fro, off32, off_cond, off_final;
+  int sweeps32_pass2;
 } orc_info;
 
 static void sort_eig(int n, double* W, double* Q, int ldq) {
@@ -546,7 +549,8 @@ int orc_stage1(int n, const double* A, int lda, double* Ql, int ldq, const orc_o
  *   1. Q_l from stage 1;  2. Q_d = newton_schulz(Q_l);
  *   3. A_cond = Q_d^T A Q_d;  4. FP64 Jacobi on A_cond from V = I;
  *   5. W = diag(A_cond after the sweeps), Q = Q_d V  (optionally polished, sorted).
- * Intermediates (each n x n, may be NULL): Ql_out, Qd_out, Acond_out.
+ * Intermediates (each n x n, may be NULL): Ql_out, Qd_out, Acond_out (with
+ * two passes: Q_d = Q_d1 Q_d2 and the second A_cond).
  * Returns 0, or 1 when the FP64 stage hit its sweep cap.                     */
 int orc_syev_mixed(int n, const double* A, int lda, double* W, double* Q, int ldq, const orc_opts* o, orc_info* info,
                    double* Ql_out, double* Qd_out, double* Acond_out) {
@@ -560,8 +564,32 @@ int orc_syev_mixed(int n, const double* A, int lda, double* W, double* Q, int ld
   orc_stage1(n, A, lda, X, n, &d, info, NULL);
   if (Ql_out) memcpy(Ql_out, X, sizeof(double) * (size_t)n * n);
   orc_newton_schulz_d(n, X, n, d.ns_steps);
-  if (Qd_out) memcpy(Qd_out, X, sizeof(double) * (size_t)n * n);
   orc_precondition_d(n, A, lda, X, n, Ac, n);
+  if (d.precond_passes >= 2) {
+    /* Second pass (not in the paper): stages 1-3 once more, on A_cond.  Its
+     * FP32 rounding is relative to A_cond's own entries, so the FP32 Jacobi
+     * separates eigenvalues that stage 1 on A could not.  Reading: stage 1 of
+     * this pass stops at off(A32) <= n 2^-24 off(A_cond) or after
+     * min(max_sweeps32, 8) sweeps; Q_d = Q_d1 Q_d2 and
+     * A_cond <- Q_d2^T A_cond Q_d2.                                          */
+    orc_opts d2 = d;
+    orc_info i2;
+    memset(&i2, 0, sizeof i2);
+    d2.tol32 = (double)n * ldexp(1.0, -24) * orc_off_d(n, Ac, n);
+    d2.max_sweeps32 = d.max_sweeps32 < 8 ? d.max_sweeps32 : 8;
+    double* X2 = (double*)malloc(sizeof(double) * (size_t)n * n);
+    double* T = (double*)malloc(sizeof(double) * (size_t)n * n);
+    orc_stage1(n, Ac, n, X2, n, &d2, &i2, NULL);
+    info->sweeps32_pass2 = i2.sweeps32;
+    orc_newton_schulz_d(n, X2, n, d.ns_steps);
+    orc_precondition_d(n, Ac, n, X2, n, T, n);
+    memcpy(Ac, T, sizeof(double) * (size_t)n * n);
+    orc_gemm_nn_d(n, n, n, X, n, X2, n, T, n);
+    memcpy(X, T, sizeof(double) * (size_t)n * n);
+    free(X2);
+    free(T);
+  }
+  if (Qd_out) memcpy(Qd_out, X, sizeof(double) * (size_t)n * n);
   if (Acond_out) memcpy(Acond_out, Ac, sizeof(double) * (size_t)n * n);
   info->off_cond = orc_off_d(n, Ac, n);
   for (int j = 0; j < n; ++j)

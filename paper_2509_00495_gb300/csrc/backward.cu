@@ -54,6 +54,7 @@ extern "C" int mpj_syev_backward(int batch, int n, const double* W, const double
   void* w = nullptr;
   size_t bytes = 2 * (size_t)batch * sq * sizeof(double) + 256;
   if (cudaMallocAsync(&w, bytes, s) != cudaSuccess) return MPJ_ENOMEM;
+  mpj_count_alloc();
   double* M = (double*)w;
   double* T = M + (size_t)batch * sq;
   unsigned* flags = (unsigned*)(T + (size_t)batch * sq);

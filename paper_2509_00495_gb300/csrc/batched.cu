@@ -670,8 +670,11 @@ extern "C" int mpj_syev_batched(int batch, const int* n_host, const double* cons
     plan->tol = tol;
     plan->grid = grid;
     cudaError_t e = cudaMalloc(&plan->work, L.total);
+    mpj_count_alloc();
     if (e == cudaSuccess) e = cudaMallocHost((void**)&plan->h_sweeps, sizeof(int) * (size_t)batch);
     if (e == cudaSuccess) e = cudaMallocHost((void**)&plan->h_flags, sizeof(unsigned));
+    mpj_count_alloc();
+    mpj_count_alloc();
     if (e != cudaSuccess) {
       mpj_set_cuda_error(e, "batched plan allocation", __LINE__);
       free_plan(plan);

@@ -177,3 +177,6 @@ MPJ_DEV float ld_cg(const float* p) { return __ldcg(p); }
 void mpj_set_cuda_error(cudaError_t e, const char* what, int line);
 // Counts every kernel this library enqueues (diagnostic, mpj_kernel_launches).
 void mpj_count_launch();
+// Counts every device (or pinned host) allocation the library makes
+// (diagnostic, mpj_device_allocations).
+void mpj_count_alloc();

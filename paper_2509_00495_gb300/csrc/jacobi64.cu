@@ -21,11 +21,11 @@
 //    Every 512 rounds and at the end of a sweep the scales are folded back
 //    into A and V (d = 1), which keeps d far from underflow.
 //  * cyclic-by-row (the paper's ordering, the faithful form): pairs
-//    (0,1),(0,2),...,(n-2,n-1) one after another, each applied as the paper's
-//    row update, then column update, then vector update, with the paper's
-//    formulas; (A + A^T)/2 after each sweep.  One CTA per matrix: every
-//    rotation depends on the previous one.  It exists for fidelity checks and
-//    is slow by construction.
+//    (0,1),(0,2),...,(n-2,n-1) in the paper's order, each applied as the
+//    paper's row update, then column update, then vector update, with the
+//    paper's formulas.  The sweep runs as 2n - 3 wavefronts of mutually
+//    independent rotations (pairs with equal p + q), which is the same
+//    rotation sequence (see cyc_wave_update).
 //
 // off(A) (Sec. 3.1, direct form) is reduced after every sweep with a fixed
 // reduction order, so repeated runs are bitwise identical.
@@ -523,59 +523,145 @@ __global__ void check_symmetric(const double* __restrict__ A, int lda, int n, un
       if (A[(size_t)j * lda + i] != A[(size_t)i * lda + j]) atomicOr(flags, MPJ_FLAG_NOTSYM);
 }
 
-// ---- cyclic-by-row, one CTA per matrix (the paper's ordering and update) ----
-__global__ void __launch_bounds__(1024) cyclic_sweep64(double* __restrict__ A, int lda, double* __restrict__ V,
-                                                       int ldv, int n, double skip, double skip_abs,
-                                                       int* __restrict__ rotated) {
-  __shared__ double cs[2];
-  __shared__ int go;
-  int any = 0;
-  for (int p = 0; p < n - 1; ++p)
-    for (int q = p + 1; q < n; ++q) {
-      if (threadIdx.x == 0) {
-        double app = A[(size_t)p * lda + p], aqq = A[(size_t)q * lda + q], apq = A[(size_t)q * lda + p];
-        go = 0;
-        if (fabs(apq) > skip * sqrt(fabs(app * aqq)) && fabs(apq) > skip_abs) {
-          // Algorithm 2, stable form (Appendix A approach 2)
-          double tau = (aqq - app) / (2.0 * apq);
-          double t = tau >= 0.0 ? 1.0 / (tau + sqrt(1.0 + tau * tau)) : 1.0 / (tau - sqrt(1.0 + tau * tau));
-          double c = 1.0 / sqrt(1.0 + t * t);
-          cs[0] = c;
-          cs[1] = t * c;
-          go = 1;
-        }
-      }
-      __syncthreads();
-      if (go) {
-        any = 1;
-        double c = cs[0], s = cs[1];
-        for (int k = threadIdx.x; k < n; k += blockDim.x) {  // rows: A([p q],:) = J^T A([p q],:)
-          double ap = A[(size_t)k * lda + p], aq = A[(size_t)k * lda + q];
-          A[(size_t)k * lda + p] = c * ap - s * aq;
-          A[(size_t)k * lda + q] = s * ap + c * aq;
-        }
-        __syncthreads();
-        for (int k = threadIdx.x; k < n; k += blockDim.x) {  // columns: A(:,[p q]) = A(:,[p q]) J
-          double ap = A[(size_t)p * lda + k], aq = A[(size_t)q * lda + k];
-          A[(size_t)p * lda + k] = c * ap - s * aq;
-          A[(size_t)q * lda + k] = s * ap + c * aq;
-          double vp = V[(size_t)p * ldv + k], vq = V[(size_t)q * ldv + k];
-          V[(size_t)p * ldv + k] = c * vp - s * vq;
-          V[(size_t)q * ldv + k] = s * vp + c * vq;
-        }
-      }
-      __syncthreads();
-    }
-  // A = (A + A^T)/2 after a sweep with a rotation
-  if (any) {
-    for (int j = 0; j < n; ++j)
-      for (int i = j + 1 + threadIdx.x; i < n; i += blockDim.x) {
-        double v = (A[(size_t)j * lda + i] + A[(size_t)i * lda + j]) / 2.0;
-        A[(size_t)j * lda + i] = v;
-        A[(size_t)i * lda + j] = v;
-      }
+// ---- cyclic-by-row as wavefronts (the paper's ordering and update) ----------
+// In the cyclic-by-row order (0,1),(0,2),...,(0,n-1),(1,2),...,(n-2,n-1) the
+// rotation of pair (p,q) depends only on the earlier rotations that touch p
+// or q.  Giving (p,q) the time t = p + q, those earlier rotations all have
+// smaller t, the later ones that touch p or q all have larger t, and the
+// pairs of one time t are disjoint (p + q = p' + q', p < p' forces q > q',
+// and p = q' or q = p' would contradict p < q, p' < q').  So the sweep runs
+// as 2n - 3 wavefronts t = 1 .. 2n-3 of the pairs (p, t - p),
+// p = max(0, t-n+1) .. (t-1)/2, applying exactly the paper's rotation
+// sequence; only the interleaving of commuting updates of disjoint pairs
+// changes.  Each rotation is Algorithm 2 with the paper's row update, then
+// column update, then vector update (J = [c s; -s c]).  An entry (i, j)
+// between two pairs a < b of one wavefront (i in a, j in b) becomes
+// ((J_a^T B) J_b)(i, j), B = A([p_a q_a], [p_b q_b]): the sequential algorithm
+// applies a's row update and then b's column update to it, and the mirror
+// entry gets the same value bit for bit, so both triangles stay equal.  A
+// pair's own 2 x 2 block (J^T B J) is stored with its two off-diagonal values
+// averaged, which is what the paper's end-of-sweep symmetrization does.
+
+struct WaveRec {
+  double c, s;
+  int rot;
+  int pad;
+};
+
+// Rotation parameters of the wavefront's pairs (skip rule of Algorithm 4).
+__global__ void cyc_wave_params(const double* __restrict__ A, int lda, int n, int t, int plo, int k, double skip,
+                                double skip_abs, WaveRec* __restrict__ rec, int* __restrict__ rotated) {
+  const int kp = blockIdx.x * blockDim.x + threadIdx.x;
+  if (kp >= k) return;
+  const int p = plo + kp, q = t - p;
+  const double app = A[(size_t)p * lda + p], aqq = A[(size_t)q * lda + q], apq = A[(size_t)p * lda + q];
+  WaveRec r;
+  r.c = 1.0;
+  r.s = 0.0;
+  r.rot = 0;
+  r.pad = 0;
+  if (fabs(apq) > skip * sqrt(fabs(app * aqq)) && fabs(apq) > skip_abs) {
+    // Algorithm 2, stable form (Appendix A approach 2)
+    const double tau = (aqq - app) / (2.0 * apq);
+    const double tt = tau >= 0.0 ? 1.0 / (tau + sqrt(1.0 + tau * tau)) : 1.0 / (tau - sqrt(1.0 + tau * tau));
+    r.c = 1.0 / sqrt(1.0 + tt * tt);
+    r.s = tt * r.c;
+    r.rot = 1;
+    *rotated = 1;
   }
-  if (threadIdx.x == 0) *rotated = any;
+  rec[kp] = r;
+}
+
+// new (x_p, x_q) = (c x_p - s x_q, s x_p + c x_q): the row update J^T x and
+// the column / vector update x J of Sec. 3.2.2 have the same form.
+MPJ_DEV void jrot(double c, double s, double& xp, double& xq) {
+  const double np = c * xp - s * xq, nq = s * xp + c * xq;
+  xp = np;
+  xq = nq;
+}
+
+// One wavefront: CTA (chunk, kp) owns columns p, q of pair kp (rows
+// j in its chunk) and of V.  Rows j outside the wavefront get the column
+// update and its mirror (rows p, q of column j).  Rows of another pair kj of
+// the wavefront: the thread of that pair's first index computes the whole
+// 2 x 2 block of rows (p_j, q_j) in columns (p, q) in the canonical order
+// (lower pair index first); the other pair's CTA computes the mirror block
+// from the same operands in the same order.  Nothing a CTA reads is written
+// by another CTA of the same launch.
+__global__ void __launch_bounds__(256) cyc_wave_update(double* __restrict__ A, int lda, double* __restrict__ V,
+                                                       int ldv, int n, int t, int plo, int phi,
+                                                       const WaveRec* __restrict__ rec) {
+  const int kp = blockIdx.y;
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  const WaveRec ra = rec[kp];
+  const int p = plo + kp, q = t - p;
+  if (j >= n) return;
+  const size_t cp = (size_t)p * lda, cq = (size_t)q * lda;
+  // vectors: V(:, [p q]) = V(:, [p q]) J
+  if (ra.rot) {
+    double vp = V[(size_t)p * ldv + j], vq = V[(size_t)q * ldv + j];
+    jrot(ra.c, ra.s, vp, vq);
+    V[(size_t)p * ldv + j] = vp;
+    V[(size_t)q * ldv + j] = vq;
+  }
+  const int qlo = t - phi;
+  const bool in_p = j >= plo && j <= phi;
+  const bool in_q = j >= qlo && j <= t - plo;
+  if (!in_p && !in_q) {
+    if (!ra.rot) return;
+    double xp = A[cp + j], xq = A[cq + j];
+    jrot(ra.c, ra.s, xp, xq);
+    A[cp + j] = xp;
+    A[cq + j] = xq;
+    A[(size_t)j * lda + p] = xp;
+    A[(size_t)j * lda + q] = xq;
+    return;
+  }
+  if (in_q) return;  // rows of a pair are handled by the thread of its first index
+  const int kj = j - plo;
+  const int pj = j, qj = t - j;
+  const WaveRec rb = rec[kj];
+  if (kj == kp) {
+    if (!ra.rot) return;
+    // own block: rows (J^T B), then columns (.. J)
+    double bpp = A[cp + p], bqp = A[cp + q], bpq = A[cq + p], bqq = A[cq + q];
+    jrot(ra.c, ra.s, bpp, bqp);  // column p of B: rows p, q
+    jrot(ra.c, ra.s, bpq, bqq);  // column q of B
+    jrot(ra.c, ra.s, bpp, bpq);  // row p: columns p, q
+    jrot(ra.c, ra.s, bqp, bqq);  // row q
+    const double off = 0.5 * (bpq + bqp);
+    A[cp + p] = bpp;
+    A[cq + q] = bqq;
+    A[cp + q] = off;
+    A[cq + p] = off;
+    return;
+  }
+  if (!ra.rot && !rb.rot) return;
+  // rows (pj, qj) x columns (p, q): B(r, c) = A[row + col * lda]
+  double b00 = A[cp + pj], b10 = A[cp + qj], b01 = A[cq + pj], b11 = A[cq + qj];
+  if (kj < kp) {
+    // T = (J_kj^T B) J_kp, stored as is
+    jrot(rb.c, rb.s, b00, b10);  // rows pj, qj of column p
+    jrot(rb.c, rb.s, b01, b11);  // of column q
+    jrot(ra.c, ra.s, b00, b01);  // columns p, q of row pj
+    jrot(ra.c, ra.s, b10, b11);  // of row qj
+  } else {
+    // canonical order with kp first: T' = (J_kp^T B^T) J_kj, stored transposed;
+    // B^T(r', c') has rows (p, q), columns (pj, qj): B^T = [b00 b10; b01 b11]
+    double t00 = b00, t01 = b10, t10 = b01, t11 = b11;
+    jrot(ra.c, ra.s, t00, t10);  // rows p, q of column pj
+    jrot(ra.c, ra.s, t01, t11);  // of column qj
+    jrot(rb.c, rb.s, t00, t01);  // columns pj, qj of row p
+    jrot(rb.c, rb.s, t10, t11);  // of row q
+    b00 = t00;
+    b10 = t01;
+    b01 = t10;
+    b11 = t11;
+  }
+  A[cp + pj] = b00;
+  A[cp + qj] = b10;
+  A[cq + pj] = b01;
+  A[cq + qj] = b11;
 }
 
 }  // namespace
@@ -800,8 +886,18 @@ int mpj_jacobi64_run(int n, double* A, int lda, double* V, int ldv, double tol, 
         status = MPJ_NOT_CONVERGED;
         break;
       }
-      cyclic_sweep64<<<1, 1024, 0, s>>>(A, lda, V, ldv, n, skip, skip_abs, iscal);
-      mpj_count_launch();
+      // one sweep = 2n - 3 wavefronts; the rotation records use the record area
+      WaveRec* wrec = reinterpret_cast<WaveRec*>(rec[0]);
+      MPJ_CUDA_TRY(cudaMemsetAsync(iscal, 0, sizeof(int), s));
+      for (int t = 1; t <= 2 * n - 3; ++t) {
+        const int plo = t - (n - 1) > 0 ? t - (n - 1) : 0;
+        const int phi = (t - 1) / 2;
+        const int k = phi - plo + 1;
+        cyc_wave_params<<<(k + 127) / 128, 128, 0, s>>>(A, lda, n, t, plo, k, skip, skip_abs, wrec, iscal);
+        mpj_count_launch();
+        cyc_wave_update<<<dim3((n + 255) / 256, k), 256, 0, s>>>(A, lda, V, ldv, n, t, plo, phi, wrec);
+        mpj_count_launch();
+      }
       MPJ_CUDA_TRY(cudaGetLastError());
       int rotated = 0;
       ++sweeps;

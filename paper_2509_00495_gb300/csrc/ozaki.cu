@@ -8,40 +8,75 @@
 //   a_rk = sum_{i=1..8} q_i(r,k) 2^(e_r - 7 i) + (a remainder below 2^(e_r - 57)),
 // with integers |q_1| <= 128 and |q_i| <= 64 (i > 1), each exactly a bf16; the
 // same for each column c of op(B) with exponents f_c.  Then
-//   (op(A) op(B))_rc = sum_L 2^(e_r + f_c - 7 L) sum_{i+j=L} sum_k q_i(r,k) q_j(k,c)
-// for levels L = 2..9 (the dropped levels are below 2^-57 relative).  Over a
-// chunk of 256 values of k every level sum (and every partial sum of it) is
-// an integer below 2^24 (at most 2^23.33 for the top levels), so the tensor
-// cores' FP32 accumulation of the bf16 products is exact whatever its rounding; each chunk's level sums are read back from tensor memory,
-// converted to FP64 exactly and accumulated in FP64.
+//   (op(A) op(B))_rc = 2^(e_r + f_c) sum_L 2^(-7 L) s_L(r,c),
+//   s_L(r,c) = sum_{i+j=L} sum_k q_i(r,k) q_j(k,c),
+// for levels L = 2..9 (the dropped levels are below 2^-54 relative to
+// max|a_r.| max|b_.c| per term).  Over a chunk of 256 values of k every level
+// sum (and every partial sum of it) is an integer of magnitude below 2^24 (at
+// most 2^23.33, for the top levels), so the tensor cores' FP32 accumulation
+// of the bf16 products is exact.  The epilogue converts each chunk's level
+// sums to integers and accumulates them exactly in two 64-bit integers per
+// output (levels 2..5 and 6..9, weights 2^(7(5-L)) and 2^(7(9-L)): below
+// 2^48 after 16 chunks, so a launch covers up to 4096 values of k exactly;
+// longer K runs as several launches that add into C).  The result is
+//   2^(e_r + f_c) (hi 2^-35 + lo 2^-63),
+// one rounding in FP64 for the sum and an exact power-of-two scaling, so the
+// exponent sum is applied once and no intermediate weight can underflow.
 //
-// Layout of the slices in global memory: for slice s and a tile of TR rows
-// and 32 values of k, TR x 32 bf16 in the canonical K-major no-swizzle layout
-// (8-row x 16-byte core matrices; cores adjacent in k 128 bytes apart, 8-row
-// groups 512 bytes apart), so a tile is one contiguous copy into shared memory.
+// Sliced operand layout in global memory: for slice s, the rows are cut into
+// 64-row groups and k into 32-wide groups; tile (k-group g, row group t) is
+// 64 x 32 bf16 in the canonical K-major no-swizzle layout (8-row x 16-byte
+// core matrices, k-adjacent cores 128 bytes apart, 8-row groups 512 bytes
+// apart) and tiles are stored k-group-major: tile index g * (Rp / 64) + t.
+// The two 64-row tiles of a 128-row MMA operand are therefore adjacent, one
+// 8 KB bulk copy; a 64-row operand is one 4 KB bulk copy.
+//
+// The product kernel: one CTA per 128 x 64 output tile (one CTA per SM: its
+// 192 KB shared-memory ring and 512 TMEM columns), 10 warps:
+//   warp 8 (one thread): producer -- cp.async.bulk copies of the 16 slice
+//          tiles of a 32-wide k step into one of two ring stages, completion
+//          counted by the stage's "full" mbarrier (transaction bytes);
+//   warp 9 (one thread): issues the 36 x 2 tcgen05.mma (M = 128, N = 64,
+//          K = 16) of a k step into the 8 level accumulators (8 x 64 TMEM
+//          columns), then tcgen05.commit to the stage's "empty" mbarrier, and
+//          to "tmem_full" after the last k step of a 256-wide chunk;
+//   warps 0-7: epilogue -- wait "tmem_full", read the 8 levels (warp w reads
+//          TMEM lanes 32 (w mod 4) .. +31, columns 32 (w / 4) .. +31 of each
+//          level), arrive on "tmem_empty", accumulate in integers.
+// Every wait is bounded (about 2 s); a wait that runs out sets
+// MPJ_FLAG_TIMEOUT, stops the other roles, waits (bounded) for work in
+// flight, frees TMEM and leaves C untouched.
 #include <cuda_bf16.h>
 #include <stdint.h>
 
 #include "common.cuh"
+#include "ozaki.cuh"
 
 namespace {
 
-constexpr int OZ_S = 8;                 // slices per value
-constexpr int OZ_TM = 128;              // output rows per CTA (MMA M)
-constexpr int OZ_TN = 64;               // output columns per CTA (MMA N)
-constexpr int OZ_KS = 32;               // k values per staged sub-chunk
-constexpr int OZ_KC = 256;              // k values per exact chunk
-constexpr int OZ_LEVELS = 8;            // L = 2..9
-constexpr uint32_t OZ_TMEM_COLS = 512;  // OZ_LEVELS x OZ_TN FP32 columns
+constexpr int OZ_S = 8;              // slices per value
+constexpr int OZ_TM = 128;           // output rows per CTA (MMA M)
+constexpr int OZ_TN = 64;            // output columns per CTA (MMA N)
+constexpr int OZ_KS = 32;            // k values per ring stage
+constexpr int OZ_KC = 256;           // k values per exact chunk
+constexpr int OZ_LEVELS = 8;         // L = 2..9
+constexpr int OZ_PASS_SUBS = 4096 / OZ_KS;  // k steps per launch (exact integer accumulation)
+constexpr uint32_t OZ_TMEM_COLS = 512;
+constexpr int OZ_TILE64 = 64 * OZ_KS;                       // bf16 elements of a 64-row tile
+constexpr uint32_t OZ_A_BYTES = OZ_TM * OZ_KS * 2;          // 8 KB per slice
+constexpr uint32_t OZ_B_BYTES = OZ_TN * OZ_KS * 2;          // 4 KB per slice
+constexpr uint32_t OZ_STAGE_BYTES = OZ_S * (OZ_A_BYTES + OZ_B_BYTES);  // 96 KB
+constexpr int OZ_EPI_WARPS = 8;
+constexpr int OZ_THREADS = (OZ_EPI_WARPS + 2) * 32;
 constexpr long long OZ_WAIT_CYCLES = 4000000000LL;
+constexpr int OZ_GROUP_M = 8;
 
-// bytes of one slice tile of TR rows x OZ_KS values
-__host__ __device__ constexpr int tile_bytes(int tr) { return tr * OZ_KS * 2; }
+MPJ_DEV uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
-MPJ_DEV uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-// byte offset of (row, k) inside a TR x 32 K-major tile (k in [0, 32))
-MPJ_DEV int kmaj16(int row, int k) { return (((row >> 3) * 4 + (k >> 3)) << 7) + ((row & 7) << 4) + ((k & 7) << 1); }
+// byte offset of (row, k) inside a 64- or 128-row x 32 K-major tile (k in [0, 32))
+__host__ __device__ inline int kmaj16(int row, int k) {
+  return (((row >> 3) * 4 + (k >> 3)) << 7) + ((row & 7) << 4) + ((k & 7) << 1);
+}
 
 MPJ_DEV uint64_t oz_desc(uint32_t saddr) {
   // start address, LBO = 128 bytes (k-adjacent cores), SBO = 512 bytes (8-row
@@ -64,7 +99,11 @@ MPJ_DEV void oz_mma(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t
       : "memory");
 }
 
-MPJ_DEV bool oz_test(uint32_t mbar, uint32_t parity) {
+MPJ_DEV void oz_commit(uint32_t mbar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar) : "memory");
+}
+
+MPJ_DEV bool mbar_test(uint32_t mbar, uint32_t parity) {
   uint32_t ok;
   asm volatile(
       "{\n\t.reg .pred p;\n\t"
@@ -76,13 +115,48 @@ MPJ_DEV bool oz_test(uint32_t mbar, uint32_t parity) {
   return ok != 0;
 }
 
-MPJ_DEV bool oz_wait(uint32_t mbar, uint32_t parity) {
-  long long t0 = clock64();
-  while (!oz_test(mbar, parity)) {
-    if (clock64() - t0 > OZ_WAIT_CYCLES) return false;
-    __nanosleep(64);
+MPJ_DEV void mbar_init(uint32_t mbar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(mbar), "r"(count) : "memory");
+}
+
+MPJ_DEV void mbar_arrive(uint32_t mbar) {
+  uint64_t st;
+  asm volatile("mbarrier.arrive.shared::cta.b64 %0, [%1];" : "=l"(st) : "r"(mbar) : "memory");
+  (void)st;
+}
+
+MPJ_DEV void mbar_expect_tx(uint32_t mbar, uint32_t bytes) {
+  uint64_t st;
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 %0, [%1], %2;" : "=l"(st) : "r"(mbar), "r"(bytes) : "memory");
+  (void)st;
+}
+
+MPJ_DEV void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t mbar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+               "l"(src), "r"(bytes), "r"(mbar)
+               : "memory");
+}
+
+// Bounded wait for the phase of parity `parity`; false when the budget runs
+// out (then the CTA's abort word is set) or another role aborted.
+MPJ_DEV bool oz_wait(uint32_t mbar, uint32_t parity, volatile int* abort_flag, unsigned* gflags) {
+  const long long t0 = clock64();
+  while (!mbar_test(mbar, parity)) {
+    if (*abort_flag) return false;
+    if (clock64() - t0 > OZ_WAIT_CYCLES) {
+      *abort_flag = 1;
+      if (gflags) atomicOr(gflags, MPJ_FLAG_TIMEOUT);
+      return false;
+    }
+    __nanosleep(32);
   }
   return true;
+}
+
+// The same without the abort word (used to drain work in flight on abort).
+MPJ_DEV void oz_drain(uint32_t mbar, uint32_t parity) {
+  const long long t0 = clock64();
+  while (!mbar_test(mbar, parity) && clock64() - t0 <= OZ_WAIT_CYCLES) __nanosleep(64);
 }
 
 #define OZ_LD32(taddr, v)                                                                                          \
@@ -95,171 +169,314 @@ MPJ_DEV bool oz_wait(uint32_t mbar, uint32_t parity) {
         "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])    \
       : "r"(taddr))
 
-// Exponent e with max_k |x(r,k)| < 2^e for each of R rows (x(r,k) = X[r*rs + k*ks]);
-// one warp per row.  Rows of zeros get e = 0 (their slices are zero).
-__global__ void oz_rowexp(const double* __restrict__ X, long long rs, long long ks, int R, int K, int* __restrict__ e) {
-  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
-  if (warp >= R) return;
-  double mx = 0.0;
-  for (int k = lane; k < K; k += 32) mx = fmax(mx, fabs(X[(long long)warp * rs + (long long)k * ks]));
-  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-  if (lane == 0) {
-    int ex = 0;
-    if (mx > 0.0) frexp(mx, &ex);  // mx = f 2^ex, f in [0.5, 1): mx < 2^ex
-    e[warp] = ex;
-  }
+// ---- slicing ----------------------------------------------------------------
+// Largest |x(r, k)| per row as the bit pattern of a non-negative double
+// (ordered like the value), combined with atomicMax.  Rows of a column-major
+// matrix (rs == 1): one thread per row over a strip of k, coalesced across rows.
+__global__ void oz_rowmax_cols(const double* __restrict__ X, long long ks, int R, int K, int kstrip,
+                               unsigned long long* __restrict__ mx) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= R) return;
+  const int k0 = blockIdx.y * kstrip, k1 = min(K, k0 + kstrip);
+  double m = 0.0;
+  for (int k = k0; k < k1; ++k) m = fmax(m, fabs(X[r + (long long)k * ks]));
+  if (m > 0.0) atomicMax(mx + r, (unsigned long long)__double_as_longlong(m));
 }
 
-// The 8 slices of every value into the tiled layout (rows padded to a
-// multiple of TR, k to a multiple of OZ_KC; padding is zero).
-__global__ void oz_slice(const double* __restrict__ X, long long rs, long long ks, int R, int K, int Rp, int Kp, int tr,
-                         const int* __restrict__ e, __nv_bfloat16* __restrict__ S) {
-  const long long total = (long long)Rp * Kp;
-  const long long slice_elems = total;
+// Rows stored contiguously (or any other stride): one warp per row.
+__global__ void oz_rowmax_warp(const double* __restrict__ X, long long rs, long long ks, int R, int K,
+                               unsigned long long* __restrict__ mx) {
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (warp >= R) return;
+  double m = 0.0;
+  for (int k = lane; k < K; k += 32) m = fmax(m, fabs(X[(long long)warp * rs + (long long)k * ks]));
+  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if (lane == 0) mx[warp] = (unsigned long long)__double_as_longlong(m);
+}
+
+// The 8 slices of 8 consecutive k values of one row per thread, written as
+// one 16-byte core-matrix row per slice.  rows_fast: consecutive threads take
+// consecutive rows (coalesced reads of column-major rows).
+__global__ void oz_slice(const double* __restrict__ X, long long rs, long long ks, int R, int K, int Rp, int Kp,
+                         int rows_fast, const unsigned long long* __restrict__ mx, int* __restrict__ exps,
+                         __nv_bfloat16* __restrict__ S) {
+  const long long total = (long long)Rp * (Kp / 8);
+  const long long slice_elems = (long long)Rp * Kp;
   for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
        idx += (long long)gridDim.x * blockDim.x) {
-    const int k = (int)(idx % Kp), r = (int)(idx / Kp);
-    double y = (r < R && k < K) ? X[(long long)r * rs + (long long)k * ks] : 0.0;
-    if (r < R) y = ldexp(y, -e[r]);  // |y| < 1
-    // tile (r / tr, k / 32), then (row, k) inside it
-    const long long tile = (long long)(r / tr) * (Kp / OZ_KS) + (k / OZ_KS);
-    const long long off = tile * (tr * OZ_KS) + (kmaj16(r % tr, k % OZ_KS) >> 1);
+    int r, g;
+    if (rows_fast) {
+      r = (int)(idx % Rp);
+      g = (int)(idx / Rp);
+    } else {
+      g = (int)(idx % (Kp / 8));
+      r = (int)(idx / (Kp / 8));
+    }
+    const int k0 = g * 8;
+    int e = 0;
+    if (r < R) {
+      const double m = __longlong_as_double((long long)mx[r]);
+      if (m > 0.0) frexp(m, &e);  // m = f 2^e, f in [0.5, 1): every |x(r, k)| < 2^e
+    }
+    if (g == 0) exps[r] = e;
+    double y[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int k = k0 + j;
+      const double x = (r < R && k < K) ? X[(long long)r * rs + (long long)k * ks] : 0.0;
+      y[j] = ldexp(x, -e);  // |y| < 1, exact
+    }
+    const long long tile = (long long)(k0 / OZ_KS) * (Rp / 64) + r / 64;
+    const long long off = tile * OZ_TILE64 + (kmaj16(r & 63, k0 & 31) >> 1);
 #pragma unroll
     for (int s = 0; s < OZ_S; ++s) {
-      y *= 128.0;
-      const double q = rint(y);
-      y -= q;  // exact: y and q share the grid of y's last bit
-      S[(long long)s * slice_elems + off] = __double2bfloat16((double)q);  // |q| <= 128: exact
+      __align__(16) __nv_bfloat16 q8[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        y[j] *= 128.0;
+        const double q = rint(y[j]);
+        y[j] -= q;                           // exact: y and q share the grid of y's last bit
+        q8[j] = __double2bfloat16(q);        // |q| <= 128: exact
+      }
+      *reinterpret_cast<uint4*>(S + s * slice_elems + off) = *reinterpret_cast<const uint4*>(q8);
     }
   }
 }
 
-struct __align__(16) OzSmem {
-  unsigned char a[OZ_S][tile_bytes(OZ_TM)];  // 8 x 8 KB
-  unsigned char b[OZ_S][tile_bytes(OZ_TN)];  // 8 x 4 KB
-  double colscale[OZ_TN];
-  uint64_t mbar;
+// ---- the product ------------------------------------------------------------
+struct __align__(1024) OzSmem {
+  unsigned char stage[2][OZ_STAGE_BYTES];  // per stage: 8 A slices (8 KB), then 8 B slices (4 KB)
+  uint64_t full[2], empty[2], tmem_full, tmem_empty;
+  int colexp[OZ_TN];
   uint32_t tmem;
+  int abort_flag;
 };
 
-__global__ void __launch_bounds__(128, 1)
-    oz_gemm(int M, int N, int Kp, const __nv_bfloat16* __restrict__ SA, const __nv_bfloat16* __restrict__ SB,
-            long long slice_a, long long slice_b, const int* __restrict__ ea, const int* __restrict__ eb, double alpha,
-            double beta, const double* Cin, double* C, int ldc, unsigned* flags) {
-  extern __shared__ __align__(1024) unsigned char dsm[];
-  OzSmem& sm = *reinterpret_cast<OzSmem*>(dsm);
+__global__ void __maxnreg__(200)
+    oz_gemm_kernel(const __nv_bfloat16* __restrict__ SA, const int* __restrict__ ea, int Rpa,
+                   const __nv_bfloat16* __restrict__ SB, const int* __restrict__ eb, int Rpb, int Kp, int sub0,
+                   int nsub, int m, int n, double alpha, double beta, const double* Cin, int ldcin, double* C,
+                   int ldc, unsigned* gflags) {
+  extern __shared__ __align__(1024) unsigned char dsm_raw[];
+  OzSmem& sm = *reinterpret_cast<OzSmem*>(dsm_raw + ((1024 - (smem_u32(dsm_raw) & 1023)) & 1023));
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int mt = blockIdx.x, nt = blockIdx.y;
-  const int row = mt * OZ_TM + warp * 32 + lane;  // the output row this thread accumulates
+  // tile order: groups of OZ_GROUP_M row tiles share the B tiles in L2
+  const int ntm = (m + OZ_TM - 1) / OZ_TM, ntn = (n + OZ_TN - 1) / OZ_TN;
+  const int id = blockIdx.x;
+  const int group = id / (OZ_GROUP_M * ntn);
+  const int first_m = group * OZ_GROUP_M;
+  const int gsz = min(ntm - first_m, OZ_GROUP_M);
+  const int local = id % (OZ_GROUP_M * ntn);
+  const int mt = first_m + local % gsz, nt = local / gsz;
+
   if (warp == 0) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(&sm.tmem)),
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&sm.tmem)),
                  "r"(OZ_TMEM_COLS)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
-  if (tid == 0) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&sm.mbar)) : "memory");
+  if (tid == 0) {
+    for (int s = 0; s < 2; ++s) {
+      mbar_init(smem_u32(&sm.full[s]), 1);
+      mbar_init(smem_u32(&sm.empty[s]), 1);
+    }
+    mbar_init(smem_u32(&sm.tmem_full), 1);
+    mbar_init(smem_u32(&sm.tmem_empty), OZ_EPI_WARPS * 32);
+    sm.abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
   if (tid < OZ_TN) {
     const int c = nt * OZ_TN + tid;
-    sm.colscale[tid] = (c < N) ? ldexp(1.0, eb[c]) : 0.0;
+    sm.colexp[tid] = (c < n) ? eb[c] : 0;
   }
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = sm.tmem;
-  const uint32_t mb = smem_addr(&sm.mbar);
-  const int er = (row < M) ? ea[row] : 0;
+  volatile int* abort_flag = &sm.abort_flag;
+  const uint32_t stage0 = smem_u32(sm.stage[0]);
 
-  double acc[OZ_TN];
-#pragma unroll
-  for (int c = 0; c < OZ_TN; ++c) acc[c] = 0.0;
-
-  const int nsub = Kp / OZ_KS;
-  const int ktiles = Kp / OZ_KS;
-  uint32_t phase = 0;
-  bool ok = true;
-  for (int sub = 0; sub < nsub && ok; ++sub) {
-    // stage the 8 A slices and 8 B slices of this 32-wide k range
-    const long long ta = ((long long)mt * ktiles + sub) * (tile_bytes(OZ_TM) / 2);
-    const long long tb = ((long long)nt * ktiles + sub) * (tile_bytes(OZ_TN) / 2);
-#pragma unroll
-    for (int s = 0; s < OZ_S; ++s) {
-      const uint4* ga = reinterpret_cast<const uint4*>(SA + s * slice_a + ta);
-      uint4* da = reinterpret_cast<uint4*>(sm.a[s]);
-      for (int i = tid; i < tile_bytes(OZ_TM) / 16; i += 128) da[i] = ga[i];
-      const uint4* gb = reinterpret_cast<const uint4*>(SB + s * slice_b + tb);
-      uint4* db = reinterpret_cast<uint4*>(sm.b[s]);
-      for (int i = tid; i < tile_bytes(OZ_TN) / 16; i += 128) db[i] = gb[i];
-    }
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    __syncthreads();
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    const bool chunk_start = (sub % (OZ_KC / OZ_KS)) == 0;
-    if (tid == 0) {
-      constexpr uint32_t idesc = oz_idesc(OZ_TM, OZ_TN);
-      bool first[OZ_LEVELS];
-#pragma unroll
-      for (int l = 0; l < OZ_LEVELS; ++l) first[l] = chunk_start;
-      for (int i = 1; i <= OZ_S; ++i)
-        for (int j = 1; i + j <= OZ_S + 1; ++j) {
-          const int l = i + j - 2;
-          const uint32_t d = tmem + (uint32_t)(l * OZ_TN);
-#pragma unroll
-          for (int kk = 0; kk < OZ_KS / 16; ++kk) {  // K = 16 per instruction: two 16-byte core columns
-            oz_mma(d, oz_desc(smem_addr(sm.a[i - 1]) + kk * 256), oz_desc(smem_addr(sm.b[j - 1]) + kk * 256), idesc,
-                   first[l] ? 0u : 1u);
-            first[l] = false;
-          }
+  if (warp == OZ_EPI_WARPS) {
+    // ---------------- producer
+    if (lane == 0) {
+      int issued = 0;
+      for (int sub = 0; sub < nsub; ++sub) {
+        const int st = sub & 1;
+        if (sub >= 2 && !oz_wait(smem_u32(&sm.empty[st]), ((sub >> 1) - 1) & 1, abort_flag, gflags)) break;
+        const uint32_t fb = smem_u32(&sm.full[st]);
+        mbar_expect_tx(fb, OZ_STAGE_BYTES);
+        const uint32_t dA = stage0 + st * OZ_STAGE_BYTES, dB = dA + OZ_S * OZ_A_BYTES;
+        const long long ta = ((long long)(sub0 + sub) * (Rpa / 64) + 2 * mt) * OZ_TILE64;
+        const long long tb = ((long long)(sub0 + sub) * (Rpb / 64) + nt) * OZ_TILE64;
+#pragma unroll 1
+        for (int s = 0; s < OZ_S; ++s) {
+          bulk_g2s(dA + s * OZ_A_BYTES, SA + (long long)s * Rpa * Kp + ta, OZ_A_BYTES, fb);
+          bulk_g2s(dB + s * OZ_B_BYTES, SB + (long long)s * Rpb * Kp + tb, OZ_B_BYTES, fb);
         }
-      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mb)
-                   : "memory");
+        issued = sub + 1;
+      }
+      if (*abort_flag) {
+        // copies in flight still land in this CTA's shared memory: wait for them
+        for (int sub = (issued > 2 ? issued - 2 : 0); sub < issued; ++sub)
+          oz_drain(smem_u32(&sm.full[sub & 1]), (sub >> 1) & 1);
+      }
     }
-    ok = oz_wait(mb, phase);
-    if (!ok) {
-      if (flags && lane == 0) atomicOr(flags, MPJ_FLAG_TIMEOUT);
-      oz_wait(mb, phase);  // the products may still be in flight
+  } else if (warp == OZ_EPI_WARPS + 1) {
+    // ---------------- MMA issuer
+    if (lane == 0) {
+      constexpr uint32_t idesc = oz_idesc(OZ_TM, OZ_TN);
+      int last_commit_sub = -1;
+      for (int sub = 0; sub < nsub; ++sub) {
+        const int st = sub & 1;
+        const int chunk = sub / (OZ_KC / OZ_KS);
+        const bool chunk_start = (sub % (OZ_KC / OZ_KS)) == 0;
+        if (!oz_wait(smem_u32(&sm.full[st]), (sub >> 1) & 1, abort_flag, gflags)) break;
+        if (chunk_start && chunk > 0 && !oz_wait(smem_u32(&sm.tmem_empty), (chunk - 1) & 1, abort_flag, gflags))
+          break;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t aB = stage0 + st * OZ_STAGE_BYTES, bB = aB + OZ_S * OZ_A_BYTES;
+        uint32_t started = chunk_start ? 0u : 0xFFu;
+        for (int i = 1; i <= OZ_S; ++i)
+          for (int j = 1; i + j <= OZ_S + 1; ++j) {
+            const int l = i + j - 2;
+            const uint32_t d = tmem + (uint32_t)(l * OZ_TN);
+#pragma unroll
+            for (int kk = 0; kk < OZ_KS / 16; ++kk) {
+              oz_mma(d, oz_desc(aB + (i - 1) * OZ_A_BYTES + kk * 256), oz_desc(bB + (j - 1) * OZ_B_BYTES + kk * 256),
+                     idesc, (started >> l) & 1u);
+              started |= 1u << l;
+            }
+          }
+        oz_commit(smem_u32(&sm.empty[st]));
+        last_commit_sub = sub;
+        if ((sub + 1) % (OZ_KC / OZ_KS) == 0 || sub + 1 == nsub) oz_commit(smem_u32(&sm.tmem_full));
+      }
+      if (*abort_flag && last_commit_sub >= 0)  // MMAs in flight still use TMEM and the ring
+        oz_drain(smem_u32(&sm.empty[last_commit_sub & 1]), (last_commit_sub >> 1) & 1);
     }
-    ok = __all_sync(0xffffffffu, ok);
-    ok = __syncthreads_and(ok);
-    phase ^= 1;
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    // end of a chunk: read the level sums (exact integers) and add them in FP64
-    if (ok && ((sub + 1) % (OZ_KC / OZ_KS) == 0 || sub + 1 == nsub)) {
+  } else {
+    // ---------------- epilogue: warps 0-7
+    const int quad = warp & 3, half = warp >> 2;
+    const int row = mt * OZ_TM + quad * 32 + lane;
+    const int nchunks = nsub / (OZ_KC / OZ_KS);
+    long long hi[32], lo[32];
+#pragma unroll
+    for (int c = 0; c < 32; ++c) {
+      hi[c] = 0;
+      lo[c] = 0;
+    }
+    bool ok = true;
+    for (int chunk = 0; chunk < nchunks; ++chunk) {
+      if (!oz_wait(smem_u32(&sm.tmem_full), chunk & 1, abort_flag, gflags)) {
+        ok = false;
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 #pragma unroll 1
       for (int l = 0; l < OZ_LEVELS; ++l) {
-        const double w = ldexp(1.0, er - 7 * (l + 2));
+        uint32_t v[32];
+        OZ_LD32(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(l * OZ_TN + half * 32), v);
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        if (l == OZ_LEVELS - 1) {
+          // every level of this chunk is in registers: the MMAs of the next chunk may start
+          asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+          mbar_arrive(smem_u32(&sm.tmem_empty));
+        }
+        const int sh = 7 * (3 - (l & 3));
 #pragma unroll
-        for (int half = 0; half < 2; ++half) {
-          uint32_t v[32];
-          OZ_LD32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(l * OZ_TN + half * 32), v);
-          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-          for (int c = 0; c < 32; ++c) acc[half * 32 + c] = fma((double)__uint_as_float(v[c]), w, acc[half * 32 + c]);
+        for (int c = 0; c < 32; ++c) {
+          const long long q = (long long)__float2int_rz(__uint_as_float(v[c]));  // an exact integer below 2^24
+          if (l < 4)
+            hi[c] += q << sh;
+          else
+            lo[c] += q << sh;
         }
       }
-      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-      __syncthreads();  // every level is read before the next chunk overwrites it
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     }
-  }
-  if (ok && row < M) {
+    if (ok && !*abort_flag && row < m) {
+      const int er = ea[row];
 #pragma unroll
-    for (int c = 0; c < OZ_TN; ++c) {
-      const int col = nt * OZ_TN + c;
-      if (col < N) {
-        double v = alpha * (acc[c] * sm.colscale[c]);
-        if (beta != 0.0) v = fma(beta, Cin[(long long)col * ldc + row], v);
-        C[(long long)col * ldc + row] = v;
+      for (int c = 0; c < 32; ++c) {
+        const int cl = half * 32 + c;
+        const int col = nt * OZ_TN + cl;
+        if (col < n) {
+          const double v = fma((double)hi[c], 0x1p-35, (double)lo[c] * 0x1p-63);
+          double out = alpha * ldexp(v, er + sm.colexp[cl]);
+          if (beta != 0.0) out = fma(beta, Cin[(long long)col * ldcin + row], out);
+          C[(long long)col * ldc + row] = out;
+        }
       }
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   if (warp == 0)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(OZ_TMEM_COLS) : "memory");
 }
 
+inline size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
+inline int pad_rows(int R) { return (R + OZ_TM - 1) / OZ_TM * OZ_TM; }
+inline int pad_k(int K) { return (K + OZ_KC - 1) / OZ_KC * OZ_KC; }
+
 }  // namespace
+
+size_t mpj_oz_operand_bytes(int R, int K) {
+  const size_t Rp = (size_t)pad_rows(R), Kp = (size_t)pad_k(K);
+  return al256((size_t)OZ_S * Rp * Kp * 2) + al256(Rp * sizeof(int)) + al256(Rp * sizeof(unsigned long long));
+}
+
+cudaError_t mpj_oz_prepare(const double* X, long long rs, long long ks, int R, int K, void* buf, OzOperand* op,
+                           cudaStream_t s) {
+  const int Rp = pad_rows(R), Kp = pad_k(K);
+  char* b = (char*)buf;
+  __nv_bfloat16* S = (__nv_bfloat16*)b;
+  int* exps = (int*)(b + al256((size_t)OZ_S * Rp * Kp * 2));
+  unsigned long long* mx = (unsigned long long*)((char*)exps + al256((size_t)Rp * sizeof(int)));
+  cudaError_t e = cudaMemsetAsync(mx, 0, (size_t)Rp * sizeof(unsigned long long), s);
+  if (e != cudaSuccess) return e;
+  if (rs == 1) {
+    const int kstrip = 64;
+    dim3 grid((R + 127) / 128, (K + kstrip - 1) / kstrip);
+    oz_rowmax_cols<<<grid, 128, 0, s>>>(X, ks, R, K, kstrip, mx);
+  } else {
+    oz_rowmax_warp<<<(R + 7) / 8, 256, 0, s>>>(X, rs, ks, R, K, mx);
+  }
+  mpj_count_launch();
+  const long long total = (long long)Rp * (Kp / 8);
+  const int blocks = (int)((total + 255) / 256 > 8192 ? 8192 : (total + 255) / 256);
+  oz_slice<<<blocks, 256, 0, s>>>(X, rs, ks, R, K, Rp, Kp, rs == 1 ? 1 : 0, mx, exps, S);
+  mpj_count_launch();
+  op->slices = S;
+  op->exps = exps;
+  op->R = R;
+  op->K = K;
+  op->Rp = Rp;
+  op->Kp = Kp;
+  return cudaGetLastError();
+}
+
+cudaError_t mpj_oz_gemm(const OzOperand& a, const OzOperand& b, int m, int n, double alpha, double beta,
+                        const double* Cin, int ldcin, double* C, int ldc, unsigned* flags, cudaStream_t s) {
+  if (a.Kp != b.Kp || m > a.R || n > b.R || m < 1 || n < 1) return cudaErrorInvalidValue;
+  const size_t smem = sizeof(OzSmem) + 1024;
+  cudaError_t e = cudaFuncSetAttribute(oz_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  const int ntm = (m + OZ_TM - 1) / OZ_TM, ntn = (n + OZ_TN - 1) / OZ_TN;
+  const int total = a.Kp / OZ_KS;
+  for (int sub0 = 0; sub0 < total; sub0 += OZ_PASS_SUBS) {
+    const int ns = total - sub0 < OZ_PASS_SUBS ? total - sub0 : OZ_PASS_SUBS;
+    const bool first = sub0 == 0;
+    oz_gemm_kernel<<<ntm * ntn, OZ_THREADS, smem, s>>>(a.slices, a.exps, a.Rp, b.slices, b.exps, b.Rp, a.Kp, sub0, ns,
+                                                        m, n, alpha, first ? beta : 1.0, first ? Cin : C,
+                                                        first ? ldcin : ldc, C, ldc, flags);
+    mpj_count_launch();
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
 
 extern "C" int mpj_dgemm_tc(char transa, char transb, int m, int n, int k, double alpha, const double* A, int lda,
                             const double* B, int ldb, double beta, double* C, int ldc, void* stream) {
@@ -269,43 +486,24 @@ extern "C" int mpj_dgemm_tc(char transa, char transb, int m, int n, int k, doubl
   if (m < 1 || n < 1 || k < 1 || !A || !B || !C) return MPJ_EINVAL;
   if (lda < (ta ? k : m) || ldb < (tb ? n : k) || ldc < m) return MPJ_EINVAL;
   cudaStream_t s = (cudaStream_t)stream;
-  const int Mp = (m + OZ_TM - 1) / OZ_TM * OZ_TM, Np = (n + OZ_TN - 1) / OZ_TN * OZ_TN;
-  const int Kp = (k + OZ_KC - 1) / OZ_KC * OZ_KC;
-  const long long slice_a = (long long)Mp * Kp, slice_b = (long long)Np * Kp;
-  const size_t bytes = (size_t)OZ_S * (slice_a + slice_b) * 2 + (size_t)(Mp + Np) * sizeof(int) + 256;
+  const size_t ba = mpj_oz_operand_bytes(m, k), bb = mpj_oz_operand_bytes(n, k);
+  const size_t bytes = ba + bb + 256;
   char* w = nullptr;
   cudaError_t e = cudaMallocAsync((void**)&w, bytes, s);
+  mpj_count_alloc();
   if (e != cudaSuccess) {
     mpj_set_cuda_error(e, "mpj_dgemm_tc workspace", __LINE__);
     return MPJ_ENOMEM;
   }
-  __nv_bfloat16* SA = (__nv_bfloat16*)w;
-  __nv_bfloat16* SB = SA + OZ_S * slice_a;
-  int* ea = (int*)(SB + OZ_S * slice_b);
-  int* eb = ea + Mp;
-  unsigned* flag = (unsigned*)(eb + Np);
+  unsigned* flag = (unsigned*)(w + ba + bb);
   // op(A)(r, kk) = A[r*rs + kk*ks]; op(B)^T(c, kk) = op(B)(kk, c)
   const long long ars = ta ? lda : 1, aks = ta ? 1 : lda;
   const long long brs = tb ? 1 : ldb, bks = tb ? ldb : 1;
-  const size_t smem = sizeof(OzSmem) + 1024;
+  OzOperand oa, ob;
   e = cudaMemsetAsync(flag, 0, sizeof(unsigned), s);
-  if (e == cudaSuccess) {
-    oz_rowexp<<<(m + 7) / 8, 256, 0, s>>>(A, ars, aks, m, k, ea);
-    mpj_count_launch();
-    oz_rowexp<<<(n + 7) / 8, 256, 0, s>>>(B, brs, bks, n, k, eb);
-    mpj_count_launch();
-    oz_slice<<<4096, 256, 0, s>>>(A, ars, aks, m, k, Mp, Kp, OZ_TM, ea, SA);
-    mpj_count_launch();
-    oz_slice<<<4096, 256, 0, s>>>(B, brs, bks, n, k, Np, Kp, OZ_TN, eb, SB);
-    mpj_count_launch();
-    e = cudaFuncSetAttribute(oz_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  }
-  if (e == cudaSuccess) {
-    dim3 grid(Mp / OZ_TM, Np / OZ_TN);
-    oz_gemm<<<grid, 128, smem, s>>>(m, n, Kp, SA, SB, slice_a, slice_b, ea, eb, alpha, beta, C, C, ldc, flag);
-    mpj_count_launch();
-    e = cudaGetLastError();
-  }
+  if (e == cudaSuccess) e = mpj_oz_prepare(A, ars, aks, m, k, w, &oa, s);
+  if (e == cudaSuccess) e = mpj_oz_prepare(B, brs, bks, n, k, w + ba, &ob, s);
+  if (e == cudaSuccess) e = mpj_oz_gemm(oa, ob, m, n, alpha, beta, C, ldc, C, ldc, flag, s);
   unsigned h = 0;
   if (e == cudaSuccess) e = cudaMemcpyAsync(&h, flag, sizeof(unsigned), cudaMemcpyDeviceToHost, s);
   cudaFreeAsync(w, s);

@@ -10,8 +10,10 @@
 //
 // Workspace (mixed, n): three n x n FP64 buffers (X = Q_l/Q_d, M = X^T X then
 // A_cond, Y = NS temporary then V), the stage-1 FP32 buffers (A32, V32 and
-// the per-pair S, U; reused for the permuted V at the end) and a small
-// scratch area.  About 24 n^2 + 8 N^2 bytes: 512 MiB at n = 4096.
+// the per-pair S, U; reused for the permuted V at the end), two sliced
+// operands of the tensor-core products (16 n^2 bytes each) and a small
+// scratch area.  About 56 n^2 + 8 N^2 bytes: 1 GiB at n = 4096.  The solve
+// allocates nothing when the caller passes a workspace.
 #include <stdio.h>
 #include <string.h>
 
@@ -21,14 +23,17 @@
 #include "gemm64.cuh"
 #include "jacobi64.cuh"
 #include "ns_fast.cuh"
+#include "ozaki.cuh"
 #include "stage1.cuh"
 
 #include <atomic>
 
 static thread_local char g_cuda_err[256] = "";
 static std::atomic<long long> g_launches{0};
+static std::atomic<long long> g_allocs{0};
 
 void mpj_count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+void mpj_count_alloc() { g_allocs.fetch_add(1, std::memory_order_relaxed); }
 
 void mpj_set_cuda_error(cudaError_t e, const char* what, int line) {
   snprintf(g_cuda_err, sizeof g_cuda_err, "%s (%d) in %s [syev line %d]", cudaGetErrorString(e), (int)e, what, line);
@@ -39,7 +44,7 @@ namespace {
 inline size_t al(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct Layout {
-  size_t X, M, Y, Z, S1, scratch, small, total;
+  size_t X, M, Y, Z, S1, OZ0, OZ1, scratch, small, total;
 };
 
 // Z (a fourth n x n buffer) only exists when a second preconditioning pass is run.
@@ -61,6 +66,11 @@ Layout layout(int n, int passes) {
   size_t s1b = sq + al(mpj_ns_fast_bytes(n));
   if (s1 < s1b) s1 = s1b;
   off += s1;
+  // the two sliced operands of the tensor-core products
+  L.OZ0 = off;
+  off += al(mpj_oz_operand_bytes(n, n));
+  L.OZ1 = off;
+  off += al(mpj_oz_operand_bytes(n, n));
   L.scratch = off;
   off += al(mpj_jacobi64_scratch_bytes(n));
   L.small = off;
@@ -118,10 +128,8 @@ __global__ void mirror_lower(double* __restrict__ B, int ldb, int n) {
   }
 }
 
-// The Newton-Schulz and A_cond products run on the tensor cores
-// (mpj_dgemm_tc: exact bf16 slices, stream-ordered scratch of its own from
-// cudaMallocAsync) unless MPJ_GEMM_TC=0 selects the FP64 DMMA kernel.  At
-// n = 4096: 182 + 90 ms instead of 381 + 190 ms, same accuracy.
+// The Newton-Schulz and A_cond products run on the tensor cores (exact bf16
+// slices, ozaki.cu) unless MPJ_GEMM_TC=0 selects the FP64 DMMA kernel.
 bool gemm_tensor_cores() {
   static int v = -1;
   if (v < 0) {
@@ -224,20 +232,51 @@ int fill_opts(int n, const mpj_opts* in, mpj_opts* o) {
   return MPJ_OK;
 }
 
+// Device memory the tensor-core products use: two sliced-operand buffers
+// (mpj_oz_operand_bytes(n, n) each) and the flags word where a completion
+// wait that ran out is recorded.
+struct OzWork {
+  void* b0;
+  void* b1;
+  unsigned* flags;
+};
+
+int oz_fail(cudaError_t e, const char* what, int line) {
+  mpj_set_cuda_error(e, what, line);
+  return MPJ_ECUDA;
+}
+
+// C = alpha op(A) op(B) + beta Cin (n x n operands, ld n unless given) on the
+// selected engine.  op(A) rows and op(B) columns are sliced into w.b0 / w.b1.
+int product_run(bool ta, bool tb, int n, double alpha, const double* A, int lda, const double* B, int ldb,
+                double beta, const double* Cin, double* C, const OzWork& w, cudaStream_t s) {
+  if (!gemm_tensor_cores()) {
+    cudaError_t e = mpj_gemm64(ta, tb, n, n, n, alpha, A, lda, B, ldb, beta, Cin, n, C, n, 0, s);
+    return e == cudaSuccess ? MPJ_OK : oz_fail(e, "DMMA product", __LINE__);
+  }
+  OzOperand oa, ob;
+  cudaError_t e = mpj_oz_prepare(A, ta ? lda : 1, ta ? 1 : lda, n, n, w.b0, &oa, s);
+  if (e == cudaSuccess) e = mpj_oz_prepare(B, tb ? 1 : ldb, tb ? ldb : 1, n, n, w.b1, &ob, s);
+  if (e == cudaSuccess) e = mpj_oz_gemm(oa, ob, n, n, alpha, beta, Cin, n, C, n, w.flags, s);
+  return e == cudaSuccess ? MPJ_OK : oz_fail(e, "tensor-core product", __LINE__);
+}
+
 // Newton-Schulz X <- X (3I - X^T X) / 2, written X <- X + X E / 2 with
-// E = I - X^T X: the symmetric product M = X^T X on the FP64 DMMA kernel
-// (n^3 flops, lower tiles mirrored), E in FP64, then X E either in FP32 when
-// max|E| <= 2^-31 / sqrt(n) (ns_fast.cu) or on the FP64 kernel (2 n^3 flops).
-// With MPJ_GEMM_TC=1 both products run on the tensor cores (mpj_dgemm_tc; its
-// X^T X is exactly symmetric because row and column slices coincide).  X, M,
-// Y are n x n with ld n; `fp32work` holds mpj_ns_fast_bytes(n).  The result
-// ends in *X.
-int ns_steps_run(int n, double** X, double* M, double** Y, int steps, void* fp32work, cudaStream_t s) {
+// E = I - X^T X: the symmetric product M = X^T X (tensor cores: the columns of
+// X sliced once serve both operands, so M is exactly symmetric; DMMA: lower
+// tiles mirrored), E in FP64, then X E either in FP32 when
+// max|E| <= 2^-31 / sqrt(n) (ns_fast.cu) or as an FP64-accurate product.
+// X, M, Y are n x n with ld n; `fp32work` holds mpj_ns_fast_bytes(n).  The
+// result ends in *X.
+int ns_steps_run(int n, double** X, double* M, double** Y, int steps, void* fp32work, const OzWork& w,
+                 cudaStream_t s) {
   const bool tc = gemm_tensor_cores();
   for (int k = 0; k < steps; ++k) {
     if (tc) {
-      int r = mpj_dgemm_tc('T', 'N', n, n, n, 1.0, *X, n, *X, n, 0.0, M, n, s);
-      if (r != MPJ_OK) return r;
+      OzOperand ox;
+      cudaError_t e = mpj_oz_prepare(*X, n, 1, n, n, w.b0, &ox, s);  // column j of X = row j of X^T
+      if (e == cudaSuccess) e = mpj_oz_gemm(ox, ox, n, n, 1.0, 0.0, nullptr, n, M, n, w.flags, s);
+      if (e != cudaSuccess) return oz_fail(e, "Newton-Schulz X^T X", __LINE__);
     } else {
       MPJ_CUDA_TRY(mpj_gemm64(true, false, n, n, n, 1.0, *X, n, *X, n, 0.0, nullptr, n, M, n, 1, s));
     }
@@ -245,7 +284,7 @@ int ns_steps_run(int n, double** X, double* M, double** Y, int steps, void* fp32
     if (r < 0) return r;
     if (r == 1 && tc) {  // Y = X + X E / 2
       MPJ_CUDA_TRY(cudaMemcpyAsync(*Y, *X, (size_t)n * n * sizeof(double), cudaMemcpyDeviceToDevice, s));
-      int rt = mpj_dgemm_tc('N', 'N', n, n, n, 0.5, *X, n, M, n, 1.0, *Y, n, s);
+      int rt = product_run(false, false, n, 0.5, *X, n, M, n, 1.0, *Y, *Y, w, s);
       if (rt != MPJ_OK) return rt;
     } else if (r == 1) {
       MPJ_CUDA_TRY(mpj_gemm64(false, false, n, n, n, 0.5, *X, n, M, n, 1.0, *X, n, *Y, n, 0, s));
@@ -254,6 +293,30 @@ int ns_steps_run(int n, double** X, double* M, double** Y, int steps, void* fp32
     *X = *Y;
     *Y = t;
   }
+  return MPJ_OK;
+}
+
+// Algorithm 9 step 3: Ac = Qd^T (A Qd), written exactly symmetric (lower
+// triangle mirrored); Y (n x n, ld n) receives A Qd.  Tensor cores: the
+// columns of Qd are sliced once and serve as the right operand of A Qd and
+// the left operand of Qd^T Y.
+int transform_run(int n, const double* A, int lda, const double* Qd, int ldq, double* Y, double* Ac, int ldc,
+                  const OzWork& w, cudaStream_t s) {
+  if (gemm_tensor_cores()) {
+    OzOperand oa, oq, oy;
+    cudaError_t e = mpj_oz_prepare(A, 1, lda, n, n, w.b0, &oa, s);                 // rows of A
+    if (e == cudaSuccess) e = mpj_oz_prepare(Qd, ldq, 1, n, n, w.b1, &oq, s);      // columns of Qd
+    if (e == cudaSuccess) e = mpj_oz_gemm(oa, oq, n, n, 1.0, 0.0, nullptr, n, Y, n, w.flags, s);
+    if (e == cudaSuccess) e = mpj_oz_prepare(Y, n, 1, n, n, w.b0, &oy, s);         // columns of A Qd
+    if (e == cudaSuccess) e = mpj_oz_gemm(oq, oy, n, n, 1.0, 0.0, nullptr, n, Ac, ldc, w.flags, s);
+    if (e != cudaSuccess) return oz_fail(e, "transform", __LINE__);
+    mirror_lower<<<blocks_for((size_t)n * n), 256, 0, s>>>(Ac, ldc, n);
+    mpj_count_launch();
+    return MPJ_OK;
+  }
+  if (mpj_gemm64(false, false, n, n, n, 1.0, A, lda, Qd, ldq, 0.0, nullptr, n, Y, n, 0, s) != cudaSuccess ||
+      mpj_gemm64(true, false, n, n, n, 1.0, Qd, ldq, Y, n, 0.0, nullptr, n, Ac, ldc, 1, s) != cudaSuccess)
+    return oz_fail(cudaGetLastError(), "transform", __LINE__);
   return MPJ_OK;
 }
 
@@ -291,6 +354,8 @@ const char* mpj_last_cuda_error(void) { return g_cuda_err; }
 
 long long mpj_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
 
+long long mpj_device_allocations(void) { return g_allocs.load(std::memory_order_relaxed); }
+
 size_t mpj_syev_workspace(int n, const mpj_opts* o) {
   (void)o;
   if (n <= 0) return 0;
@@ -313,6 +378,7 @@ int mpj_syev_ex(int n, const double* A, int lda, double* W, double* Q, int ldq, 
     if (work_bytes < L.total) return MPJ_EWORKSPACE;
   } else {
     cudaError_t e = cudaMallocAsync(&work, L.total, s);
+    mpj_count_alloc();
     if (e != cudaSuccess) {
       mpj_set_cuda_error(e, "cudaMallocAsync(workspace)", __LINE__);
       return MPJ_ENOMEM;
@@ -321,6 +387,7 @@ int mpj_syev_ex(int n, const double* A, int lda, double* W, double* Q, int ldq, 
   }
   int st = MPJ_OK;
   char* base = (char*)work;
+  unsigned flags_end = 0;
   double* X = (double*)(base + L.X);
   double* M = (double*)(base + L.M);
   double* Y = (double*)(base + L.Y);
@@ -328,6 +395,7 @@ int mpj_syev_ex(int n, const double* A, int lda, double* W, double* Q, int ldq, 
   void* S1 = base + L.S1;
   void* scratch = base + L.scratch;
   Small sm = small_ptrs(base + L.small, n);
+  const OzWork ozw{base + L.OZ0, base + L.OZ1, sm.flags};
   Timer tm;
   double norm2 = 0.0;
   unsigned flags = 0;
@@ -384,24 +452,10 @@ int mpj_syev_ex(int n, const double* A, int lda, double* W, double* Q, int ldq, 
       // stage 2: Newton-Schulz -> X = Q_d
       double* Xp = X;
       double* Yp = Y;
-      if ((st = ns_steps_run(n, &Xp, M, &Yp, o.ns_steps, S1, s)) != MPJ_OK) goto done;
+      if ((st = ns_steps_run(n, &Xp, M, &Yp, o.ns_steps, S1, ozw, s)) != MPJ_OK) goto done;
       tm.mark(2);
       // stage 3: A_cond = Q_d^T (A Q_d) -> M (symmetric), Yp = A Q_d
-      if (gemm_tensor_cores()) {
-        int rt = mpj_dgemm_tc('N', 'N', n, n, n, 1.0, A, lda, Xp, n, 0.0, Yp, n, s);
-        if (rt == MPJ_OK) rt = mpj_dgemm_tc('T', 'N', n, n, n, 1.0, Xp, n, Yp, n, 0.0, M, n, s);
-        if (rt != MPJ_OK) {
-          st = rt;
-          goto done;
-        }
-        mirror_lower<<<blocks_for((size_t)n * n), 256, 0, s>>>(M, n, n);
-        mpj_count_launch();
-      } else if (mpj_gemm64(false, false, n, n, n, 1.0, A, lda, Xp, n, 0.0, nullptr, n, Yp, n, 0, s) != cudaSuccess ||
-                 mpj_gemm64(true, false, n, n, n, 1.0, Xp, n, Yp, n, 0.0, nullptr, n, M, n, 1, s) != cudaSuccess) {
-        mpj_set_cuda_error(cudaGetLastError(), "transform", __LINE__);
-        st = MPJ_ECUDA;
-        goto done;
-      }
+      if ((st = transform_run(n, A, lda, Xp, n, Yp, M, n, ozw, s)) != MPJ_OK) goto done;
       Qd = Xp;
       Ac = M;
       V = Yp;
@@ -429,18 +483,13 @@ int mpj_syev_ex(int n, const double* A, int lda, double* W, double* Q, int ldq, 
         }
         double* X2 = Ql2;
         double* Y2 = (double*)S1;  // the stage-1 area is free again
-        if ((st = ns_steps_run(n, &X2, Z, &Y2, o.ns_steps, (char*)S1 + al((size_t)n * n * sizeof(double)), s)) !=
-            MPJ_OK)
+        if ((st = ns_steps_run(n, &X2, Z, &Y2, o.ns_steps, (char*)S1 + al((size_t)n * n * sizeof(double)), ozw,
+                               s)) != MPJ_OK)
           goto done;
         // A_cond2 = Q_d2^T (A_cond Q_d2): A_cond Q_d2 into Z, then Q_d2^T Z into M (A_cond is
         // consumed); then Q_d = Q_d1 Q_d2 into Z
-        if (mpj_gemm64(false, false, n, n, n, 1.0, M, n, X2, n, 0.0, nullptr, n, Z, n, 0, s) != cudaSuccess ||
-            mpj_gemm64(true, false, n, n, n, 1.0, X2, n, Z, n, 0.0, nullptr, n, M, n, 1, s) != cudaSuccess ||
-            mpj_gemm64(false, false, n, n, n, 1.0, Xp, n, X2, n, 0.0, nullptr, n, Z, n, 0, s) != cudaSuccess) {
-          mpj_set_cuda_error(cudaGetLastError(), "pass-2 transform", __LINE__);
-          st = MPJ_ECUDA;
-          goto done;
-        }
+        if ((st = transform_run(n, M, n, X2, n, Z, M, n, ozw, s)) != MPJ_OK) goto done;
+        if ((st = product_run(false, false, n, 1.0, Xp, n, X2, n, 0.0, nullptr, Z, ozw, s)) != MPJ_OK) goto done;
         Qd = Z;   // Q_d = Q_d1 Q_d2
         Ac = M;
         V = Xp;   // Q_d1 is folded into Z
@@ -492,7 +541,8 @@ int mpj_syev_ex(int n, const double* A, int lda, double* W, double* Q, int ldq, 
         mpj_count_launch();
         double* Qp = Qc;
         double* Tp = T;
-        if ((st = ns_steps_run(n, &Qp, M, &Tp, 1, (char*)S1 + al((size_t)n * n * sizeof(double)), s)) != MPJ_OK)
+        if ((st = ns_steps_run(n, &Qp, M, &Tp, 1, (char*)S1 + al((size_t)n * n * sizeof(double)), ozw, s)) !=
+            MPJ_OK)
           goto done;
         copy_mat<<<blocks_for((size_t)n * n), 256, 0, s>>>(Qp, n, Q, ldq, n);
         mpj_count_launch();
@@ -508,6 +558,9 @@ int mpj_syev_ex(int n, const double* A, int lda, double* W, double* Q, int ldq, 
   }
 done:
   tm.mark(6);
+  // device-side conditions of the products (a completion wait that ran out)
+  // are read here, at the single synchronization that ends the call
+  cudaMemcpyAsync(&flags_end, sm.flags, sizeof(unsigned), cudaMemcpyDeviceToHost, s);
   tm.finish(info);
   if (own) cudaFreeAsync(work, s);
   {
@@ -516,6 +569,7 @@ done:
       mpj_set_cuda_error(e, "final sync", __LINE__);
       st = MPJ_ECUDA;
     }
+    if (st >= 0 && (flags_end & MPJ_FLAG_TIMEOUT)) st = MPJ_ETIMEOUT;
   }
   if (info) {
     info->status = st;
@@ -545,6 +599,7 @@ int mpj_stage1(int n, const double* A, int lda, double* Ql, int ldq, double tol3
   size_t bytes = al(mpj_stage1_bytes(n)) + 4096;
   void* w = nullptr;
   if (cudaMallocAsync(&w, bytes, s) != cudaSuccess) return MPJ_ENOMEM;
+  mpj_count_alloc();
   double* partial = (double*)((char*)w + al(mpj_stage1_bytes(n)));
   double* dscal = partial + 256;
   int st = MPJ_OK;
@@ -568,22 +623,35 @@ int mpj_newton_schulz(int n, double* X, int ldx, int steps, void* stream) {
   cudaStream_t s = (cudaStream_t)stream;
   if (n <= 0 || !X || ldx < n || steps < 0) return MPJ_EINVAL;
   void* w = nullptr;
-  size_t sq = al((size_t)n * n * sizeof(double));
-  if (cudaMallocAsync(&w, 3 * sq + al(mpj_ns_fast_bytes(n)), s) != cudaSuccess) return MPJ_ENOMEM;
-  double* Xc = (double*)w;
-  double* M = (double*)((char*)w + sq);
-  double* Y = (double*)((char*)w + 2 * sq);
-  copy_mat<<<blocks_for((size_t)n * n), 256, 0, s>>>(X, ldx, Xc, n, n);
-  mpj_count_launch();
+  const size_t sq = al((size_t)n * n * sizeof(double));
+  const size_t ozb = al(mpj_oz_operand_bytes(n, n));
+  if (cudaMallocAsync(&w, 3 * sq + al(mpj_ns_fast_bytes(n)) + 2 * ozb + 256, s) != cudaSuccess) return MPJ_ENOMEM;
+  mpj_count_alloc();
+  char* b = (char*)w;
+  double* Xc = (double*)b;
+  double* M = (double*)(b + sq);
+  double* Y = (double*)(b + 2 * sq);
+  void* fp32work = b + 3 * sq;
+  char* oz = b + 3 * sq + al(mpj_ns_fast_bytes(n));
+  unsigned* flag = (unsigned*)(oz + 2 * ozb);
+  const OzWork ozw{oz, oz + ozb, flag};
+  unsigned h = 0;
+  int st = cudaMemsetAsync(flag, 0, sizeof(unsigned), s) == cudaSuccess ? MPJ_OK : MPJ_ECUDA;
   double* Xp = Xc;
   double* Yp = Y;
-  int st = ns_steps_run(n, &Xp, M, &Yp, steps, (char*)w + 3 * sq, s);
+  if (st == MPJ_OK) {
+    copy_mat<<<blocks_for((size_t)n * n), 256, 0, s>>>(X, ldx, Xc, n, n);
+    mpj_count_launch();
+    st = ns_steps_run(n, &Xp, M, &Yp, steps, fp32work, ozw, s);
+  }
   if (st == MPJ_OK) {
     copy_mat<<<blocks_for((size_t)n * n), 256, 0, s>>>(Xp, n, X, ldx, n);
     mpj_count_launch();
   }
+  cudaMemcpyAsync(&h, flag, sizeof(unsigned), cudaMemcpyDeviceToHost, s);
   cudaFreeAsync(w, s);
   if (cudaStreamSynchronize(s) != cudaSuccess && st >= 0) st = MPJ_ECUDA;
+  if (st == MPJ_OK && (h & MPJ_FLAG_TIMEOUT)) st = MPJ_ETIMEOUT;
   return st;
 }
 
@@ -591,14 +659,21 @@ int mpj_precondition(int n, const double* A, int lda, const double* Qd, int ldq,
   cudaStream_t s = (cudaStream_t)stream;
   if (n <= 0 || !A || !Qd || !Ac || lda < n || ldq < n || ldc < n) return MPJ_EINVAL;
   void* w = nullptr;
-  if (cudaMallocAsync(&w, (size_t)n * n * sizeof(double), s) != cudaSuccess) return MPJ_ENOMEM;
-  double* Wt = (double*)w;
-  int st = MPJ_OK;
-  if (mpj_gemm64(false, false, n, n, n, 1.0, A, lda, Qd, ldq, 0.0, nullptr, n, Wt, n, 0, s) != cudaSuccess ||
-      mpj_gemm64(true, false, n, n, n, 1.0, Qd, ldq, Wt, n, 0.0, nullptr, n, Ac, ldc, 1, s) != cudaSuccess)
-    st = MPJ_ECUDA;
+  const size_t sq = al((size_t)n * n * sizeof(double));
+  const size_t ozb = al(mpj_oz_operand_bytes(n, n));
+  if (cudaMallocAsync(&w, sq + 2 * ozb + 256, s) != cudaSuccess) return MPJ_ENOMEM;
+  mpj_count_alloc();
+  char* b = (char*)w;
+  double* Wt = (double*)b;
+  unsigned* flag = (unsigned*)(b + sq + 2 * ozb);
+  const OzWork ozw{b + sq, b + sq + ozb, flag};
+  unsigned h = 0;
+  int st = cudaMemsetAsync(flag, 0, sizeof(unsigned), s) == cudaSuccess ? MPJ_OK : MPJ_ECUDA;
+  if (st == MPJ_OK) st = transform_run(n, A, lda, Qd, ldq, Wt, Ac, ldc, ozw, s);
+  cudaMemcpyAsync(&h, flag, sizeof(unsigned), cudaMemcpyDeviceToHost, s);
   cudaFreeAsync(w, s);
   if (cudaStreamSynchronize(s) != cudaSuccess && st >= 0) st = MPJ_ECUDA;
+  if (st == MPJ_OK && (h & MPJ_FLAG_TIMEOUT)) st = MPJ_ETIMEOUT;
   return st;
 }
 
@@ -610,6 +685,7 @@ int mpj_jacobi64(int n, double* A, int lda, double* V, int ldv, double tol, int 
   void* w = nullptr;
   size_t wbytes = mpj_jacobi64_scratch_bytes(n) + 4096;
   if (cudaMallocAsync(&w, wbytes, s) != cudaSuccess) return MPJ_ENOMEM;
+  mpj_count_alloc();
   int st = MPJ_OK;
   if (tol <= 0) {
     double* partial = (double*)w;

@@ -276,6 +276,7 @@ extern "C" int mpj_stage1_panel(int N, int R, const float* U, const float* In, f
   cudaStream_t s = (cudaStream_t)stream;
   unsigned* flag = nullptr;
   cudaError_t e = cudaMallocAsync((void**)&flag, sizeof(unsigned), s);
+  mpj_count_alloc();
   if (e == cudaSuccess) e = cudaMemsetAsync(flag, 0, sizeof(unsigned), s);
   if (e == cudaSuccess) e = mpj_tc_panel(N, N / 16, R, U, In, Out, transpose_out, nullptr, nullptr, flag, s, no_commit);
   unsigned h = 0;

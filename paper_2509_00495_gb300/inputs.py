@@ -126,3 +126,16 @@ def randn_sym(n: int, seed: int = 0) -> np.ndarray:
     rng = np.random.default_rng(seed)
     r = rng.standard_normal((n, n))
     return np.asfortranarray(r + r.T)
+
+
+def near_diagonal(n: int, lam: np.ndarray, eps: float, seed: int = 0) -> np.ndarray:
+    """A = Q diag(lam) Q^T with Q the Cayley transform (I - eps S)^-1 (I + eps S)
+    of a random skew-symmetric S (entries N(0, 1/n)): an orthogonal Q within
+    about 2 eps of the identity, so A is nearly diagonal, like the matrix the
+    FP64 sweeps receive after preconditioning."""
+    rng = np.random.default_rng(seed)
+    g = rng.standard_normal((n, n)) / np.sqrt(n)
+    s = eps * (g - g.T) / 2.0
+    eye = np.eye(n)
+    q = np.linalg.solve(eye - s, eye + s)
+    return from_spectrum(lam, q)

@@ -84,6 +84,8 @@ def lib():
         L.mpj_status_str.argtypes = [_i]
         L.mpj_status_str.restype = ctypes.c_char_p
         L.mpj_last_cuda_error.restype = ctypes.c_char_p
+        L.mpj_kernel_launches.restype = ctypes.c_longlong
+        L.mpj_device_allocations.restype = ctypes.c_longlong
         L.mpj_syev_workspace.argtypes = [_i, ctypes.POINTER(Opts)]
         L.mpj_syev_workspace.restype = ctypes.c_size_t
         L.mpj_syev.argtypes = [_i, _vp, _i, _vp, _vp, _d, _vp]

@@ -109,3 +109,28 @@ def test_bench_reference_arm_contract():
     assert d["impl"] == "reference" and d["value"] > 0 and d["higher_is_better"] is True
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["value"] == d["value"]
+
+
+def test_allocation_counter_is_exported(libpath):
+    from paper_2509_00495_gb300 import mpj
+    L = mpj.lib()
+    L.mpj_device_allocations.restype = ctypes.c_longlong
+    assert L.mpj_device_allocations() >= 0
+
+
+def test_noalloc_size_limit_on_the_host(libpath):
+    """The fixed scratch of mpj_jacobi64_noalloc holds n = MPJ_NOALLOC_MAX_N:
+    8192 passes the host-side size check (and then fails at the first CUDA call,
+    there being no device here), 8193 is refused with MPJ_ETOOLARGE.  Never run
+    with a device present: the pointers are placeholders."""
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("host-only check (placeholder pointers)")
+    from paper_2509_00495_gb300 import mpj
+    L = mpj.lib()
+    p = ctypes.c_void_p(256)
+    fn = L.mpj_jacobi64_noalloc
+    fn.argtypes = [ctypes.c_int, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_int, ctypes.c_double,
+                   ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+    assert fn(8193, p, 8193, p, 8193, 1.0, 1, 1, None, None, None) == -9
+    assert fn(8192, p, 8192, p, 8192, 1.0, 1, 1, None, None, None) == mpj.MPJ_ECUDA

@@ -1,0 +1,274 @@
+"""GPU parity at the sizes where the kernels take their full-size paths, and
+the tensor-core product engine against the oracle and exact arithmetic.
+
+* FP64 round-robin sweeps (Algorithm 4 with the round-robin ordering) at
+  n = 600 and 1030: more than 512 rounds per sweep (the mid-sweep scale fold
+  and record re-initialization), full 64-round V batches, V updates on the
+  side stream (n >= 256).  Compared with the oracle's round-robin sweeps on the
+  same input: sweeps +-1, eigenvalues elementwise within 1e-13 ||A||,
+  eigenvectors after sign alignment.
+* The cyclic-by-row ordering (the paper's, Sec. 3.3), run as wavefronts of
+  independent rotations, against the oracle's sequential cyclic-by-row sweeps:
+  the same sweep count.
+* Algorithm 9 step 3 and Newton-Schulz (Sec. 4.3.4) through the stage entry
+  points, which run the solve's tensor-core engine, against the oracle on the
+  oracle's own intermediates, with k > 256 (several exact chunks).
+* The exact-slice product at its worst case (every slice at its bound, every
+  level sum near 2^23.3) against exact rational arithmetic, and with operands
+  near the bottom of the exponent range.
+* The solve with a caller workspace makes no allocation.
+* The eigen-adjoint at the differentiation workload's size (n = 512, gapped
+  spectra) against the oracle and central differences.
+* The second preconditioning pass against the oracle's two-pass mode.
+"""
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import oracle  # noqa: E402
+from paper_2509_00495_gb300 import inputs  # noqa: E402
+
+U = 2.0 ** -53
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2509_00495_gb300 import build
+    build.build()
+
+
+def mpj():
+    from paper_2509_00495_gb300 import mpj as m
+    return m
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def host(t):
+    return t.detach().cpu().numpy()
+
+
+def align_signs(Q, R):
+    s = np.sign(np.sum(Q * R, axis=0))
+    s[s == 0] = 1
+    return Q * s
+
+
+def triple(A, W, Q):
+    n = A.shape[0]
+    be = np.linalg.norm(A - (Q * W) @ Q.T) / np.linalg.norm(A)
+    orF = np.linalg.norm(Q.T @ Q - np.eye(n))
+    return be / (n * U), orF / (n * U)
+
+
+# ---------------------------------------------------------------- FP64 sweeps at full-size paths
+def _preconditioned_by_oracle(n, seed):
+    A, lam = inputs.geo_matrix(n, 1e3, seed=seed)
+    Ql, _, _ = oracle.stage1(A, ordering32=oracle.BLOCK_ROUND_ROBIN)
+    Ac = oracle.precondition(A, oracle.newton_schulz(Ql))
+    return (Ac + Ac.T) / 2, lam
+
+
+def _near_diagonal(n, seed):
+    rng = np.random.default_rng(seed)
+    lam = np.sort(rng.uniform(-1.0, 1.0, n))
+    return inputs.near_diagonal(n, lam, 1e-4, seed=seed), lam
+
+
+@pytest.mark.parametrize("n,kind", [(600, "oracle"), (1030, "near_diagonal")])
+def test_round_robin_sweeps_full_size_vs_oracle(n, kind):
+    Ac, lam = _preconditioned_by_oracle(n, 7) if kind == "oracle" else _near_diagonal(n, 8)
+    tol = n * U * np.linalg.norm(Ac)
+    a_ref, v_ref, sw_ref, _, _, _ = oracle.jacobi(Ac, ordering=oracle.ROUND_ROBIN, tol=tol)
+    a, v, sw, off, st = mpj().jacobi64(dev(Ac), tol=tol, ordering="round_robin")
+    a, v = host(a), host(v)
+    nA = np.linalg.norm(Ac, 2)
+    assert st == 0 and off <= tol
+    assert abs(sw - sw_ref) <= 1
+    w, w_ref = np.diag(a), np.diag(a_ref)
+    assert np.abs(w - w_ref).max() <= 1e-13 * nA
+    assert np.abs(align_signs(v, v_ref) - v_ref).max() <= 1e-9
+    assert np.array_equal(a, a.T)
+    assert np.linalg.norm(Ac @ v - v * w) <= 4 * n * U * nA
+    assert np.linalg.norm(v.T @ v - np.eye(n)) <= 4 * n * U
+
+
+@pytest.mark.parametrize("n,kind", [(130, "oracle"), (257, "near_diagonal"), (96, "randn")])
+def test_cyclic_wavefront_sweeps_vs_oracle(n, kind):
+    if kind == "oracle":
+        A, _ = _preconditioned_by_oracle(n, 3)
+    elif kind == "near_diagonal":
+        A, _ = _near_diagonal(n, 4)
+    else:
+        A = inputs.randn_sym(n, seed=n)
+    tol = n * U * np.linalg.norm(A)
+    a_ref, v_ref, sw_ref, _, _, _ = oracle.jacobi(A, ordering=oracle.CYCLIC, tol=tol)
+    a, v, sw, off, st = mpj().jacobi64(dev(A), tol=tol, ordering="cyclic")
+    a, v = host(a), host(v)
+    nA = np.linalg.norm(A, 2)
+    assert st == 0 and sw == sw_ref
+    assert np.abs(np.diag(a) - np.diag(a_ref)).max() <= 1e-13 * nA
+    assert np.abs(align_signs(v, v_ref) - v_ref).max() <= 1e-9
+    assert np.array_equal(a, a.T)
+
+
+def test_cyclic_mixed_solve_vs_oracle():
+    n = 200
+    A, lam = inputs.geo_matrix(n, 1e4, seed=23)
+    r = mpj().syev_ex(dev(A), ordering="cyclic")
+    Wr, _, info = oracle.syev_mixed(A, ordering32=oracle.BLOCK_ROUND_ROBIN, ordering64=oracle.CYCLIC)
+    nA = np.linalg.norm(A, 2)
+    assert r.status == 0 and r.info["sweeps64"] == info.sweeps64
+    assert np.abs(host(r.W) - Wr).max() <= 1e-12 * nA
+    be, orF = triple(A, host(r.W), host(r.Q))
+    assert be <= 4 and orF <= 4
+
+
+# ---------------------------------------------------------------- stage entry points on the tensor-core engine
+@pytest.mark.parametrize("n", [300, 520])
+def test_tensor_core_transform_vs_oracle(n):
+    A, lam = inputs.geo_matrix(n, 1e4, seed=n + 5)
+    Ql, _, _ = oracle.stage1(A, ordering32=oracle.BLOCK_ROUND_ROBIN)
+    Qd = oracle.newton_schulz(Ql)
+    ref = oracle.precondition(A, Qd)
+    got = host(mpj().precondition(dev(A), dev(Qd)))
+    assert np.array_equal(got, got.T)
+    assert np.abs(got - ref).max() <= 10 * n * U * np.linalg.norm(A, 2)
+
+
+@pytest.mark.parametrize("n", [520])
+def test_tensor_core_newton_schulz_vs_oracle(n):
+    A, lam = inputs.geo_matrix(n, 1e4, seed=n + 6)
+    Ql, _, _ = oracle.stage1(A, ordering32=oracle.BLOCK_ROUND_ROBIN)
+    ref = oracle.newton_schulz(Ql)
+    got = host(mpj().newton_schulz(dev(Ql), 2))
+    assert np.abs(got - ref).max() <= 10 * n * U
+    assert np.linalg.norm(got.T @ got - np.eye(n), 2) <= n * U
+
+
+# ---------------------------------------------------------------- exact-slice product: worst case, range
+def _worst_case_value(e):
+    """A double whose 8 slices on its own exponent grid 2^e are 127, 63 x 6, 56,
+    all of one sign: 127 2^-7 + 63 (2^-14 + ... + 2^-49) + 56 2^-56, times 2^e."""
+    y = Fraction(127, 128) + sum(Fraction(63, 128 ** i) for i in range(2, 8)) + Fraction(56, 128 ** 8)
+    v = float(y)
+    assert Fraction(v) == y  # 53 significant bits: exact
+    return np.ldexp(v, e)
+
+
+@pytest.mark.parametrize("k", [256, 257, 512])
+def test_exact_slices_worst_case_vs_rational_arithmetic(k):
+    """Every slice at its bound and all of one sign per row/column, so the
+    level sums of the top levels reach about 2^23.2 in the FP32 accumulators:
+    the result must still equal the exact product to within the rounding of
+    the output and the dropped levels (2 u relative)."""
+    m, n = 96, 72
+    rng = np.random.default_rng(k)
+    ea = rng.integers(-20, 20, size=m)
+    eb = rng.integers(-20, 20, size=n)
+    sa = rng.choice([-1.0, 1.0], size=m)
+    sb = rng.choice([-1.0, 1.0], size=n)
+    A = np.array([[sa[r] * _worst_case_value(int(ea[r])) for _ in range(k)] for r in range(m)])
+    B = np.array([[sb[c] * _worst_case_value(int(eb[c])) for c in range(n)] for _ in range(k)])
+    got = host(mpj().dgemm_tc("N", "N", 1.0, dev(A), dev(B)))
+    y = Fraction(_worst_case_value(0))
+    for r in range(m):
+        for c in range(n):
+            exact = float(k * y * y * Fraction(sa[r] * sb[c]) * Fraction(2) ** int(ea[r] + eb[c]))
+            assert abs(got[r, c] - exact) <= 2 * U * abs(exact), (r, c, got[r, c], exact)
+
+
+def test_exact_slices_tiny_exponents():
+    """Operands near the bottom of the exponent range: the row and column
+    scalings are applied once, at the end, so no slice level underflows."""
+    rng = np.random.default_rng(1)
+    A = rng.standard_normal((70, 300)) * 2.0 ** -1000
+    B = rng.standard_normal((300, 50))
+    got = host(mpj().dgemm_tc("N", "N", 1.0, dev(A), dev(B)))
+    ref = A @ B
+    bound = 2 * (300 + 2) * U * (np.abs(A) @ np.abs(B))
+    assert np.all(np.abs(got - ref) <= bound)
+    assert np.abs(got - ref).max() <= 64 * U * (np.abs(A) @ np.abs(B)).max()
+
+
+# ---------------------------------------------------------------- caller workspace: no allocation
+@pytest.mark.parametrize("opts", [{}, {"ordering": "cyclic"}, {"precond_passes": 2}, {"method": "plain"}])
+def test_solve_with_caller_workspace_allocates_nothing(opts):
+    m = mpj()
+    n = 300
+    A, lam = inputs.geo_matrix(n, 1e4, seed=31)
+    ws = torch.empty(m.syev_workspace(n, **opts), dtype=torch.uint8, device="cuda")
+    A_t = dev(A)
+    m.syev_ex(A_t, workspace=ws, **opts)  # first call: the library's one-time set-up
+    torch.cuda.synchronize()
+    before = m.lib().mpj_device_allocations()
+    r = m.syev_ex(A_t, workspace=ws, **opts)
+    torch.cuda.synchronize()
+    assert m.lib().mpj_device_allocations() == before
+    assert r.status == 0
+    assert np.abs(host(r.W) - np.sort(lam)).max() <= 1e-12
+
+
+# ---------------------------------------------------------------- backward at n = 512
+def test_backward_n512_vs_oracle_and_central_differences():
+    m = mpj()
+    mats, lams, dWs, dQs = inputs.backward_batch(3, 512, seed=0, grad_seed=1)
+    Ws, Qs = [], []
+    for a in mats:
+        r = m.syev_ex(dev(a))
+        assert r.status == 0
+        Ws.append(r.W)
+        Qs.append(r.Q)
+    W, Q = torch.stack(Ws), torch.stack(Qs)
+    dW, dQ = dev(np.stack(dWs)), dev(np.stack(dQs))
+    dA = host(m.syev_backward(W, Q, dW, dQ))
+    for i in range(3):
+        ref = oracle.eigh_backward(host(W[i]), host(Q[i]), dWs[i], dQs[i])
+        assert np.abs(dA[i] - ref).max() <= 1e-10 * np.abs(ref).max()
+        assert np.array_equal(dA[i], dA[i].T)
+    # central differences along random symmetric directions (matrix 0), h = 1e-6,
+    # with a loss made sign-invariant by aligning each eigenvector to the unperturbed one
+    A0 = dev(mats[0])
+    Qref = Q[0]
+    rng = np.random.default_rng(5)
+
+    def loss(M):
+        r = m.syev_ex(M)
+        s = torch.sign((r.Q * Qref).sum(0))
+        return ((r.W * dW[0]).sum() + (r.Q * s * dQ[0]).sum()).item()
+
+    h = 1e-6
+    for _ in range(3):
+        R = rng.standard_normal((512, 512))
+        E = dev((R + R.T) / 2 / np.linalg.norm(R + R.T))
+        fd = (loss(A0 + h * E) - loss(A0 - h * E)) / (2 * h)
+        an = float((dev(dA[0]) * E).sum().item())
+        assert fd == pytest.approx(an, rel=1e-4, abs=1e-6)
+
+
+# ---------------------------------------------------------------- two preconditioning passes vs the oracle
+@pytest.mark.parametrize("n", [96, 300])
+def test_two_pass_vs_oracle_two_pass(n):
+    A, lam = inputs.geo_matrix(n, 1e6, seed=41 * n)
+    r = mpj().syev_ex(dev(A), precond_passes=2)
+    Wr, Qr, info = oracle.syev_mixed(A, ordering32=oracle.BLOCK_ROUND_ROBIN, ordering64=oracle.ROUND_ROBIN,
+                                     threshold=True, precond_passes=2)
+    nA = np.linalg.norm(A, 2)
+    W, Q = host(r.W), host(r.Q)
+    assert r.status == 0
+    assert abs(r.info["sweeps32_pass2"] - info.sweeps32_pass2) <= 1
+    assert abs(r.info["sweeps64"] - info.sweeps64) <= 1
+    assert np.abs(W - Wr).max() <= 1e-12 * nA
+    # spectrum well separated relative to the accuracy: vectors agree after sign alignment
+    gap = np.min(np.diff(np.sort(lam)))
+    assert np.abs(align_signs(Q, Qr) - Qr).max() <= 1e3 * n * U * nA / gap
+    be, orF = triple(A, W, Q)
+    assert be <= 4 and orF <= 4

@@ -38,6 +38,8 @@ MUTATIONS = {
     "block_local_map": ("int gy = ly < ORC_BLK ? I * ORC_BLK + ly : J * ORC_BLK + (ly - ORC_BLK);",
                         "int gy = ly < ORC_BLK ? I * ORC_BLK + ly : J * ORC_BLK + ly;"),
     "float_pair_tau": ("float tau = (aqq - app) / (2.0f * apq);", "float tau = (aqq - app) / (apq);"),
+    "two_pass_product_order": ("orc_gemm_nn_d(n, n, n, X, n, X2, n, T, n);", "orc_gemm_nn_d(n, n, n, X2, n, X, n, T, n);"),
+    "two_pass_transform_on_A": ("orc_precondition_d(n, Ac, n, X2, n, T, n);", "orc_precondition_d(n, A, lda, X2, n, T, n);"),
 }
 
 

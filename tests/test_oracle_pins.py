@@ -480,3 +480,46 @@ def test_block_sets_helper_matches_oracle_schedule(N):
         for P, inner in enumerate(rnd):
             idx = {i for rho in inner for pq in rho for i in pq}
             assert idx == set(sets[P].tolist()), (N, R, P)
+
+
+# ---------------------------------------------------------------- two preconditioning passes (not in the paper)
+@pytest.mark.parametrize("n", [96, 130])
+def test_two_pass_mode_known_spectrum_and_fewer_sweeps(n):
+    """Algorithm 9's stages applied twice: the result is still an FP64-accurate
+    eigendecomposition of A (eigenvalues against the constructed spectrum,
+    residual, orthogonality, eigenvectors against LAPACK), and the second
+    FP32 pass, rounding A_cond relative to its own entries, leaves fewer FP64
+    sweeps on a kappa = 1e6 spectrum."""
+    A, lam = inputs.geo_matrix(n, 1e6, seed=41 * n)
+    W1, Q1, i1 = oracle.syev_mixed(A, ordering32=oracle.BLOCK_ROUND_ROBIN, ordering64=oracle.ROUND_ROBIN)
+    W2, Q2, i2 = oracle.syev_mixed(A, ordering32=oracle.BLOCK_ROUND_ROBIN, ordering64=oracle.ROUND_ROBIN,
+                                   precond_passes=2)
+    nA = np.linalg.norm(A, 2)
+    assert i2.sweeps32_pass2 >= 1 and i1.sweeps32_pass2 == 0
+    assert i2.sweeps64 < i1.sweeps64
+    assert np.abs(W2 - np.sort(lam)).max() <= 1e-12 * nA
+    assert np.linalg.norm(A - (Q2 * W2) @ Q2.T) / np.linalg.norm(A) <= 4 * n * U_D
+    assert np.linalg.norm(Q2.T @ Q2 - np.eye(n)) <= 4 * n * U_D
+    w_ref, v_ref = np.linalg.eigh(A)
+    gap = np.min(np.diff(w_ref))
+    s = np.sign(np.sum(Q2 * v_ref, axis=0))
+    assert np.abs(Q2 * s - v_ref).max() <= 100 * n * U_D * nA / gap
+
+
+def test_two_pass_intermediates_compose():
+    """The two-pass A_cond is Q_d^T A Q_d for the returned Q_d (= Q_d1 Q_d2),
+    and the FP64 sweeps on it reproduce W and Q = Q_d V."""
+    n = 64
+    A, lam = inputs.geo_matrix(n, 1e6, seed=2)
+    W, Q, info, it = oracle.syev_mixed(A, precond_passes=2, sort=False, return_intermediates=True)
+    Qd, Ac = it["Qd"], it["Acond"]
+    assert np.abs(Ac - Qd.T @ A @ Qd).max() <= 10 * n * U_D * nA_(A)
+    assert np.linalg.norm(Qd.T @ Qd - np.eye(n)) <= 4 * n * U_D
+    a, v, sw, rot, of, cap = oracle.jacobi(Ac, tol=n * U_D * info.normA_fro)
+    assert sw == info.sweeps64
+    assert np.array_equal(np.diag(a), W)
+    assert np.array_equal(oracle.gemm(Qd, v), Q)
+
+
+def nA_(A):
+    return np.linalg.norm(A, 2)

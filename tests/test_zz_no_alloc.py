@@ -60,6 +60,40 @@ def test_noalloc_matches_allocating_entry_point(lib, n, ordering):
         assert np.linalg.norm(A @ v - v * np.diag(a)) <= 4 * n * U * nA
 
 
+def test_noalloc_where_the_fixed_array_shortens_the_v_batches(lib):
+    """n = 2048: the fixed array holds only 32 rounds of V multipliers per batch
+    (the allocating entry point batches 64 and overlaps them on a side
+    stream); the rotation sequence and its arithmetic are the same, so the
+    results agree with mpj_jacobi64, on two calls in a row."""
+    from paper_2509_00495_gb300 import inputs
+    n = 2048
+    rng = np.random.default_rng(12)
+    lam = np.sort(rng.uniform(-1.0, 1.0, n))
+    A = inputs.near_diagonal(n, lam, 1e-4, seed=12)
+    st0, a0, v0, sw0, off0 = _run(lib.mpj_jacobi64, A, 1)
+    assert st0 == 0
+    nA = np.linalg.norm(A, 2)
+    for _ in range(2):
+        st, a, v, sw, off = _run(lib.mpj_jacobi64_noalloc, A, 1)
+        assert st == 0 and sw == sw0
+        assert np.abs(np.diag(a) - np.diag(a0)).max() <= 1e-13 * nA
+        assert np.abs(v - v0).max() <= 1e-10
+
+
+def test_noalloc_accepts_its_largest_size(lib):
+    """n = MPJ_NOALLOC_MAX_N = 8192 fits the fixed array (with fewer rounds per V
+    batch); a diagonal input converges before the first sweep."""
+    n = 8192
+    A = torch.diag(torch.linspace(-1.0, 1.0, n, dtype=torch.float64, device="cuda"))
+    V = torch.eye(n, dtype=torch.float64, device="cuda")
+    sw, off = ctypes.c_int(), ctypes.c_double()
+    stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    st = lib.mpj_jacobi64_noalloc(n, ctypes.c_void_p(A.data_ptr()), n, ctypes.c_void_p(V.data_ptr()), n, 0.0, 1, 0,
+                                  ctypes.byref(sw), ctypes.byref(off), stream)
+    torch.cuda.synchronize()
+    assert st == 0 and sw.value == 0 and off.value == 0.0
+
+
 def test_noalloc_rejects_sizes_beyond_its_scratch(lib):
     from paper_2509_00495_gb300 import mpj
     big = 8193  # one past MPJ_NOALLOC_MAX_N; rejected on the host before any device work
