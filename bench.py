@@ -243,6 +243,8 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--ref-step-seconds", type=float, default=8.0)
     ap.add_argument("--plain-solves", type=int, default=3)
+    ap.add_argument("--product-only", action="store_true",
+                    help="time only the FP64-accurate tensor-core product (n x n x n, mpj_dgemm_tc); for profiling")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
@@ -264,6 +266,9 @@ def main():
     from paper_2509_00495_gb300 import inputs, mpj
 
     n = args.n
+    if args.product_only:
+        product_only(mpj, torch, dev, n, args)
+        return
     A_np, lam = inputs.geo_4096(seed=0, n=n) if n == 4096 else inputs.geo_matrix(n, 1e6, seed=0)
     A = torch.from_numpy(A_np).to(dev)
     ws = torch.empty(mpj.syev_workspace(n), dtype=torch.uint8, device=dev)
@@ -469,6 +474,33 @@ def main():
         print(json.dumps(out), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+def product_only(mpj, torch, dev, n: int, args) -> None:
+    """`--warmup` then `--steps` products C = A B of n x n FP64 matrices on the
+    tensor-core exact-slice engine (mpj_dgemm_tc: slicing of both operands and
+    the product kernel), CUDA-event timed; prints one JSON line."""
+    g = torch.Generator(device="cpu").manual_seed(0)
+    A = torch.randn(n, n, dtype=torch.float64, generator=g).to(dev)
+    B = torch.randn(n, n, dtype=torch.float64, generator=g).to(dev)
+    for _ in range(args.warmup):
+        mpj.dgemm_tc("N", "N", 1.0, A, B)
+    torch.cuda.synchronize()
+    ms = []
+    for _ in range(args.steps):
+        e_a = torch.cuda.Event(enable_timing=True)
+        e_b = torch.cuda.Event(enable_timing=True)
+        e_a.record()
+        C = mpj.dgemm_tc("N", "N", 1.0, A, B)
+        e_b.record()
+        e_b.synchronize()
+        ms.append(e_a.elapsed_time(e_b))
+    err = ((C - A @ B).abs().max() / (A.abs() @ B.abs()).max()).item()
+    t = statistics.median(ms) if ms else float("nan")
+    print(json.dumps({"kernel": "mpj_dgemm_tc", "n": n, "ms_per_product": t,
+                      "fp64_equiv_tflops": 2.0 * n ** 3 / (t / 1000.0) / 1e12,
+                      "bf16_tensor_tflops": 36 * 2.0 * n ** 3 / (t / 1000.0) / 1e12,
+                      "max_err_over_abs_product": err}), flush=True)
 
 
 def extras(mpj, torch, dev, inputs) -> dict:

@@ -48,6 +48,7 @@
 // flight, frees TMEM and leaves C untouched.
 #include <cuda_bf16.h>
 #include <stdint.h>
+#include <stdio.h>
 
 #include "common.cuh"
 #include "ozaki.cuh"
@@ -252,7 +253,7 @@ struct __align__(1024) OzSmem {
   int abort_flag;
 };
 
-__global__ void __maxnreg__(200)
+__global__ void __maxnreg__(168)
     oz_gemm_kernel(const __nv_bfloat16* __restrict__ SA, const int* __restrict__ ea, int Rpa,
                    const __nv_bfloat16* __restrict__ SB, const int* __restrict__ eb, int Rpb, int Kp, int sub0,
                    int nsub, int m, int n, double alpha, double beta, const double* Cin, int ldcin, double* C,
@@ -444,17 +445,27 @@ cudaError_t mpj_oz_prepare(const double* X, long long rs, long long ks, int R, i
     oz_rowmax_warp<<<(R + 7) / 8, 256, 0, s>>>(X, rs, ks, R, K, mx);
   }
   mpj_count_launch();
+  e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    mpj_set_cuda_error(e, "oz_rowmax launch", __LINE__);
+    return e;
+  }
   const long long total = (long long)Rp * (Kp / 8);
   const int blocks = (int)((total + 255) / 256 > 8192 ? 8192 : (total + 255) / 256);
   oz_slice<<<blocks, 256, 0, s>>>(X, rs, ks, R, K, Rp, Kp, rs == 1 ? 1 : 0, mx, exps, S);
   mpj_count_launch();
+  e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    mpj_set_cuda_error(e, "oz_slice launch", __LINE__);
+    return e;
+  }
   op->slices = S;
   op->exps = exps;
   op->R = R;
   op->K = K;
   op->Rp = Rp;
   op->Kp = Kp;
-  return cudaGetLastError();
+  return cudaSuccess;
 }
 
 cudaError_t mpj_oz_gemm(const OzOperand& a, const OzOperand& b, int m, int n, double alpha, double beta,
@@ -473,7 +484,17 @@ cudaError_t mpj_oz_gemm(const OzOperand& a, const OzOperand& b, int m, int n, do
                                                         first ? ldcin : ldc, C, ldc, flags);
     mpj_count_launch();
     e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
+    if (e != cudaSuccess) {
+      cudaFuncAttributes fa;
+      char what[160];
+      if (cudaFuncGetAttributes(&fa, oz_gemm_kernel) == cudaSuccess)
+        snprintf(what, sizeof what, "oz_gemm_kernel launch (regs %d, max threads %d, static smem %zu, dyn smem %zu)",
+                 fa.numRegs, fa.maxThreadsPerBlock, fa.sharedSizeBytes, smem);
+      else
+        snprintf(what, sizeof what, "oz_gemm_kernel launch");
+      mpj_set_cuda_error(e, what, __LINE__);
+      return e;
+    }
   }
   return cudaSuccess;
 }
@@ -504,12 +525,13 @@ extern "C" int mpj_dgemm_tc(char transa, char transb, int m, int n, int k, doubl
   if (e == cudaSuccess) e = mpj_oz_prepare(A, ars, aks, m, k, w, &oa, s);
   if (e == cudaSuccess) e = mpj_oz_prepare(B, brs, bks, n, k, w + ba, &ob, s);
   if (e == cudaSuccess) e = mpj_oz_gemm(oa, ob, m, n, alpha, beta, C, ldc, C, ldc, flag, s);
+  const bool described = e != cudaSuccess;  // the failing step already recorded its message
   unsigned h = 0;
   if (e == cudaSuccess) e = cudaMemcpyAsync(&h, flag, sizeof(unsigned), cudaMemcpyDeviceToHost, s);
   cudaFreeAsync(w, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) {
-    mpj_set_cuda_error(e, "mpj_dgemm_tc", __LINE__);
+    if (!described) mpj_set_cuda_error(e, "mpj_dgemm_tc", __LINE__);
     return MPJ_ECUDA;
   }
   return (h & MPJ_FLAG_TIMEOUT) ? MPJ_ETIMEOUT : MPJ_OK;
