@@ -67,7 +67,7 @@ typedef enum {
   MPJ_ETOOLARGE = -9      /* n exceeds the fixed scratch of an allocation-free entry point */
 } mpj_status;
 
-enum { MPJ_ORDER_CYCLIC = 0, MPJ_ORDER_ROUND_ROBIN = 1 };
+enum { MPJ_ORDER_CYCLIC = 0, MPJ_ORDER_ROUND_ROBIN = 1, MPJ_ORDER_BLOCK = 2 };
 enum { MPJ_METHOD_MIXED = 0, MPJ_METHOD_PLAIN = 1 };
 
 typedef struct {

@@ -712,6 +712,14 @@ size_t mpj_jacobi64_scratch_bytes_rv(int n, int rv) {
 // half while the batched V update of the other half runs on a side stream.
 size_t mpj_jacobi64_scratch_bytes(int n) { return mpj_jacobi64_scratch_bytes_rv(n, 2 * RV_MAX); }
 
+// The block ordering needs, after the fixed part, an n x n FP64 buffer and the
+// per-round digit tiles of the U_P.
+size_t mpj_jacobi64_scratch_bytes_ordering(int n, int ordering) {
+  if (ordering == MPJ_ORDER_BLOCK)
+    return scratch_fixed(n) + align256((size_t)n * n * sizeof(double)) + align256(mpj_blocked_scratch_bytes(n));
+  return mpj_jacobi64_scratch_bytes(n);
+}
+
 namespace {
 // Side stream and events for overlapping the V updates with the rotation
 // rounds; released when the solve returns.  On every exit (also an early
@@ -794,7 +802,9 @@ int mpj_jacobi64_run(int n, double* A, int lda, double* V, int ldv, double tol, 
   int* iscal = (int*)(dscal + 2);
   off_b += align256(RED_CTAS * sizeof(double) + 4 * sizeof(double) + 64);
   double2* hist = (double2*)(base + off_b);
-  if (mpj_jacobi64_scratch_bytes_rv(n, 1) > scratch_bytes) return MPJ_EWORKSPACE;
+  if (ordering == MPJ_ORDER_BLOCK ? mpj_jacobi64_scratch_bytes_ordering(n, ordering) > scratch_bytes
+                                  : mpj_jacobi64_scratch_bytes_rv(n, 1) > scratch_bytes)
+    return MPJ_EWORKSPACE;
   // rounds of history that fit; with the side stream two halves of rv rounds
   const size_t cap = (scratch_bytes - scratch_fixed(n)) / ((size_t)half * sizeof(double2));
   bool overlap = side_stream && ordering == MPJ_ORDER_ROUND_ROBIN && overlap_enabled(n) && cap >= 16;
@@ -879,6 +889,32 @@ int mpj_jacobi64_run(int n, double* A, int lda, double* V, int ldv, double tol, 
       MPJ_CUDA_TRY(cudaMemcpyAsync(&off2, dscal, sizeof(double), cudaMemcpyDeviceToHost, s));
       MPJ_CUDA_TRY(cudaStreamSynchronize(s));
       off = sqrt(off2);
+    }
+  } else if (ordering == MPJ_ORDER_BLOCK) {
+    double* B = (double*)(base + scratch_fixed(n));
+    void* bscratch = base + scratch_fixed(n) + align256((size_t)n * n * sizeof(double));
+    unsigned* bflags = (unsigned*)(iscal + 1);
+    unsigned hflags = 0;
+    MPJ_CUDA_TRY(cudaMemsetAsync(bflags, 0, sizeof(unsigned), s));
+    const int rounds = mpj_blocked_rounds_per_sweep(n);
+    while (off > tol && n > 1) {
+      if (sweeps >= max_sweeps) {
+        status = MPJ_NOT_CONVERGED;
+        break;
+      }
+      for (int R = 0; R < rounds; ++R)
+        MPJ_CUDA_TRY(mpj_blocked_round(A, lda, V, ldv, B, n, R, skip, skip_abs, bscratch, bflags, s));
+      MPJ_CUDA_TRY(mpj_blocked_symmetrize(A, lda, n, s));
+      ++sweeps;
+      MPJ_CUDA_TRY(mpj_sumsq(A, lda, n, true, partial, dscal, nullptr, s));
+      MPJ_CUDA_TRY(cudaMemcpyAsync(&off2, dscal, sizeof(double), cudaMemcpyDeviceToHost, s));
+      MPJ_CUDA_TRY(cudaMemcpyAsync(&hflags, bflags, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+      MPJ_CUDA_TRY(cudaStreamSynchronize(s));
+      off = sqrt(off2);
+      if (hflags & MPJ_FLAG_TIMEOUT) {
+        status = MPJ_ETIMEOUT;
+        break;
+      }
     }
   } else {
     while (off > tol && n > 1) {

@@ -5,8 +5,21 @@
 
 // Scratch (records, scales, reduction partials, V history) for mpj_jacobi64_run
 // with the full 64-round V batching; _rv: with rv rounds per V batch.
+// _ordering: what mpj_jacobi64_run needs for that ordering (the block
+// ordering adds an n x n FP64 buffer and the digit tiles of the U_P).
 size_t mpj_jacobi64_scratch_bytes(int n);
 size_t mpj_jacobi64_scratch_bytes_rv(int n, int rv);
+size_t mpj_jacobi64_scratch_bytes_ordering(int n, int ordering);
+
+// Block round-robin FP64 sweeps with tensor-core block updates (blocked64.cu):
+// one outer round R (subproblem solves, then A <- U~^T A U~ and V <- V U~
+// through the n x n buffer B), the scratch it needs, rounds per sweep, and
+// the end-of-sweep symmetrization.
+size_t mpj_blocked_scratch_bytes(int n);
+cudaError_t mpj_blocked_round(double* A, int lda, double* V, int ldv, double* B, int n, int R, double skip,
+                              double skip_abs, void* scratch, unsigned* flags, cudaStream_t s);
+int mpj_blocked_rounds_per_sweep(int n);
+cudaError_t mpj_blocked_symmetrize(double* A, int lda, int n, cudaStream_t s);
 
 // FP64 sweeps in place (see mpjacobi.h, mpj_jacobi64).  Synchronizes `s` once
 // per sweep to read off(A).  `scratch_bytes` bounds the V batching (at least

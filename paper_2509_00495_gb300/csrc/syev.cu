@@ -47,8 +47,9 @@ struct Layout {
   size_t X, M, Y, Z, S1, OZ0, OZ1, scratch, small, total;
 };
 
-// Z (a fourth n x n buffer) only exists when a second preconditioning pass is run.
-Layout layout(int n, int passes) {
+// Z (a fourth n x n buffer) only exists when a second preconditioning pass is
+// run; the sweep scratch depends on the FP64 ordering.
+Layout layout(int n, int passes, int ordering) {
   Layout L;
   size_t sq = al((size_t)n * n * sizeof(double));
   size_t off = 0;
@@ -72,7 +73,7 @@ Layout layout(int n, int passes) {
   L.OZ1 = off;
   off += al(mpj_oz_operand_bytes(n, n));
   L.scratch = off;
-  off += al(mpj_jacobi64_scratch_bytes(n));
+  off += al(mpj_jacobi64_scratch_bytes_ordering(n, ordering));
   L.small = off;
   // flags + scalar (256 B), partials (2048 B), ranks (4n B, then rounded up to 256), w (8n B)
   off += al(2560 + 256 + (size_t)n * (sizeof(int) + sizeof(double)));
@@ -227,7 +228,8 @@ int fill_opts(int n, const mpj_opts* in, mpj_opts* o) {
   if (o->max_sweeps64 <= 0) o->max_sweeps64 = 30;
   if (o->max_sweeps32 <= 0) o->max_sweeps32 = 15;
   if (o->ns_steps <= 0) o->ns_steps = (n < 52000) ? 2 : 3;
-  if (o->ordering != MPJ_ORDER_CYCLIC && o->ordering != MPJ_ORDER_ROUND_ROBIN) return MPJ_EINVAL;
+  if (o->ordering != MPJ_ORDER_CYCLIC && o->ordering != MPJ_ORDER_ROUND_ROBIN && o->ordering != MPJ_ORDER_BLOCK)
+    return MPJ_EINVAL;
   if (o->method != MPJ_METHOD_MIXED && o->method != MPJ_METHOD_PLAIN) return MPJ_EINVAL;
   return MPJ_OK;
 }
@@ -360,7 +362,7 @@ size_t mpj_syev_workspace(int n, const mpj_opts* o) {
   (void)o;
   if (n <= 0) return 0;
   int passes = (o && o->precond_passes >= 2 && o->method == MPJ_METHOD_MIXED) ? 2 : 1;
-  return layout(n, passes).total;
+  return layout(n, passes, o ? o->ordering : MPJ_ORDER_ROUND_ROBIN).total;
 }
 
 int mpj_syev_ex(int n, const double* A, int lda, double* W, double* Q, int ldq, const mpj_opts* opts_in,
@@ -372,7 +374,7 @@ int mpj_syev_ex(int n, const double* A, int lda, double* W, double* Q, int ldq, 
   if (fill_opts(n, opts_in, &o) != MPJ_OK) return MPJ_EINVAL;
   if (n == 0) return MPJ_OK;
   const int passes = (o.method == MPJ_METHOD_MIXED && o.precond_passes >= 2) ? 2 : 1;
-  Layout L = layout(n, passes);
+  Layout L = layout(n, passes, o.ordering);
   bool own = false;
   if (work) {
     if (work_bytes < L.total) return MPJ_EWORKSPACE;
@@ -514,9 +516,9 @@ int mpj_syev_ex(int n, const double* A, int lda, double* W, double* Q, int ldq, 
       V = Qd;
     }
     {
-      const bool thr = o.threshold > 0 || (o.threshold < 0 && o.ordering == MPJ_ORDER_ROUND_ROBIN);
+      const bool thr = o.threshold > 0 || (o.threshold < 0 && o.ordering != MPJ_ORDER_CYCLIC);
       int r4 = mpj_jacobi64_run(n, Ac, n, V, n, tol, o.ordering, o.max_sweeps64, &sweeps64, &offf, &offc, scratch,
-                                mpj_jacobi64_scratch_bytes(n), s, thr ? tol / n : 0.0);
+                                mpj_jacobi64_scratch_bytes_ordering(n, o.ordering), s, thr ? tol / n : 0.0);
       if (r4 < 0) {
         st = r4;
         goto done;
@@ -681,9 +683,10 @@ int mpj_jacobi64(int n, double* A, int lda, double* V, int ldv, double tol, int 
                  double* off_final, void* stream) {
   cudaStream_t s = (cudaStream_t)stream;
   if (n <= 0 || !A || !V || lda < n || ldv < n) return MPJ_EINVAL;
-  if (ordering != MPJ_ORDER_CYCLIC && ordering != MPJ_ORDER_ROUND_ROBIN) return MPJ_EINVAL;
+  if (ordering != MPJ_ORDER_CYCLIC && ordering != MPJ_ORDER_ROUND_ROBIN && ordering != MPJ_ORDER_BLOCK)
+    return MPJ_EINVAL;
   void* w = nullptr;
-  size_t wbytes = mpj_jacobi64_scratch_bytes(n) + 4096;
+  size_t wbytes = mpj_jacobi64_scratch_bytes_ordering(n, ordering) + 4096;
   if (cudaMallocAsync(&w, wbytes, s) != cudaSuccess) return MPJ_ENOMEM;
   mpj_count_alloc();
   int st = MPJ_OK;

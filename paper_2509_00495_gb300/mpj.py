@@ -34,6 +34,7 @@ MPJ_ETIMEOUT = -8
 
 ORDER_CYCLIC = 0
 ORDER_ROUND_ROBIN = 1
+ORDER_BLOCK = 2
 METHOD_MIXED = 0
 METHOD_PLAIN = 1
 
@@ -141,7 +142,7 @@ def default_opts(**kw) -> Opts:
         if v is None:
             continue
         if k == "ordering" and isinstance(v, str):
-            v = {"cyclic": ORDER_CYCLIC, "round_robin": ORDER_ROUND_ROBIN}[v]
+            v = {"cyclic": ORDER_CYCLIC, "round_robin": ORDER_ROUND_ROBIN, "block": ORDER_BLOCK}[v]
         if k == "method" and isinstance(v, str):
             v = {"mixed": METHOD_MIXED, "plain": METHOD_PLAIN}[v]
         setattr(o, k, int(v) if isinstance(v, bool) else v)
@@ -231,7 +232,7 @@ def jacobi64(A: torch.Tensor, V: torch.Tensor | None = None, *, tol: float = 0.0
     A = _dev(A, "A")
     n = A.shape[0]
     if isinstance(ordering, str):
-        ordering = {"cyclic": ORDER_CYCLIC, "round_robin": ORDER_ROUND_ROBIN}[ordering]
+        ordering = {"cyclic": ORDER_CYCLIC, "round_robin": ORDER_ROUND_ROBIN, "block": ORDER_BLOCK}[ordering]
     At = A.T.contiguous()
     Vt = (torch.eye(n, dtype=torch.float64, device=A.device) if V is None else _dev(V, "V")).T.contiguous()
     sw, of = ctypes.c_int(), ctypes.c_double()
