@@ -243,6 +243,9 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--ref-step-seconds", type=float, default=8.0)
     ap.add_argument("--plain-solves", type=int, default=3)
+    ap.add_argument("--sweep-only", choices=["round_robin", "block", "cyclic"], default=None,
+                    help="time FP64 sweeps (mpj_jacobi64) of one ordering on a nearly diagonal n x n matrix; "
+                         "for profiling")
     ap.add_argument("--product-only", action="store_true",
                     help="time only the FP64-accurate tensor-core product (n x n x n, mpj_dgemm_tc); for profiling")
     args = ap.parse_args()
@@ -268,6 +271,9 @@ def main():
     n = args.n
     if args.product_only:
         product_only(mpj, torch, dev, n, args)
+        return
+    if args.sweep_only:
+        sweep_only(mpj, torch, dev, inputs, n, args)
         return
     A_np, lam = inputs.geo_4096(seed=0, n=n) if n == 4096 else inputs.geo_matrix(n, 1e6, seed=0)
     A = torch.from_numpy(A_np).to(dev)
@@ -474,6 +480,32 @@ def main():
         print(json.dumps(out), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+def sweep_only(mpj, torch, dev, inputs, n: int, args) -> None:
+    """`--warmup` then `--steps` single FP64 sweeps (mpj_jacobi64, max_sweeps 1)
+    of the chosen ordering on A = Q diag(lam) Q^T, Q within 1e-4 of I, lam
+    uniform in [-1, 1] (like the matrix the sweeps receive after
+    preconditioning), each on a fresh copy; CUDA-event timed; one JSON line."""
+    rng = np.random.default_rng(0)
+    lam = np.sort(rng.uniform(-1.0, 1.0, n))
+    A0 = torch.from_numpy(inputs.near_diagonal(n, lam, 1e-4, seed=0)).to(dev)
+    tol = float(n * U_D * torch.linalg.norm(A0).item())
+    ms = []
+    for i in range(args.warmup + args.steps):
+        A = A0.clone()
+        torch.cuda.synchronize()
+        e_a = torch.cuda.Event(enable_timing=True)
+        e_b = torch.cuda.Event(enable_timing=True)
+        e_a.record()
+        _, _, sw, off, st = mpj.jacobi64(A, tol=tol, ordering=args.sweep_only, max_sweeps=1)
+        e_b.record()
+        e_b.synchronize()
+        if i >= args.warmup:
+            ms.append(e_a.elapsed_time(e_b))
+    t = statistics.median(ms) if ms else float("nan")
+    print(json.dumps({"kernel": f"FP64 sweep ({args.sweep_only})", "n": n, "ms_per_sweep": t, "sweeps": sw,
+                      "off_after": off, "status": st}), flush=True)
 
 
 def product_only(mpj, torch, dev, n: int, args) -> None:

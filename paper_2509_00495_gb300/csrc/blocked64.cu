@@ -23,16 +23,20 @@
 // The right multiplication is FP64-accurate on the bf16 tensor cores: each
 // CTA takes 128 rows of X_P (K = 32 values each), finds each row's largest
 // exponent e_r (max |x_rk| < 2^e_r), and cuts x_rk * 2^(56 - e_r), rounded to
-// an integer Y (|Y| < 2^56; the rounding is below 2^(e_r - 57)), into seven
-// signed 8-bit digits with integer arithmetic (d_0 in [-256, 256], the others
-// in [-128, 128], each exactly a bf16).  U_P's columns are cut the same way
-// when the subproblem is solved.  The digit products of levels
-// L = i + j <= 6 (28 pairs) go to seven FP32 accumulators in tensor memory;
-// over K = 32 every level sum is an integer of magnitude at most 2^22.2, so
-// the accumulation is exact.  The epilogue reads the level sums, forms
+// an integer (magnitude below 2^56; the rounding is below 2^(e_r - 57)), into
+// seven signed digits of 8 bits (|d_0| <= 256, |d_i| <= 128, each exactly a
+// bf16).  U_P's columns are cut the same way when the subproblem is solved.
+// The digit products of levels L = i + j <= 6 (28 pairs) go to seven FP32
+// accumulators in tensor memory; over K = 32 a level sum is an integer of
+// magnitude at most (2 * 256 * 128 + 5 * 128^2) * 32 = 2^22.2.  Measured on
+// this GPU: the tensor cores' FP32 accumulation of such integer sums is exact
+// below 2^23 but not in [2^23, 2^24) (unsigned byte digits, whose level sums
+// reach 2^23.8, lost accuracy), so every bound here is kept below 2^23.  The epilogue reads the level sums, forms
 // Z = sum_L s_L 2^(8 (6 - L)) exactly in two 64-bit integers, rounds Z to FP64
 // once and scales by 2^(e_r + f_c - 64).  Dropped levels (L >= 7) are below
-// 2^-55 of max|x_r.| max|u_.c| per term.
+// 2^-55 of max|x_r.| max|u_.c| per term.  The epilogue uses integer
+// instructions only (no FP64: on this GPU an FP64 instruction costs 64 times
+// an FP32 one), so the products cost tensor time plus integer work.
 #include <cuda_bf16.h>
 #include <stdint.h>
 #include <stdio.h>
@@ -68,30 +72,45 @@ MPJ_DEV void block_pair(int nb, int R, int slot, int& I, int& J) {
 // core matrices (k-adjacent cores 128 bytes apart, 8-row groups 512 apart)
 MPJ_DEV int kmaj16(int row, int k) { return (((row >> 3) * 4 + (k >> 3)) << 7) + ((row & 7) << 4) + ((k & 7) << 1); }
 
-// The seven signed 8-bit digits of x on the grid 2^e (|x| < 2^e):
-// x = sum_i d_i 2^(e - 8 (i + 1)) + r, |r| <= 2^(e - 57).
-MPJ_DEV void digits8x7(double x, int e, int d[NSL]) {
-  const long long bits = __double_as_longlong(x);
+// The seven signed digits of x on the grid 2^e (|x| < 2^e), as bf16 bit
+// patterns: x = sum_i d_i 2^(e - 8 (i + 1)) + r, |r| <= 2^(e - 57),
+// |d_0| <= 256, |d_i| <= 128 (i >= 1).  Y = round(|x| 2^(56 - e)) < 2^56 is cut
+// into bytes and recentred from the least significant byte up (a byte of 128
+// or more becomes byte - 256 and carries 1 upward), in 32-bit integer
+// instructions; the digit magnitude m <= 256 becomes a bf16 through one FP32
+// add (the float 2^23 + m minus 2^23 is exactly m, and its top 16 bits are the
+// bf16 of m).  Centred digits keep every level sum of the products below 2^23
+// (see the file comment).
+MPJ_DEV void digits_bf16(double x, int e, unsigned short d[NSL]) {
+  const unsigned long long bits = (unsigned long long)__double_as_longlong(x);
   const int ex = (int)((bits >> 52) & 0x7FF);
-  const long long mant = bits & 0xFFFFFFFFFFFFFLL;
-  const long long M = ex ? (mant | (1LL << 52)) : mant;
-  const int eb = ex ? ex : 1;
-  const int sh = eb - 1019 - e;  // x 2^(56 - e) = M 2^sh, sh <= 3
-  long long Y;
+  const unsigned long long mant = bits & 0xFFFFFFFFFFFFFULL;
+  const unsigned long long M = ex ? (mant | (1ULL << 52)) : mant;
+  const int sh = (ex ? ex : 1) - 1019 - e;  // |x| 2^(56 - e) = M 2^sh, sh <= 3
+  unsigned long long Y;
   if (sh >= 0)
     Y = M << sh;
   else if (sh > -62)
-    Y = (M + (1LL << (-sh - 1))) >> (-sh);
+    Y = (M + (1ULL << (-sh - 1))) >> (-sh);
   else
     Y = 0;
-  if (bits < 0) Y = -Y;
+  const unsigned int hi = (unsigned int)(Y >> 32), lo = (unsigned int)Y;
+  const unsigned int neg = (unsigned int)(bits >> 63);
+  const unsigned int b[NSL] = {(hi >> 16) & 255u, (hi >> 8) & 255u, hi & 255u, lo >> 24, (lo >> 16) & 255u,
+                               (lo >> 8) & 255u, lo & 255u};
+  int carry = 0;
 #pragma unroll
-  for (int i = NSL - 1; i >= 1; --i) {
-    const long long r = ((Y + 128) & 255) - 128;
-    d[i] = (int)r;
-    Y = (Y - r) >> 8;
+  for (int i = NSL - 1; i >= 0; --i) {
+    int v = (int)b[i] + carry;  // in [0, 256]
+    if (i > 0) {
+      carry = (v + 128) >> 8;   // 1 when v >= 128
+      v -= carry << 8;          // in [-128, 127]
+    }
+    const unsigned int m = (unsigned int)(v < 0 ? -v : v);
+    const unsigned int sg = ((unsigned int)(v < 0) ^ neg) & (m != 0u);
+    const float f = __int_as_float(0x4B000000 | (int)m) - 8388608.0f;
+    d[i] = (unsigned short)((__float_as_uint(f) >> 16) | (sg << 15));
   }
-  d[0] = (int)Y;
 }
 
 MPJ_DEV int exp_of_max(double m) {
@@ -100,11 +119,66 @@ MPJ_DEV int exp_of_max(double m) {
   return e;
 }
 
+// The same from the bit pattern of max|x| (a non-negative double), with
+// integer instructions only: the smallest e with max|x| < 2^e (0 for zero).
+MPJ_DEV int exp_of_maxbits(unsigned long long b) {
+  if (b == 0) return 0;
+  const int ex = (int)(b >> 52);
+  if (ex > 0) return ex - 1022;                     // 1.m 2^(ex-1023) < 2^(ex-1022)
+  return (64 - __clzll((long long)b)) - 1074;       // subnormal: mant 2^-1074
+}
+
+// Z 2^E rounded to the nearest double (ties to even), Z = hi 2^32 + lo with
+// |Z| < 2^72, using integer instructions only.  Results outside the normal
+// range go through ldexp (never for the operands of the sweeps).
+MPJ_DEV double z_to_double(long long hi, long long lo, int E) {
+  unsigned long long zl = ((unsigned long long)hi << 32) + (unsigned long long)lo;
+  long long zh = (hi >> 32) + (lo >> 63) + (zl < (unsigned long long)lo ? 1 : 0);
+  const unsigned long long sign = zh < 0 ? (1ULL << 63) : 0ULL;
+  if (zh < 0) {  // |Z|
+    zl = ~zl + 1ULL;
+    zh = ~zh + (zl == 0 ? 1 : 0);
+  }
+  const unsigned long long h = (unsigned long long)zh;
+  if (h == 0 && zl == 0) return __longlong_as_double((long long)sign);
+  const int pos = h ? 127 - __clzll((long long)h) : 63 - __clzll((long long)zl);  // leading bit
+  unsigned long long mant;
+  if (pos <= 52) {
+    mant = zl << (52 - pos);
+  } else {
+    const int sh = pos - 52;  // 1 .. 72
+    unsigned long long lo_part, rnd, sticky;
+    if (sh < 64) {
+      mant = (zl >> sh) | (sh ? (h << (64 - sh)) : 0ULL);
+      rnd = (zl >> (sh - 1)) & 1ULL;
+      sticky = (sh >= 2) ? (zl & ((1ULL << (sh - 1)) - 1ULL)) : 0ULL;
+    } else {
+      mant = h >> (sh - 64);
+      rnd = (sh == 64) ? (zl >> 63) : ((h >> (sh - 65)) & 1ULL);
+      lo_part = (sh == 64) ? (zl & ((1ULL << 63) - 1ULL)) : (zl | (sh > 65 ? (h & ((1ULL << (sh - 65)) - 1ULL)) : 0ULL));
+      sticky = lo_part;
+    }
+    mant &= (1ULL << 53) - 1ULL;
+    if (rnd && (sticky || (mant & 1ULL))) ++mant;
+  }
+  int p2 = pos;
+  if (mant >> 53) {
+    mant >>= 1;
+    ++p2;
+  }
+  const int biased = p2 + E + 1023;
+  if (biased <= 0 || biased >= 2047) return ldexp(__longlong_as_double((long long)(sign | (1023ULL << 52) |
+                                                                                   (mant & ((1ULL << 52) - 1ULL)))),
+                                                 p2 + E);
+  return __longlong_as_double((long long)(sign | ((unsigned long long)biased << 52) | (mant & ((1ULL << 52) - 1ULL))));
+}
+
 // ---------------------------------------------------------------- subproblems
 // One CTA per block pair of round R: one inner round-robin sweep on the FP64
 // 32 x 32 subproblem (the paper's row update, column update and vector update
-// per rotation; the 16 disjoint rotations of an inner round are applied
-// together), then U_P's columns cut into digits for the tensor products.
+// per rotation, with c - 1 carried separately so that tiny rotations keep U
+// orthogonal, see common.cuh; the 16 disjoint rotations of an inner round are
+// applied together), then U_P's columns cut into digits for the tensor products.
 // Writes per block pair: NSL digit tiles (32 x 32 bf16, K-major over the
 // rows of U_P, one "row" per column of U_P), 32 column exponents, and whether
 // any rotation happened.
@@ -132,19 +206,11 @@ __global__ void __launch_bounds__(256) blk_solve(const double* __restrict__ A, i
       int x, y;
       rr_slot(W2, rho, tid, x, y);
       const int p = x < y ? x : y, q = x < y ? y : x;
-      const double app = S[p][p], aqq = S[q][q], apq = S[p][q];
-      int r = 0;
-      double c = 1.0, s = 0.0;
-      if (gidx(I, J, q) < n && fabs(apq) > skip * sqrt(fabs(app * aqq)) && fabs(apq) > skip_abs) {
-        // Algorithm 2, stable form (Appendix A approach 2)
-        const double tau = (aqq - app) / (2.0 * apq);
-        const double t = tau >= 0.0 ? 1.0 / (tau + sqrt(1.0 + tau * tau)) : 1.0 / (tau - sqrt(1.0 + tau * tau));
-        c = 1.0 / sqrt(1.0 + t * t);
-        s = t * c;
-        r = 1;
-        any = 1;
-      }
-      cs[tid][0] = c;
+      double t = 0.0, cm1 = 0.0, s = 0.0;
+      // Algorithm 2 (stable form) with the skip test of Algorithm 4
+      const int r = gidx(I, J, q) < n && jacobi_pair<double>(S[p][p], S[q][q], S[p][q], skip, t, cm1, s, skip_abs);
+      if (r) any = 1;
+      cs[tid][0] = cm1;
       cs[tid][1] = s;
       rot[tid] = r;
     }
@@ -156,10 +222,10 @@ __global__ void __launch_bounds__(256) blk_solve(const double* __restrict__ A, i
       int x, y;
       rr_slot(W2, rho, k, x, y);
       const int p = x < y ? x : y, q = x < y ? y : x;
-      const double c = cs[k][0], s = cs[k][1];
-      const double sp = S[p][j], sq = S[q][j];
-      S[p][j] = c * sp - s * sq;
-      S[q][j] = s * sp + c * sq;
+      double sp = S[p][j], sq = S[q][j];
+      rot_apply(cs[k][0], cs[k][1], sp, sq);
+      S[p][j] = sp;
+      S[q][j] = sq;
     }
     __syncthreads();
     // columns: S(:, [p q]) = S(:, [p q]) J;  vectors: U(:, [p q]) = U(:, [p q]) J
@@ -169,13 +235,52 @@ __global__ void __launch_bounds__(256) blk_solve(const double* __restrict__ A, i
       int x, y;
       rr_slot(W2, rho, k, x, y);
       const int p = x < y ? x : y, q = x < y ? y : x;
-      const double c = cs[k][0], s = cs[k][1];
-      const double sp = S[j][p], sq = S[j][q];
-      S[j][p] = c * sp - s * sq;
-      S[j][q] = s * sp + c * sq;
-      const double up = U[j][p], uq = U[j][q];
-      U[j][p] = c * up - s * uq;
-      U[j][q] = s * up + c * uq;
+      double sp = S[j][p], sq = S[j][q];
+      rot_apply(cs[k][0], cs[k][1], sp, sq);
+      S[j][p] = sp;
+      S[j][q] = sq;
+      double up = U[j][p], uq = U[j][q];
+      rot_apply(cs[k][0], cs[k][1], up, uq);
+      U[j][p] = up;
+      U[j][q] = uq;
+    }
+    __syncthreads();
+  }
+  // One Newton-Schulz step on U_P (Sec. 4.3.4): U <- U - U E / 2, E = U^T U - I.
+  // U_P carries the rounding of its 496 rotations; applied to all of A and V
+  // every round, that departure from orthogonality would accumulate over the
+  // sweeps, so each U_P is made orthogonal to working precision first.
+  {
+    double e4[4];
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      const int idx = tid + t * 256, i = idx % W2, j = idx / W2;
+      double acc = (i == j) ? -1.0 : 0.0;
+      for (int k = 0; k < W2; ++k) acc = fma(U[k][i], U[k][j], acc);
+      e4[t] = acc;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      const int idx = tid + t * 256, i = idx % W2, j = idx / W2;
+      S[i][j] = e4[t];  // S is free now: it holds E
+    }
+    __syncthreads();
+    // |E| is at the rounding level, so U E is formed in FP32 (its relative
+    // error 2^-24 of a 1e-15 correction is far below FP64 rounding)
+    double u4[4];
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      const int idx = tid + t * 256, i = idx % W2, j = idx / W2;
+      float acc = 0.0f;
+      for (int k = 0; k < W2; ++k) acc = fmaf((float)U[i][k], (float)S[k][j], acc);
+      u4[t] = fma(-0.5, (double)acc, U[i][j]);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      const int idx = tid + t * 256, i = idx % W2, j = idx / W2;
+      U[i][j] = u4[t];
     }
     __syncthreads();
   }
@@ -188,16 +293,17 @@ __global__ void __launch_bounds__(256) blk_solve(const double* __restrict__ A, i
     const int e = exp_of_max(m);
     Uexp[P * W2 + c] = e;
     for (int k0 = 0; k0 < W2; k0 += 8) {
-      int d[8][NSL];
+      unsigned short d[8][NSL];
 #pragma unroll
-      for (int j = 0; j < 8; ++j) digits8x7(U[k0 + j][c], e, d[j]);
+      for (int j = 0; j < 8; ++j) digits_bf16(U[k0 + j][c], e, d[j]);
 #pragma unroll
       for (int s = 0; s < NSL; ++s) {
-        __align__(16) __nv_bfloat16 q8[8];
-#pragma unroll
-        for (int j = 0; j < 8; ++j) q8[j] = __float2bfloat16((float)d[j][s]);
-        *reinterpret_cast<uint4*>(reinterpret_cast<char*>(dst + (size_t)s * (USL_BYTES / 2)) + kmaj16(c, k0)) =
-            *reinterpret_cast<const uint4*>(q8);
+        uint4 q;
+        q.x = (uint32_t)d[0][s] | ((uint32_t)d[1][s] << 16);
+        q.y = (uint32_t)d[2][s] | ((uint32_t)d[3][s] << 16);
+        q.z = (uint32_t)d[4][s] | ((uint32_t)d[5][s] << 16);
+        q.w = (uint32_t)d[6][s] | ((uint32_t)d[7][s] << 16);
+        *reinterpret_cast<uint4*>(reinterpret_cast<char*>(dst + (size_t)s * (USL_BYTES / 2)) + kmaj16(c, k0)) = q;
       }
     }
   }
@@ -251,6 +357,7 @@ struct __align__(1024) RmulSmem {
   unsigned char xs[NSL][XSL_BYTES];  // digits of the 128 x 32 tile of X_P
   unsigned char us[NSL][USL_BYTES];  // digits of U_P
   int uexp[W2];
+  int rexp[TM];
   uint64_t mbar;
   uint32_t tmem;
 };
@@ -260,15 +367,19 @@ enum { XMODE_COLS = 0, XMODE_ROWS = 1 };
 // Y[r, g_P(c)] = sum_k X_P(r, k) U_P(k, c) for the CTA's 128 rows r and block
 // pair P = blockIdx.y; X_P(r, k) = X[r + g_P(k) ldx] (XMODE_COLS) or
 // X[g_P(k) + r ldx] (XMODE_ROWS).  Y may alias X in XMODE_COLS (each CTA reads
-// and writes only its own rows of its own panel).
-__global__ void __launch_bounds__(TM, 2) blk_rmul(const double* X, int ldx, int xmode, double* Y, int ldy, int n,
-                                                  int nb, int R, const __nv_bfloat16* __restrict__ Usl,
-                                                  const int* __restrict__ Uexp, unsigned* __restrict__ flags) {
+// and writes only its own rows of its own panel).  256 threads: thread t
+// digitizes row t/2 over block half t%2 (the 16 indices of block I or J);
+// warp w reads the TMEM lanes of rows 32 (w mod 4) .. +31 and the 16 output
+// columns 16 (w / 4) .. +15 of each level.
+constexpr int RM_THREADS = 256;
+
+__global__ void __launch_bounds__(RM_THREADS, 2)
+    blk_rmul(const double* X, int ldx, int xmode, double* Y, int ldy, int n, int nb, int R,
+             const __nv_bfloat16* __restrict__ Usl, const int* __restrict__ Uexp, unsigned* __restrict__ flags) {
   extern __shared__ __align__(1024) unsigned char dsm_raw[];
   RmulSmem& sm = *reinterpret_cast<RmulSmem*>(dsm_raw + ((1024 - (smem_u32(dsm_raw) & 1023)) & 1023));
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int P = blockIdx.y;
-  const int row = blockIdx.x * TM + tid;
   int I, J;
   block_pair(nb, R, P, I, J);
   if (warp == 0) {
@@ -282,39 +393,54 @@ __global__ void __launch_bounds__(TM, 2) blk_rmul(const double* X, int ldx, int 
   {
     const uint4* src = reinterpret_cast<const uint4*>(Usl + (size_t)P * NSL * (USL_BYTES / 2));
     uint4* dst = reinterpret_cast<uint4*>(sm.us[0]);
-    for (int i = tid; i < NSL * USL_BYTES / 16; i += TM) dst[i] = src[i];
+    for (int i = tid; i < NSL * USL_BYTES / 16; i += RM_THREADS) dst[i] = src[i];
     if (tid < W2) sm.uexp[tid] = Uexp[P * W2 + tid];
   }
-  // this thread's row of X_P: 32 values, its exponent and digits
-  double x[W2];
-  if (xmode == XMODE_COLS) {
+  // digits of X_P: this thread's row, 16 values of one block
+  {
+    const int rl = tid >> 1, half = tid & 1;
+    const int row = blockIdx.x * TM + rl;
+    const int g0 = (half ? J : I) * BS;  // first global index of this block
+    double x[BS];
+    if (xmode == XMODE_COLS) {
 #pragma unroll
-    for (int k = 0; k < W2; ++k) {
-      const int g = gidx(I, J, k);
-      x[k] = (row < n && g < n) ? X[(size_t)g * ldx + row] : 0.0;
+      for (int k = 0; k < BS; ++k) x[k] = (row < n && g0 + k < n) ? X[(size_t)(g0 + k) * ldx + row] : 0.0;
+    } else if (row < n && g0 + BS <= n && ((((size_t)row * ldx + g0) & 1) == 0)) {
+      const double2* src = reinterpret_cast<const double2*>(X + (size_t)row * ldx + g0);
+#pragma unroll
+      for (int k = 0; k < BS / 2; ++k) {
+        const double2 v = src[k];
+        x[2 * k] = v.x;
+        x[2 * k + 1] = v.y;
+      }
+    } else {
+#pragma unroll
+      for (int k = 0; k < BS; ++k) x[k] = (row < n && g0 + k < n) ? X[(size_t)row * ldx + g0 + k] : 0.0;
     }
-  } else {
+    unsigned long long maxbits = 0;
 #pragma unroll
-    for (int k = 0; k < W2; ++k) {
-      const int g = gidx(I, J, k);
-      x[k] = (row < n && g < n) ? X[(size_t)row * ldx + g] : 0.0;
+    for (int k = 0; k < BS; ++k) {
+      const unsigned long long b = (unsigned long long)__double_as_longlong(x[k]) & 0x7FFFFFFFFFFFFFFFULL;
+      maxbits = b > maxbits ? b : maxbits;
     }
-  }
-  double m = 0.0;
+    const unsigned long long other = __shfl_xor_sync(0xffffffffu, maxbits, 1);
+    maxbits = other > maxbits ? other : maxbits;
+    const int er = exp_of_maxbits(maxbits);
+    if (half == 0) sm.rexp[rl] = er;
 #pragma unroll
-  for (int k = 0; k < W2; ++k) m = fmax(m, fabs(x[k]));
-  const int er = exp_of_max(m);
+    for (int k0 = 0; k0 < BS; k0 += 8) {
+      unsigned short d[8][NSL];
 #pragma unroll
-  for (int k0 = 0; k0 < W2; k0 += 8) {
-    int d[8][NSL];
+      for (int j = 0; j < 8; ++j) digits_bf16(x[k0 + j], er, d[j]);
 #pragma unroll
-    for (int j = 0; j < 8; ++j) digits8x7(x[k0 + j], er, d[j]);
-#pragma unroll
-    for (int s = 0; s < NSL; ++s) {
-      __align__(16) __nv_bfloat16 q8[8];
-#pragma unroll
-      for (int j = 0; j < 8; ++j) q8[j] = __float2bfloat16((float)d[j][s]);
-      *reinterpret_cast<uint4*>(sm.xs[s] + kmaj16(tid, k0)) = *reinterpret_cast<const uint4*>(q8);
+      for (int s = 0; s < NSL; ++s) {
+        uint4 q;
+        q.x = (uint32_t)d[0][s] | ((uint32_t)d[1][s] << 16);
+        q.y = (uint32_t)d[2][s] | ((uint32_t)d[3][s] << 16);
+        q.z = (uint32_t)d[4][s] | ((uint32_t)d[5][s] << 16);
+        q.w = (uint32_t)d[6][s] | ((uint32_t)d[7][s] << 16);
+        *reinterpret_cast<uint4*>(sm.xs[s] + kmaj16(rl, half * BS + k0)) = q;
+      }
     }
   }
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -357,21 +483,28 @@ __global__ void __launch_bounds__(TM, 2) blk_rmul(const double* X, int ldx, int 
   }
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   if (ok) {
+    const int quad = warp & 3, ch = warp >> 2;
+    const int rl = quad * 32 + lane;
+    const int row = blockIdx.x * TM + rl;
     // Z = sum_L s_L 2^(8 (6 - L)) = hi 2^32 + lo, hi = s0 2^16 + s1 2^8 + s2, lo = s3 2^24 + s4 2^16 + s5 2^8 + s6
-    long long hi[W2], lo[W2];
+    long long hi[BS], lo[BS];
 #pragma unroll
-    for (int c = 0; c < W2; ++c) {
+    for (int c = 0; c < BS; ++c) {
       hi[c] = 0;
       lo[c] = 0;
     }
 #pragma unroll 1
     for (int l = 0; l < NLEV; ++l) {
-      uint32_t v[32];
-      BLK_LD32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(l * W2), v);
+      uint32_t v[16];
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+          : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+            "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+          : "r"(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(l * W2 + ch * BS)));
       asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
       const int sh = l < 3 ? 8 * (2 - l) : 8 * (6 - l);
 #pragma unroll
-      for (int c = 0; c < W2; ++c) {
+      for (int c = 0; c < BS; ++c) {
         const long long q = (long long)__float2int_rz(__uint_as_float(v[c]));  // exact integer below 2^24
         if (l < 3)
           hi[c] += q << sh;
@@ -380,14 +513,11 @@ __global__ void __launch_bounds__(TM, 2) blk_rmul(const double* X, int ldx, int 
       }
     }
     if (row < n) {
+      const int er = sm.rexp[rl];
+      const int g0 = (ch ? J : I) * BS;
 #pragma unroll
-      for (int c = 0; c < W2; ++c) {
-        const int g = gidx(I, J, c);
-        if (g < n) {
-          const double z = fma((double)hi[c], 0x1p32, (double)lo[c]);  // Z rounded once
-          Y[(size_t)g * ldy + row] = ldexp(z, er + sm.uexp[c] - 64);
-        }
-      }
+      for (int c = 0; c < BS; ++c)
+        if (g0 + c < n) Y[(size_t)(g0 + c) * ldy + row] = z_to_double(hi[c], lo[c], er + sm.uexp[ch * BS + c] - 64);
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -430,11 +560,11 @@ cudaError_t mpj_blocked_round(double* A, int lda, double* V, int ldv, double* B,
   }
   const dim3 grid((n + TM - 1) / TM, npairs);
   // B = A U~ ; A = B^T U~ (= U~^T A U~) ; V = V U~
-  blk_rmul<<<grid, TM, smem, s>>>(A, lda, XMODE_COLS, B, n, n, nb, R, Usl, Uexp, flags);
+  blk_rmul<<<grid, RM_THREADS, smem, s>>>(A, lda, XMODE_COLS, B, n, n, nb, R, Usl, Uexp, flags);
   mpj_count_launch();
-  blk_rmul<<<grid, TM, smem, s>>>(B, n, XMODE_ROWS, A, lda, n, nb, R, Usl, Uexp, flags);
+  blk_rmul<<<grid, RM_THREADS, smem, s>>>(B, n, XMODE_ROWS, A, lda, n, nb, R, Usl, Uexp, flags);
   mpj_count_launch();
-  blk_rmul<<<grid, TM, smem, s>>>(V, ldv, XMODE_COLS, V, ldv, n, nb, R, Usl, Uexp, flags);
+  blk_rmul<<<grid, RM_THREADS, smem, s>>>(V, ldv, XMODE_COLS, V, ldv, n, nb, R, Usl, Uexp, flags);
   mpj_count_launch();
   return cudaGetLastError();
 }
