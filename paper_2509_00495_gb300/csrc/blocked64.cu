@@ -72,16 +72,17 @@ MPJ_DEV void block_pair(int nb, int R, int slot, int& I, int& J) {
 // core matrices (k-adjacent cores 128 bytes apart, 8-row groups 512 apart)
 MPJ_DEV int kmaj16(int row, int k) { return (((row >> 3) * 4 + (k >> 3)) << 7) + ((row & 7) << 4) + ((k & 7) << 1); }
 
-// The seven signed digits of x on the grid 2^e (|x| < 2^e), as bf16 bit
-// patterns: x = sum_i d_i 2^(e - 8 (i + 1)) + r, |r| <= 2^(e - 57),
-// |d_0| <= 256, |d_i| <= 128 (i >= 1).  Y = round(|x| 2^(56 - e)) < 2^56 is cut
-// into bytes and recentred from the least significant byte up (a byte of 128
-// or more becomes byte - 256 and carries 1 upward), in 32-bit integer
-// instructions; the digit magnitude m <= 256 becomes a bf16 through one FP32
-// add (the float 2^23 + m minus 2^23 is exactly m, and its top 16 bits are the
-// bf16 of m).  Centred digits keep every level sum of the products below 2^23
-// (see the file comment).
-MPJ_DEV void digits_bf16(double x, int e, unsigned short d[NSL]) {
+// The seven signed digits of x on the grid 2^e (|x| < 2^e): x = sum_i d_i
+// 2^(e - 8 (i + 1)) + r, |r| <= 2^(e - 57), |d_0| <= 256, |d_i| <= 128 (i >= 1),
+// returned as FP32 bit patterns (exact small integers; their top 16 bits are
+// the bf16).  Y = round(|x| 2^(56 - e)) < 2^56; adding 128 to each of its six
+// low bytes (one 64-bit add, carries included) makes byte j of the sum
+// d_(6-j) + 128 for centred digits d in [-128, 127], and the part above bit 48
+// d_0 in [0, 256].  A byte b becomes a float through the bit pattern of
+// 2^23 + b (one byte permute), then one FMA gives sign(x) (b - 128).
+// Centred digits keep every level sum of the products below 2^23 (see the
+// file comment).
+MPJ_DEV void digits_f32(double x, int e, uint32_t d[NSL]) {
   const unsigned long long bits = (unsigned long long)__double_as_longlong(x);
   const int ex = (int)((bits >> 52) & 0x7FF);
   const unsigned long long mant = bits & 0xFFFFFFFFFFFFFULL;
@@ -94,24 +95,22 @@ MPJ_DEV void digits_bf16(double x, int e, unsigned short d[NSL]) {
     Y = (M + (1ULL << (-sh - 1))) >> (-sh);
   else
     Y = 0;
-  const unsigned int hi = (unsigned int)(Y >> 32), lo = (unsigned int)Y;
-  const unsigned int neg = (unsigned int)(bits >> 63);
-  const unsigned int b[NSL] = {(hi >> 16) & 255u, (hi >> 8) & 255u, hi & 255u, lo >> 24, (lo >> 16) & 255u,
-                               (lo >> 8) & 255u, lo & 255u};
-  int carry = 0;
-#pragma unroll
-  for (int i = NSL - 1; i >= 0; --i) {
-    int v = (int)b[i] + carry;  // in [0, 256]
-    if (i > 0) {
-      carry = (v + 128) >> 8;   // 1 when v >= 128
-      v -= carry << 8;          // in [-128, 127]
-    }
-    const unsigned int m = (unsigned int)(v < 0 ? -v : v);
-    const unsigned int sg = ((unsigned int)(v < 0) ^ neg) & (m != 0u);
-    const float f = __int_as_float(0x4B000000 | (int)m) - 8388608.0f;
-    d[i] = (unsigned short)((__float_as_uint(f) >> 16) | (sg << 15));
-  }
+  const unsigned long long T = Y + 0x0000808080808080ULL;
+  const uint32_t lo = (uint32_t)T, hi = (uint32_t)(T >> 32);
+  const float sg = (bits >> 63) ? -1.0f : 1.0f;
+  const float c128 = -8388736.0f * sg;  // -(2^23 + 128) sign(x)
+  // bytes of lo: d6+128, d5+128, d4+128, d3+128; of hi: d2+128, d1+128; hi >> 16: d0
+  d[6] = __float_as_uint(fmaf(__uint_as_float(__byte_perm(lo, 0x4B00u, 0x5440)), sg, c128));
+  d[5] = __float_as_uint(fmaf(__uint_as_float(__byte_perm(lo, 0x4B00u, 0x5441)), sg, c128));
+  d[4] = __float_as_uint(fmaf(__uint_as_float(__byte_perm(lo, 0x4B00u, 0x5442)), sg, c128));
+  d[3] = __float_as_uint(fmaf(__uint_as_float(__byte_perm(lo, 0x4B00u, 0x5443)), sg, c128));
+  d[2] = __float_as_uint(fmaf(__uint_as_float(__byte_perm(hi, 0x4B00u, 0x5440)), sg, c128));
+  d[1] = __float_as_uint(fmaf(__uint_as_float(__byte_perm(hi, 0x4B00u, 0x5441)), sg, c128));
+  d[0] = __float_as_uint(fmaf(__uint_as_float(0x4B000000u | (hi >> 16)), sg, -8388608.0f * sg));
 }
+
+// Two FP32 digit patterns packed as two bf16 (a in the low half).
+MPJ_DEV uint32_t pack_bf16x2(uint32_t a, uint32_t b) { return __byte_perm(a, b, 0x7632); }
 
 MPJ_DEV int exp_of_max(double m) {
   int e = 0;
@@ -293,16 +292,16 @@ __global__ void __launch_bounds__(256) blk_solve(const double* __restrict__ A, i
     const int e = exp_of_max(m);
     Uexp[P * W2 + c] = e;
     for (int k0 = 0; k0 < W2; k0 += 8) {
-      unsigned short d[8][NSL];
+      uint32_t d[8][NSL];
 #pragma unroll
-      for (int j = 0; j < 8; ++j) digits_bf16(U[k0 + j][c], e, d[j]);
+      for (int j = 0; j < 8; ++j) digits_f32(U[k0 + j][c], e, d[j]);
 #pragma unroll
       for (int s = 0; s < NSL; ++s) {
         uint4 q;
-        q.x = (uint32_t)d[0][s] | ((uint32_t)d[1][s] << 16);
-        q.y = (uint32_t)d[2][s] | ((uint32_t)d[3][s] << 16);
-        q.z = (uint32_t)d[4][s] | ((uint32_t)d[5][s] << 16);
-        q.w = (uint32_t)d[6][s] | ((uint32_t)d[7][s] << 16);
+        q.x = pack_bf16x2(d[0][s], d[1][s]);
+        q.y = pack_bf16x2(d[2][s], d[3][s]);
+        q.z = pack_bf16x2(d[4][s], d[5][s]);
+        q.w = pack_bf16x2(d[6][s], d[7][s]);
         *reinterpret_cast<uint4*>(reinterpret_cast<char*>(dst + (size_t)s * (USL_BYTES / 2)) + kmaj16(c, k0)) = q;
       }
     }
@@ -429,16 +428,16 @@ __global__ void __launch_bounds__(RM_THREADS, 2)
     if (half == 0) sm.rexp[rl] = er;
 #pragma unroll
     for (int k0 = 0; k0 < BS; k0 += 8) {
-      unsigned short d[8][NSL];
+      uint32_t d[8][NSL];
 #pragma unroll
-      for (int j = 0; j < 8; ++j) digits_bf16(x[k0 + j], er, d[j]);
+      for (int j = 0; j < 8; ++j) digits_f32(x[k0 + j], er, d[j]);
 #pragma unroll
       for (int s = 0; s < NSL; ++s) {
         uint4 q;
-        q.x = (uint32_t)d[0][s] | ((uint32_t)d[1][s] << 16);
-        q.y = (uint32_t)d[2][s] | ((uint32_t)d[3][s] << 16);
-        q.z = (uint32_t)d[4][s] | ((uint32_t)d[5][s] << 16);
-        q.w = (uint32_t)d[6][s] | ((uint32_t)d[7][s] << 16);
+        q.x = pack_bf16x2(d[0][s], d[1][s]);
+        q.y = pack_bf16x2(d[2][s], d[3][s]);
+        q.z = pack_bf16x2(d[4][s], d[5][s]);
+        q.w = pack_bf16x2(d[6][s], d[7][s]);
         *reinterpret_cast<uint4*>(sm.xs[s] + kmaj16(rl, half * BS + k0)) = q;
       }
     }
@@ -530,41 +529,85 @@ inline size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 }  // namespace
 
-size_t mpj_blocked_scratch_bytes(int n) {
-  const int N = (n + 2 * BS - 1) / (2 * BS) * (2 * BS);
-  const int npairs = N / (2 * BS);
+// One set of U_P digit tiles, exponents and rotation flags for a round.
+static size_t uset_bytes(int npairs) {
   return al256((size_t)npairs * NSL * USL_BYTES) + al256((size_t)npairs * W2 * sizeof(int)) +
-         al256((size_t)npairs * sizeof(int)) + 256;
+         al256((size_t)npairs * sizeof(int));
 }
 
-cudaError_t mpj_blocked_round(double* A, int lda, double* V, int ldv, double* B, int n, int R, double skip,
-                              double skip_abs, void* scratch, unsigned* flags, cudaStream_t s) {
+// Two sets (rounds alternate between them, so the V update of a round may
+// still read its set while the next round's subproblems write the other).
+size_t mpj_blocked_scratch_bytes(int n) {
   const int N = (n + 2 * BS - 1) / (2 * BS) * (2 * BS);
-  const int nb = N / BS, npairs = nb / 2;
-  char* base = (char*)scratch;
-  __nv_bfloat16* Usl = (__nv_bfloat16*)base;
-  int* Uexp = (int*)(base + al256((size_t)npairs * NSL * USL_BYTES));
-  int* rotated = (int*)((char*)Uexp + al256((size_t)npairs * W2 * sizeof(int)));
-  blk_solve<<<npairs, 256, 0, s>>>(A, lda, n, nb, R, skip, skip_abs, Usl, Uexp, rotated);
-  mpj_count_launch();
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
+  return 2 * uset_bytes(N / (2 * BS)) + 256;
+}
+
+namespace {
+struct USet {
+  __nv_bfloat16* sl;
+  int* ex;
+  int* rot;
+};
+USet uset(void* scratch, int n, int parity) {
+  const int N = (n + 2 * BS - 1) / (2 * BS) * (2 * BS);
+  const int npairs = N / (2 * BS);
+  char* base = (char*)scratch + (size_t)parity * uset_bytes(npairs);
+  USet u;
+  u.sl = (__nv_bfloat16*)base;
+  u.ex = (int*)(base + al256((size_t)npairs * NSL * USL_BYTES));
+  u.rot = (int*)((char*)u.ex + al256((size_t)npairs * W2 * sizeof(int)));
+  return u;
+}
+size_t rmul_smem() {
   // at least 80 KB of shared memory per CTA: at most two CTAs per SM, the two
   // that the 512 TMEM columns hold (256 each), so no CTA waits in tcgen05.alloc
-  const size_t smem = sizeof(RmulSmem) + 1024 > 80 * 1024 ? sizeof(RmulSmem) + 1024 : 80 * 1024;
-  static bool attr_set = false;
-  if (!attr_set) {
-    e = cudaFuncSetAttribute(blk_rmul, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    attr_set = true;
-  }
-  const dim3 grid((n + TM - 1) / TM, npairs);
-  // B = A U~ ; A = B^T U~ (= U~^T A U~) ; V = V U~
-  blk_rmul<<<grid, RM_THREADS, smem, s>>>(A, lda, XMODE_COLS, B, n, n, nb, R, Usl, Uexp, flags);
+  return sizeof(RmulSmem) + 1024 > 80 * 1024 ? sizeof(RmulSmem) + 1024 : 80 * 1024;
+}
+cudaError_t rmul_attr() {
+  static bool done = false;
+  if (done) return cudaSuccess;
+  cudaError_t e = cudaFuncSetAttribute(blk_rmul, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rmul_smem());
+  if (e == cudaSuccess) done = true;
+  return e;
+}
+}  // namespace
+
+// Round R, step 1: the subproblems of the block pairs, U_P into set R mod 2.
+cudaError_t mpj_blocked_solve(const double* A, int lda, int n, int R, double skip, double skip_abs, void* scratch,
+                              cudaStream_t s) {
+  const int N = (n + 2 * BS - 1) / (2 * BS) * (2 * BS);
+  const int nb = N / BS;
+  const USet u = uset(scratch, n, R & 1);
+  blk_solve<<<nb / 2, 256, 0, s>>>(A, lda, n, nb, R, skip, skip_abs, u.sl, u.ex, u.rot);
   mpj_count_launch();
-  blk_rmul<<<grid, RM_THREADS, smem, s>>>(B, n, XMODE_ROWS, A, lda, n, nb, R, Usl, Uexp, flags);
+  return cudaGetLastError();
+}
+
+// Round R, step 2: A <- U~^T A U~ through B (two right multiplications).
+cudaError_t mpj_blocked_update_A(double* A, int lda, double* B, int n, int R, void* scratch, unsigned* flags,
+                                 cudaStream_t s) {
+  const int N = (n + 2 * BS - 1) / (2 * BS) * (2 * BS);
+  const int nb = N / BS;
+  const USet u = uset(scratch, n, R & 1);
+  cudaError_t e = rmul_attr();
+  if (e != cudaSuccess) return e;
+  const dim3 grid((n + TM - 1) / TM, nb / 2);
+  blk_rmul<<<grid, RM_THREADS, rmul_smem(), s>>>(A, lda, XMODE_COLS, B, n, n, nb, R, u.sl, u.ex, flags);
   mpj_count_launch();
-  blk_rmul<<<grid, RM_THREADS, smem, s>>>(V, ldv, XMODE_COLS, V, ldv, n, nb, R, Usl, Uexp, flags);
+  blk_rmul<<<grid, RM_THREADS, rmul_smem(), s>>>(B, n, XMODE_ROWS, A, lda, n, nb, R, u.sl, u.ex, flags);
+  mpj_count_launch();
+  return cudaGetLastError();
+}
+
+// Round R, step 3: V <- V U~ (in place); independent of step 2.
+cudaError_t mpj_blocked_update_V(double* V, int ldv, int n, int R, void* scratch, unsigned* flags, cudaStream_t s) {
+  const int N = (n + 2 * BS - 1) / (2 * BS) * (2 * BS);
+  const int nb = N / BS;
+  const USet u = uset(scratch, n, R & 1);
+  cudaError_t e = rmul_attr();
+  if (e != cudaSuccess) return e;
+  const dim3 grid((n + TM - 1) / TM, nb / 2);
+  blk_rmul<<<grid, RM_THREADS, rmul_smem(), s>>>(V, ldv, XMODE_COLS, V, ldv, n, nb, R, u.sl, u.ex, flags);
   mpj_count_launch();
   return cudaGetLastError();
 }

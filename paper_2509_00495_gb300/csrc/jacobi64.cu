@@ -897,13 +897,41 @@ int mpj_jacobi64_run(int n, double* A, int lda, double* V, int ldv, double tol, 
     unsigned hflags = 0;
     MPJ_CUDA_TRY(cudaMemsetAsync(bflags, 0, sizeof(unsigned), s));
     const int rounds = mpj_blocked_rounds_per_sweep(n);
+    // V <- V U~ of round R runs on a private side stream, overlapping round
+    // R+1's subproblems and A update; the U_P sets alternate between rounds,
+    // and round R+2's subproblems wait for round R's V update before
+    // overwriting its set.  The side stream is joined at every sweep end.
+    std::unique_ptr<SideStream> side;
+    if (side_stream && overlap_enabled(n)) {
+      side.reset(new SideStream(s));
+      if (!side->ok) side.reset();
+    }
+    bool vpending[2] = {false, false};
     while (off > tol && n > 1) {
       if (sweeps >= max_sweeps) {
         status = MPJ_NOT_CONVERGED;
         break;
       }
-      for (int R = 0; R < rounds; ++R)
-        MPJ_CUDA_TRY(mpj_blocked_round(A, lda, V, ldv, B, n, R, skip, skip_abs, bscratch, bflags, s));
+      for (int R = 0; R < rounds; ++R) {
+        const int par = R & 1;
+        if (side && vpending[par]) MPJ_CUDA_TRY(cudaStreamWaitEvent(s, side->done[par], 0));
+        MPJ_CUDA_TRY(mpj_blocked_solve(A, lda, n, R, skip, skip_abs, bscratch, s));
+        if (side) {
+          MPJ_CUDA_TRY(cudaEventRecord(side->ready, s));
+          MPJ_CUDA_TRY(cudaStreamWaitEvent(side->sv, side->ready, 0));
+          MPJ_CUDA_TRY(mpj_blocked_update_V(V, ldv, n, R, bscratch, bflags, side->sv));
+          MPJ_CUDA_TRY(cudaEventRecord(side->done[par], side->sv));
+          vpending[par] = true;
+        } else {
+          MPJ_CUDA_TRY(mpj_blocked_update_V(V, ldv, n, R, bscratch, bflags, s));
+        }
+        MPJ_CUDA_TRY(mpj_blocked_update_A(A, lda, B, n, R, bscratch, bflags, s));
+      }
+      if (side) {
+        for (int par = 0; par < 2; ++par)
+          if (vpending[par]) MPJ_CUDA_TRY(cudaStreamWaitEvent(s, side->done[par], 0));
+        vpending[0] = vpending[1] = false;
+      }
       MPJ_CUDA_TRY(mpj_blocked_symmetrize(A, lda, n, s));
       ++sweeps;
       MPJ_CUDA_TRY(mpj_sumsq(A, lda, n, true, partial, dscal, nullptr, s));

@@ -12,12 +12,16 @@ size_t mpj_jacobi64_scratch_bytes_rv(int n, int rv);
 size_t mpj_jacobi64_scratch_bytes_ordering(int n, int ordering);
 
 // Block round-robin FP64 sweeps with tensor-core block updates (blocked64.cu):
-// one outer round R (subproblem solves, then A <- U~^T A U~ and V <- V U~
-// through the n x n buffer B), the scratch it needs, rounds per sweep, and
-// the end-of-sweep symmetrization.
+// outer round R is the subproblem solves (U_P into set R mod 2 of the
+// scratch), then A <- U~^T A U~ (through the n x n buffer B) and V <- V U~,
+// the two updates independent of each other; the scratch they need, rounds
+// per sweep, and the end-of-sweep symmetrization.
 size_t mpj_blocked_scratch_bytes(int n);
-cudaError_t mpj_blocked_round(double* A, int lda, double* V, int ldv, double* B, int n, int R, double skip,
-                              double skip_abs, void* scratch, unsigned* flags, cudaStream_t s);
+cudaError_t mpj_blocked_solve(const double* A, int lda, int n, int R, double skip, double skip_abs, void* scratch,
+                              cudaStream_t s);
+cudaError_t mpj_blocked_update_A(double* A, int lda, double* B, int n, int R, void* scratch, unsigned* flags,
+                                 cudaStream_t s);
+cudaError_t mpj_blocked_update_V(double* V, int ldv, int n, int R, void* scratch, unsigned* flags, cudaStream_t s);
 int mpj_blocked_rounds_per_sweep(int n);
 cudaError_t mpj_blocked_symmetrize(double* A, int lda, int n, cudaStream_t s);
 
