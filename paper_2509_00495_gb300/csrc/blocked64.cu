@@ -17,7 +17,9 @@
 // run as three block-diagonal right multiplications, each panel
 // Y[:, P] = X_P U_P with X_P one of
 //   A[:, P]          (B = A U~),
-//   B[P, :]^T        (C = B^T U~ = U~^T A U~ for symmetric A, written to A),
+//   B[P, :]^T        (C = B^T U~ = U~^T A U~ for symmetric A, written to A:
+//                     only its lower triangle is formed, each entry also
+//                     written to its mirror, so A stays exactly symmetric),
 //   V[:, P]          (V <- V U~, in place).
 //
 // The right multiplication is FP64-accurate on the bf16 tensor cores: each
@@ -200,6 +202,11 @@ __global__ void __launch_bounds__(256) blk_solve(const double* __restrict__ A, i
     U[li][lj] = (li == lj) ? 1.0 : 0.0;
   }
   __syncthreads();
+  // Each inner round: the 16 rotation records, then every 2 x 2 block of S
+  // between two pairs a <= b once (rows by J_a, then columns by J_b, as the
+  // sequential order does for a before b; the mirror block is the same values
+  // transposed) and the two columns of U of every pair.
+  __shared__ int pq[W2 / 2][2];
   for (int rho = 0; rho < W2 - 1; ++rho) {
     if (tid < W2 / 2) {
       int x, y;
@@ -212,36 +219,49 @@ __global__ void __launch_bounds__(256) blk_solve(const double* __restrict__ A, i
       cs[tid][0] = cm1;
       cs[tid][1] = s;
       rot[tid] = r;
+      pq[tid][0] = p;
+      pq[tid][1] = q;
     }
     __syncthreads();
-    // rows: S([p q], :) = J^T S([p q], :)
-    for (int e = tid; e < (W2 / 2) * W2; e += blockDim.x) {
-      const int k = e / W2, j = e % W2;
-      if (!rot[k]) continue;
-      int x, y;
-      rr_slot(W2, rho, k, x, y);
-      const int p = x < y ? x : y, q = x < y ? y : x;
-      double sp = S[p][j], sq = S[q][j];
-      rot_apply(cs[k][0], cs[k][1], sp, sq);
-      S[p][j] = sp;
-      S[q][j] = sq;
-    }
-    __syncthreads();
-    // columns: S(:, [p q]) = S(:, [p q]) J;  vectors: U(:, [p q]) = U(:, [p q]) J
-    for (int e = tid; e < (W2 / 2) * W2; e += blockDim.x) {
-      const int k = e / W2, j = e % W2;
-      if (!rot[k]) continue;
-      int x, y;
-      rr_slot(W2, rho, k, x, y);
-      const int p = x < y ? x : y, q = x < y ? y : x;
-      double sp = S[j][p], sq = S[j][q];
-      rot_apply(cs[k][0], cs[k][1], sp, sq);
-      S[j][p] = sp;
-      S[j][q] = sq;
-      double up = U[j][p], uq = U[j][q];
-      rot_apply(cs[k][0], cs[k][1], up, uq);
-      U[j][p] = up;
-      U[j][q] = uq;
+    for (int task = tid; task < 136 + (W2 / 2) * W2; task += blockDim.x) {
+      if (task < 136) {
+        // pair indices a <= b from the triangular task number
+        int a = 0, rem = task;
+        while (rem >= 16 - a) {
+          rem -= 16 - a;
+          ++a;
+        }
+        const int b = a + rem;
+        if (!rot[a] && !rot[b]) continue;
+        const int pa = pq[a][0], qa = pq[a][1], pb = pq[b][0], qb = pq[b][1];
+        double b00 = S[pa][pb], b01 = S[pa][qb], b10 = S[qa][pb], b11 = S[qa][qb];
+        if (rot[a]) {
+          rot_apply(cs[a][0], cs[a][1], b00, b10);  // rows pa, qa of column pb
+          rot_apply(cs[a][0], cs[a][1], b01, b11);  // of column qb
+        }
+        if (rot[b]) {
+          rot_apply(cs[b][0], cs[b][1], b00, b01);  // columns pb, qb of row pa
+          rot_apply(cs[b][0], cs[b][1], b10, b11);  // of row qa
+        }
+        S[pa][pb] = b00;
+        S[pa][qb] = b01;
+        S[qa][pb] = b10;
+        S[qa][qb] = b11;
+        if (a != b) {
+          S[pb][pa] = b00;
+          S[qb][pa] = b01;
+          S[pb][qa] = b10;
+          S[qb][qa] = b11;
+        }
+      } else {
+        const int e = task - 136, k = e / W2, j = e % W2;
+        if (!rot[k]) continue;
+        const int p = pq[k][0], q = pq[k][1];
+        double up = U[j][p], uq = U[j][q];
+        rot_apply(cs[k][0], cs[k][1], up, uq);
+        U[j][p] = up;
+        U[j][q] = uq;
+      }
     }
     __syncthreads();
   }
@@ -250,20 +270,35 @@ __global__ void __launch_bounds__(256) blk_solve(const double* __restrict__ A, i
   // every round, that departure from orthogonality would accumulate over the
   // sweeps, so each U_P is made orthogonal to working precision first.
   {
-    double e4[4];
+    // E is symmetric: the 528 entries i <= j, mirrored (S is free now: it holds E)
+    double e3[3];
+    int ij[3];
 #pragma unroll
-    for (int t = 0; t < 4; ++t) {
-      const int idx = tid + t * 256, i = idx % W2, j = idx / W2;
-      double acc = (i == j) ? -1.0 : 0.0;
-      for (int k = 0; k < W2; ++k) acc = fma(U[k][i], U[k][j], acc);
-      e4[t] = acc;
+    for (int t = 0; t < 3; ++t) {
+      const int idx = tid + t * 256;
+      e3[t] = 0.0;
+      ij[t] = -1;
+      if (idx < 528) {
+        int i = 0, rem = idx;
+        while (rem >= W2 - i) {
+          rem -= W2 - i;
+          ++i;
+        }
+        const int j = i + rem;
+        double acc = (i == j) ? -1.0 : 0.0;
+        for (int k = 0; k < W2; ++k) acc = fma(U[k][i], U[k][j], acc);
+        e3[t] = acc;
+        ij[t] = i * W2 + j;
+      }
     }
     __syncthreads();
 #pragma unroll
-    for (int t = 0; t < 4; ++t) {
-      const int idx = tid + t * 256, i = idx % W2, j = idx / W2;
-      S[i][j] = e4[t];  // S is free now: it holds E
-    }
+    for (int t = 0; t < 3; ++t)
+      if (ij[t] >= 0) {
+        const int i = ij[t] / W2, j = ij[t] % W2;
+        S[i][j] = e3[t];
+        S[j][i] = e3[t];
+      }
     __syncthreads();
     // |E| is at the rounding level, so U E is formed in FP32 (its relative
     // error 2^-24 of a 1e-15 correction is far below FP64 rounding)
@@ -374,13 +409,18 @@ constexpr int RM_THREADS = 256;
 
 __global__ void __launch_bounds__(RM_THREADS, 2)
     blk_rmul(const double* X, int ldx, int xmode, double* Y, int ldy, int n, int nb, int R,
-             const __nv_bfloat16* __restrict__ Usl, const int* __restrict__ Uexp, unsigned* __restrict__ flags) {
+             const __nv_bfloat16* __restrict__ Usl, const int* __restrict__ Uexp, unsigned* __restrict__ flags,
+             int lower) {
   extern __shared__ __align__(1024) unsigned char dsm_raw[];
   RmulSmem& sm = *reinterpret_cast<RmulSmem*>(dsm_raw + ((1024 - (smem_u32(dsm_raw) & 1023)) & 1023));
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int P = blockIdx.y;
   int I, J;
   block_pair(nb, R, P, I, J);
+  // lower: Y is symmetric; only entries on or below the diagonal are formed,
+  // each also written to its mirror, so a CTA whose rows all lie above both
+  // blocks' columns has nothing to do
+  if (lower && (int)(blockIdx.x * TM) + TM - 1 < I * BS) return;
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&sm.tmem)),
                  "r"(TMEM_COLS)
@@ -515,8 +555,14 @@ __global__ void __launch_bounds__(RM_THREADS, 2)
       const int er = sm.rexp[rl];
       const int g0 = (ch ? J : I) * BS;
 #pragma unroll
-      for (int c = 0; c < BS; ++c)
-        if (g0 + c < n) Y[(size_t)(g0 + c) * ldy + row] = z_to_double(hi[c], lo[c], er + sm.uexp[ch * BS + c] - 64);
+      for (int c = 0; c < BS; ++c) {
+        const int g = g0 + c;
+        if (g < n && (!lower || row >= g)) {
+          const double v = z_to_double(hi[c], lo[c], er + sm.uexp[ch * BS + c] - 64);
+          Y[(size_t)g * ldy + row] = v;
+          if (lower && row > g) Y[(size_t)row * ldy + g] = v;  // 16 consecutive entries of column `row`
+        }
+      }
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -592,9 +638,9 @@ cudaError_t mpj_blocked_update_A(double* A, int lda, double* B, int n, int R, vo
   cudaError_t e = rmul_attr();
   if (e != cudaSuccess) return e;
   const dim3 grid((n + TM - 1) / TM, nb / 2);
-  blk_rmul<<<grid, RM_THREADS, rmul_smem(), s>>>(A, lda, XMODE_COLS, B, n, n, nb, R, u.sl, u.ex, flags);
+  blk_rmul<<<grid, RM_THREADS, rmul_smem(), s>>>(A, lda, XMODE_COLS, B, n, n, nb, R, u.sl, u.ex, flags, 0);
   mpj_count_launch();
-  blk_rmul<<<grid, RM_THREADS, rmul_smem(), s>>>(B, n, XMODE_ROWS, A, lda, n, nb, R, u.sl, u.ex, flags);
+  blk_rmul<<<grid, RM_THREADS, rmul_smem(), s>>>(B, n, XMODE_ROWS, A, lda, n, nb, R, u.sl, u.ex, flags, 1);
   mpj_count_launch();
   return cudaGetLastError();
 }
@@ -607,7 +653,7 @@ cudaError_t mpj_blocked_update_V(double* V, int ldv, int n, int R, void* scratch
   cudaError_t e = rmul_attr();
   if (e != cudaSuccess) return e;
   const dim3 grid((n + TM - 1) / TM, nb / 2);
-  blk_rmul<<<grid, RM_THREADS, rmul_smem(), s>>>(V, ldv, XMODE_COLS, V, ldv, n, nb, R, u.sl, u.ex, flags);
+  blk_rmul<<<grid, RM_THREADS, rmul_smem(), s>>>(V, ldv, XMODE_COLS, V, ldv, n, nb, R, u.sl, u.ex, flags, 0);
   mpj_count_launch();
   return cudaGetLastError();
 }
