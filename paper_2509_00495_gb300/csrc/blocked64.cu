@@ -129,6 +129,17 @@ MPJ_DEV int exp_of_maxbits(unsigned long long b) {
   return (64 - __clzll((long long)b)) - 1074;       // subnormal: mant 2^-1074
 }
 
+// v 2^E as a double, exact for |v| < 2^53 when the result is a normal
+// number (integer instructions only); 0 for v = 0.
+MPJ_DEV double exact_scaled(long long v, int E) {
+  if (v == 0) return 0.0;
+  const unsigned long long sign = v < 0 ? (1ULL << 63) : 0ULL;
+  const unsigned long long a = v < 0 ? (unsigned long long)(-v) : (unsigned long long)v;
+  const int p = 63 - __clzll((long long)a);  // leading bit, < 53
+  const unsigned long long m = (a << (52 - p)) & ((1ULL << 52) - 1ULL);
+  return __longlong_as_double((long long)(sign | ((unsigned long long)(p + E + 1023) << 52) | m));
+}
+
 // Z 2^E rounded to the nearest double (ties to even), Z = hi 2^32 + lo with
 // |Z| < 2^72, using integer instructions only.  Results outside the normal
 // range go through ldexp (never for the operands of the sweeps).
@@ -525,14 +536,13 @@ __global__ void __launch_bounds__(RM_THREADS, 2)
     const int quad = warp & 3, ch = warp >> 2;
     const int rl = quad * 32 + lane;
     const int row = blockIdx.x * TM + rl;
-    // Z = sum_L s_L 2^(8 (6 - L)) = hi 2^32 + lo, hi = s0 2^16 + s1 2^8 + s2, lo = s3 2^24 + s4 2^16 + s5 2^8 + s6
-    long long hi[BS], lo[BS];
+    // Z = sum_L s_L 2^(8 (6 - L)) = hi 2^32 + lo, hi = s0 2^16 + (s1 2^8 + s2),
+    // lo = (s3 2^8 + s4) 2^16 + (s5 2^8 + s6); the bracketed pairs fit 32 bits
+    // (|s_L| < 2^22.2), so levels are read in pairs and combined in int32
+    int t[4][BS];
 #pragma unroll
-    for (int c = 0; c < BS; ++c) {
-      hi[c] = 0;
-      lo[c] = 0;
-    }
-#pragma unroll 1
+    for (int c = 0; c < BS; ++c) t[0][c] = t[1][c] = t[2][c] = t[3][c] = 0;
+#pragma unroll
     for (int l = 0; l < NLEV; ++l) {
       uint32_t v[16];
       asm volatile(
@@ -541,14 +551,12 @@ __global__ void __launch_bounds__(RM_THREADS, 2)
             "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
           : "r"(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(l * W2 + ch * BS)));
       asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-      const int sh = l < 3 ? 8 * (2 - l) : 8 * (6 - l);
+      // level l goes to partial (l + 1) / 2 with weight 2^8 if l is odd (l = 1, 3, 5), 1 otherwise
+      const int slot = (l + 1) >> 1;
 #pragma unroll
       for (int c = 0; c < BS; ++c) {
-        const long long q = (long long)__float2int_rz(__uint_as_float(v[c]));  // exact integer below 2^24
-        if (l < 3)
-          hi[c] += q << sh;
-        else
-          lo[c] += q << sh;
+        const int q = __float2int_rz(__uint_as_float(v[c]));  // exact integer below 2^23
+        t[slot][c] = (l & 1) ? (q << 8) : t[slot][c] + q;
       }
     }
     if (row < n) {
@@ -558,7 +566,14 @@ __global__ void __launch_bounds__(RM_THREADS, 2)
       for (int c = 0; c < BS; ++c) {
         const int g = g0 + c;
         if (g < n && (!lower || row >= g)) {
-          const double v = z_to_double(hi[c], lo[c], er + sm.uexp[ch * BS + c] - 64);
+          // hi 2^32 + lo from the partials, both exact as doubles (|hi| < 2^39, |lo| < 2^47);
+          // one FP64 add rounds the sum once (the same as rounding Z)
+          const int E = er + sm.uexp[ch * BS + c] - 64;
+          const long long hi = ((long long)t[0][c] << 16) + t[1][c];
+          const long long lo = ((long long)t[2][c] << 16) + t[3][c];
+          const int bexp = 32 + E + 1023;
+          const double v = (bexp > 60 && bexp < 2000) ? exact_scaled(hi, 32 + E) + exact_scaled(lo, E)
+                                                      : z_to_double(hi, lo, E);
           Y[(size_t)g * ldy + row] = v;
           if (lower && row > g) Y[(size_t)row * ldy + g] = v;  // 16 consecutive entries of column `row`
         }
