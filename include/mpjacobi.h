@@ -76,14 +76,17 @@ typedef struct {
   int max_sweeps64;  /* FP64 sweep cap; <= 0 selects 30 (the paper's default is 10)           */
   int max_sweeps32;  /* stage-1 sweep cap; <= 0 selects 15                                    */
   int ns_steps;      /* Newton-Schulz steps; <= 0 selects 2 for n < 52000, else 3 (Alg. 8)     */
-  int ordering;      /* FP64 sweep ordering: MPJ_ORDER_ROUND_ROBIN (default) or _CYCLIC      */
+  int ordering;      /* FP64 sweep ordering: MPJ_ORDER_BLOCK (default: block round-robin, blocks of
+                        16, block updates on the tensor cores), MPJ_ORDER_ROUND_ROBIN, or
+                        MPJ_ORDER_CYCLIC (the paper's cyclic-by-row)                          */
   int method;        /* MPJ_METHOD_MIXED (default) or MPJ_METHOD_PLAIN                        */
   int polish;        /* 1: one more FP64 Newton-Schulz step on the final Q (not in the paper) */
   int sort;          /* 1 (default): W ascending, Q's columns permuted to match              */
   int check_symmetry;/* 1: fail with MPJ_ENOTSYM unless A is exactly symmetric               */
   int threshold;     /* FP64 sweeps also skip pairs with |a_pq| <= tol / n (threshold Jacobi, the
-                        paper's future work): 1 on, 0 off, -1 (default) on for the round-robin
-                        ordering and off for cyclic-by-row.  Cannot stop the sweeps early.      */
+                        paper's future work): 1 on, 0 off, -1 (default) on for the block and
+                        round-robin orderings, off for cyclic-by-row.  Cannot stop the sweeps
+                        early.                                                                */
   int precond_passes;/* mixed method: 1 (default) = Algorithm 9; 2 = stages 1-3 applied again to
                         A_cond (FP32 Jacobi on fl32(A_cond), Newton-Schulz, Q_d2^T A_cond Q_d2,
                         Q_d = Q_d1 Q_d2) before the FP64 sweeps -- not in the paper            */

@@ -329,7 +329,7 @@ extern "C" {
 
 void mpj_opts_default(mpj_opts* o) {
   memset(o, 0, sizeof *o);
-  o->ordering = MPJ_ORDER_ROUND_ROBIN;
+  o->ordering = MPJ_ORDER_BLOCK;
   o->method = MPJ_METHOD_MIXED;
   o->sort = 1;
   o->threshold = -1;
@@ -362,7 +362,7 @@ size_t mpj_syev_workspace(int n, const mpj_opts* o) {
   (void)o;
   if (n <= 0) return 0;
   int passes = (o && o->precond_passes >= 2 && o->method == MPJ_METHOD_MIXED) ? 2 : 1;
-  return layout(n, passes, o ? o->ordering : MPJ_ORDER_ROUND_ROBIN).total;
+  return layout(n, passes, o ? o->ordering : MPJ_ORDER_BLOCK).total;
 }
 
 int mpj_syev_ex(int n, const double* A, int lda, double* W, double* Q, int ldq, const mpj_opts* opts_in,

@@ -46,7 +46,7 @@ def test_host_side_helpers_without_gpu(libpath):
     assert mpj.status_str(0) == "MPJ_OK"
     assert mpj.status_str(-3) == "MPJ_ENONFINITE"
     o = mpj.default_opts()
-    assert o.ordering == mpj.ORDER_ROUND_ROBIN and o.method == mpj.METHOD_MIXED and o.sort == 1
+    assert o.ordering == mpj.ORDER_BLOCK and o.method == mpj.METHOD_MIXED and o.sort == 1
     # workspace grows like n^2 and is zero for n = 0
     assert mpj.syev_workspace(0) == 0
     w1, w2 = mpj.syev_workspace(512), mpj.syev_workspace(1024)

@@ -274,7 +274,7 @@ def test_backward_n512_vs_oracle_and_central_differences():
 def test_two_pass_vs_oracle_two_pass(n):
     A, lam = inputs.geo_matrix(n, 1e6, seed=41 * n)
     r = mpj().syev_ex(dev(A), precond_passes=2)
-    Wr, Qr, info = oracle.syev_mixed(A, ordering32=oracle.BLOCK_ROUND_ROBIN, ordering64=oracle.ROUND_ROBIN,
+    Wr, Qr, info = oracle.syev_mixed(A, ordering32=oracle.BLOCK_ROUND_ROBIN, ordering64=oracle.BLOCK_ROUND_ROBIN,
                                      threshold=True, precond_passes=2)
     r1 = mpj().syev_ex(dev(A))
     nA = np.linalg.norm(A, 2)

@@ -152,7 +152,7 @@ def test_stage1_vs_oracle_block_ordering(n):
 @pytest.mark.parametrize("n", [1, 2, 3, 17, 96, 130, 257])
 def test_syev_mixed_vs_oracle(n):
     A, lam = inputs.geo_matrix(n, 1e3, seed=11 * n) if n > 1 else (np.array([[-0.7]]), np.array([-0.7]))
-    r = mpj().syev_ex(dev(A))
+    r = mpj().syev_ex(dev(A), ordering="round_robin")
     W, Q = host(r.W), host(r.Q)
     Wr, Qr, info = oracle.syev_mixed(A, ordering32=oracle.BLOCK_ROUND_ROBIN, ordering64=oracle.ROUND_ROBIN,
                                      threshold=True)
@@ -170,7 +170,7 @@ def test_syev_mixed_vs_oracle(n):
 @pytest.mark.parametrize("n", [33, 96])
 def test_syev_plain_vs_oracle(n):
     A, lam = inputs.geo_matrix(n, 1e3, seed=13 * n)
-    r = mpj().syev_ex(dev(A), method="plain")
+    r = mpj().syev_ex(dev(A), method="plain", ordering="round_robin")
     W, Q = host(r.W), host(r.Q)
     Wr, Qr, info = oracle.syev_plain(A, ordering64=oracle.ROUND_ROBIN, threshold=True)
     nA = np.linalg.norm(A, 2)
@@ -195,7 +195,7 @@ def test_threshold_option_vs_oracle(threshold):
     with the same rule: same sweeps (+-1), same eigenvalues, same accuracy."""
     n = 130
     A, lam = inputs.geo_matrix(n, 1e6, seed=5)
-    r = mpj().syev_ex(dev(A), threshold=threshold)
+    r = mpj().syev_ex(dev(A), threshold=threshold, ordering="round_robin")
     Wr, _, info = oracle.syev_mixed(A, ordering32=oracle.BLOCK_ROUND_ROBIN, ordering64=oracle.ROUND_ROBIN,
                                     threshold=bool(threshold))
     assert abs(r.info["sweeps64"] - info.sweeps64) <= 1
@@ -401,8 +401,8 @@ def test_autograd_matches_central_differences():
 @pytest.mark.parametrize("n", [96, 257])
 def test_two_pass_preconditioning_vs_oracle(n):
     A, lam = inputs.geo_matrix(n, 1e6, seed=17 * n)
-    r1 = mpj().syev_ex(dev(A))
-    r2 = mpj().syev_ex(dev(A), precond_passes=2)
+    r1 = mpj().syev_ex(dev(A), ordering="round_robin")
+    r2 = mpj().syev_ex(dev(A), precond_passes=2, ordering="round_robin")
     W, Q = host(r2.W), host(r2.Q)
     Wr, _, _ = oracle.syev_mixed(A, ordering32=oracle.BLOCK_ROUND_ROBIN, ordering64=oracle.ROUND_ROBIN)
     nA = np.linalg.norm(A, 2)
