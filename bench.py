@@ -40,22 +40,32 @@ FP64_PEAK_TFLOPS = 1.25  # nominal GB300 FP64 (152 SMs x 2 FP64 FMA/clk x 2 flop
 # of the sweep kernels (a "traffic_bytes_per_round:" line), taken on the kernel
 # versions the summary names; see traffic_per_round().
 TRAFFIC_PROFILE = os.path.join(ROOT, "profiles", "rr_step64_geo4096.md")
+BLOCK_TRAFFIC_PROFILE = os.path.join(ROOT, "profiles", "blk_rmul_geo4096.md")
 # Sweep counts of the GPU arm on this input (FP32 stage, FP64 sweeps), used by
 # the reference arm only while no full oracle run is recorded.
 GPU_ARM_SWEEPS = (9, 11)
 WORKLOAD = "geo4096: one symmetric FP64 matrix n=4096, |lam| geometric in [1e-6,1] (condition 1e6), random signs, Haar eigenvectors, seed 0"
 
 
-def traffic_per_round() -> float | None:
-    """dram__bytes_read.sum + dram__bytes_write.sum of one round (rr_step64 plus
-    1/64 of a v_apply_rounds launch) from the ncu summary in profiles/."""
+def traffic_per_round(path: str = TRAFFIC_PROFILE) -> float | None:
+    """dram__bytes_read.sum + dram__bytes_write.sum of one round from an ncu
+    summary in profiles/ (its "traffic_bytes_per_round:" line)."""
     try:
-        for line in open(TRAFFIC_PROFILE):
+        for line in open(path):
             if line.strip().startswith("traffic_bytes_per_round:"):
                 return float(line.split(":", 1)[1].split()[0])
     except OSError:
         return None
     return None
+
+
+def hbm_peak_gbs() -> tuple[float, str]:
+    """Measured HBM copy bandwidth (MEASURED_PEAKS.json), else the fallback."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured (MEASURED_PEAKS.json hbm_gbs)"
+    except (OSError, ValueError, KeyError):
+        return 6800.0, "fallback 6.8 TB/s"
 
 
 def oracle_record(which: str) -> dict | None:
@@ -365,8 +375,9 @@ def main():
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64+f32", "data": "synthetic",
-           "config": {"workload": WORKLOAD, "n": n, "method": "mixed: FP32 block round-robin Jacobi, 2 FP64 "
-                      "Newton-Schulz steps, Q_d^T A Q_d, FP64 round-robin Jacobi sweeps",
+           "config": {"workload": WORKLOAD, "n": n, "method": "mixed (Algorithm 9): FP32 block round-robin "
+                      "Jacobi, 2 Newton-Schulz steps and Q_d^T A Q_d as FP64-accurate tensor-core products, FP64 "
+                      "Jacobi sweeps in block round-robin order with tensor-core block updates",
                       "tol": "n 2^-53 ||A||_F", "l2": "flushed between steps (256 MiB write); working set 0.5 GiB",
                       "parallelism": f"replicas x{world}"},
            "clocks": clocks, "gpu_launches": launches, "e2e": e2e, "accuracy": accuracy,
@@ -374,26 +385,28 @@ def main():
            "stage_ms": dict(zip(["stage1_fp32", "newton_schulz", "transform", "fp64_sweeps", "finalize", "total"],
                                 [round(x, 3) for x in info["ms_stage"]]))}
 
-    # roofline of the dominant kernel: the FP64 round-robin step (one launch per round)
+    # roofline of the dominant kernel, per round of the FP64 sweeps
     sweeps64 = info["sweeps64"]
-    rounds = sweeps64 * (n - 1)
     st = info["ms_stage"]
-    dominant = "rr_step64" if st[3] >= max(st[1], st[2]) else "dgemm_kernel"
-    if rounds > 0:
-        # one round = rr_step64 (A) + its share of v_apply_rounds (V); per round the
-        # scaled rotations need one FMA (2 flops) per entry and side: the lower half
-        # of A twice (rows, columns) and all of V once -> 4 n^2 flops
-        avg_launch_s = st[3] / 1000.0 / rounds
-        flops = 4.0 * n * n
-        achieved = flops / avg_launch_s / 1e12
-        out["roofline"] = {"kernel": "rr_step64+v_apply_rounds (one round)", "bound": "alu", "achieved": achieved,
-                           "peak": FP64_PEAK_TFLOPS,
-                           "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
-                           "traffic": traffic_per_round() if n == 4096 else None,
-                           "peak_source": "nominal FP64 of the recipe table (not in MEASURED_PEAKS.json)",
-                           "algorithmic_flops_per_launch": flops, "avg_launch_ms": avg_launch_s * 1e3,
-                           "dominant_stage": dominant,
-                           "share_of_step": st[3] / st[5] if st[5] else None}
+    if sweeps64 > 0:
+        N32 = (n + 31) // 32 * 32
+        rounds = sweeps64 * (N32 // 16 - 1)
+        round_s = st[3] / 1000.0 / rounds
+        # one outer round of the block ordering: blk_solve (FP64 subproblems), then three
+        # block-diagonal right multiplications on the tensor cores (A U~ into B, B^T U~ into A,
+        # V U~), each reading and writing an n x n FP64 matrix: 48 n^2 algorithmic bytes
+        bytes_round = 48.0 * n * n
+        peak, peak_src = hbm_peak_gbs()
+        achieved = bytes_round / round_s / 1e9
+        out["roofline"] = {"kernel": "blk_rmul x3 + blk_solve (one outer round of the block ordering)",
+                           "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                           "frac": achieved / peak,
+                           "traffic": traffic_per_round(BLOCK_TRAFFIC_PROFILE) if n == 4096 else None,
+                           "peak_source": peak_src, "algorithmic_bytes_per_round": bytes_round,
+                           "avg_round_ms": round_s * 1e3, "rounds": rounds, "dominant_stage": "fp64_sweeps",
+                           "share_of_step": st[3] / st[5] if st[5] else None,
+                           "note": "integer-ALU and latency bound (digit slicing and the exact epilogue); "
+                                   "see profiles/blk_rmul_geo4096.md"}
     # GEMM stage rate (Newton-Schulz + transform: 6n^3 + 3n^3 algorithmic FP64 flops), on the
     # tensor cores from exact bf16 slices unless MPJ_GEMM_TC=0 selects the FP64 DMMA kernel
     if st[1] + st[2] > 0:
@@ -468,6 +481,27 @@ def main():
                                "stage_ms": [round(x, 3) for x in rc.info["ms_stage"]],
                                "backward_err_over_nu": bec, "orth_fro_over_nu": orc,
                                "ordering": "cyclic-by-row (the paper's), run as wavefronts of pairs with equal p+q"}
+        # the same solve with the scalar round-robin FP64 sweeps (rr_step64 + v_apply_rounds)
+        ws_r = torch.empty(mpj.syev_workspace(n, ordering="round_robin"), dtype=torch.uint8, device=dev)
+        flush.zero_()
+        torch.cuda.synchronize()
+        e_a = torch.cuda.Event(enable_timing=True)
+        e_b = torch.cuda.Event(enable_timing=True)
+        e_a.record()
+        rr = mpj.syev_ex(A, workspace=ws_r, ordering="round_robin")
+        e_b.record()
+        e_b.synchronize()
+        del ws_r
+        strr = rr.info["ms_stage"]
+        rounds_rr = rr.info["sweeps64"] * (n - 1)
+        out["mixed_round_robin"] = {
+            "ms_per_solve": e_a.elapsed_time(e_b), "status": rr.status,
+            "sweeps": {"stage1_fp32": rr.info["sweeps32"], "fp64": rr.info["sweeps64"]},
+            "stage_ms": [round(x, 3) for x in strr],
+            "fp64_round": {"kernel": "rr_step64+v_apply_rounds", "bound": "alu",
+                           "achieved_tflops": 4.0 * n * n / (strr[3] / 1000.0 / rounds_rr) / 1e12 if rounds_rr else None,
+                           "peak_tflops": FP64_PEAK_TFLOPS,
+                           "traffic_per_round": traffic_per_round() if n == 4096 else None}}
         out["extras"] = extras(mpj, torch, dev, inputs)
 
     if rank == 0 and world == 1 and not args.no_cpu:
