@@ -205,12 +205,23 @@ int mpj_newton_schulz(int n, double* X_dev, int ldx, int steps, void* stream);
 int mpj_precondition(int n, const double* A_dev, int lda, const double* Qd_dev, int ldq, double* Ac_dev, int ldc,
                      void* stream);
 
-/* FP64 Jacobi sweeps in place on the symmetric A (full storage, both triangles
- * kept equal) accumulating V <- V J (V holds the start matrix, e.g. I), with
- * ordering MPJ_ORDER_ROUND_ROBIN or MPJ_ORDER_CYCLIC, per-pair skip rule
- * |a_pq| > 2^-53 sqrt(|a_pp a_qq|), stop at off(A) <= tol (tol <= 0: n 2^-53 ||A||_F)
- * or max_sweeps (<= 0: 30).  sweeps / off_final (host, may be NULL).
- * Returns MPJ_NOT_CONVERGED at the cap. */
+/* FP64 Jacobi sweeps (Alg. 4) in place on the symmetric A (full storage, both
+ * triangles kept equal) accumulating V <- V J (V holds the start matrix, e.g.
+ * I), with ordering
+ *   MPJ_ORDER_BLOCK        block round-robin (blocks of 16; one inner
+ *                          round-robin sweep per 32 x 32 block-pair subproblem
+ *                          in FP64; the rest of A and V updated by the
+ *                          accumulated block rotations as FP64-accurate
+ *                          tensor-core products; the paper's block Jacobi,
+ *                          Ch. 6 further work),
+ *   MPJ_ORDER_ROUND_ROBIN  scalar round-robin (circle method), or
+ *   MPJ_ORDER_CYCLIC       the paper's cyclic-by-row ordering, run as
+ *                          wavefronts of the pairs with equal p + q (the same
+ *                          rotation sequence),
+ * per-pair skip rule |a_pq| > 2^-53 sqrt(|a_pp a_qq|), stop at off(A) <= tol
+ * (tol <= 0: n 2^-53 ||A||_F) or max_sweeps (<= 0: 30).  sweeps / off_final
+ * (host, may be NULL).  Returns MPJ_NOT_CONVERGED at the cap, MPJ_ETIMEOUT if
+ * a tensor-core completion wait ran out. */
 int mpj_jacobi64(int n, double* A_dev, int lda, double* V_dev, int ldv, double tol, int ordering, int max_sweeps,
                  int* sweeps, double* off_final, void* stream);
 
@@ -231,7 +242,11 @@ int mpj_jacobi64(int n, double* A_dev, int lda, double* V_dev, int ldv, double t
  * that first call before any stream capture.  All calls share the one array:
  * calls whose work overlaps on the GPU (other streams, other host threads)
  * race on it and must be serialized by the caller.  Every scratch word is
- * written before it is read, so nothing carries over between calls. */
+ * written before it is read, so nothing carries over between calls.  The
+ * looked-up address is kept for the life of the process: do not use this
+ * entry point across a cudaDeviceReset (or anything else that recreates the
+ * device's primary context).  Only the round-robin and cyclic orderings are
+ * offered here (the block ordering needs an n x n buffer). */
 #define MPJ_NOALLOC_MAX_N 8192
 #define MPJ_NOALLOC_SCRATCH_BYTES 1048576
 int mpj_jacobi64_noalloc(int n, double* A_dev, int lda, double* V_dev, int ldv, double tol, int ordering,
