@@ -64,7 +64,8 @@ typedef enum {
   MPJ_EDEGENERATE = -6,   /* backward: w_i == w_j for i != j with a nonzero coupling */
   MPJ_EWORKSPACE = -7,    /* caller workspace too small (see mpj_syev_workspace) */
   MPJ_ETIMEOUT = -8,      /* a device-side barrier gave up after its iteration limit */
-  MPJ_ETOOLARGE = -9      /* n exceeds the fixed scratch of an allocation-free entry point */
+  MPJ_ETOOLARGE = -9,     /* n exceeds the fixed scratch of an allocation-free entry point */
+  MPJ_EPREMISE = -10      /* ||Q_l^T Q_l - I||_2 >= 2: Q_l outside the Newton-Schulz convergence premise */
 } mpj_status;
 
 enum { MPJ_ORDER_CYCLIC = 0, MPJ_ORDER_ROUND_ROBIN = 1, MPJ_ORDER_BLOCK = 2 };
@@ -90,6 +91,10 @@ typedef struct {
   int precond_passes;/* mixed method: 1 (default) = Algorithm 9; 2 = stages 1-3 applied again to
                         A_cond (FP32 Jacobi on fl32(A_cond), Newton-Schulz, Q_d2^T A_cond Q_d2,
                         Q_d = Q_d1 Q_d2) before the FP64 sweeps -- not in the paper            */
+  int stage1_half;   /* 1: stage 1 in half precision (binary16 values, skip test and tol32 at
+                        2^-11; the paper's further work, Ch. 6); Newton-Schulz then takes the
+                        smallest k with (sqrt(1 + n 2^-11) - 1)^(2^k) <= n 2^-53 steps (the
+                        paper's bound of Sec. 4.3.4 with the half unit roundoff)              */
 } mpj_opts;
 
 typedef struct {
@@ -104,6 +109,10 @@ typedef struct {
   double off_cond;   /* off(A_cond) before the FP64 sweeps                                    */
   double off_final;  /* off(A) after the last FP64 sweep                                      */
   float ms_stage[6]; /* device time per stage: stage1, NS, transform, sweeps, final, total   */
+  double ns_e0;      /* ||Q_l^T Q_l - I||_2 before Newton-Schulz, a 30-step power-iteration
+                        estimate (the iteration converges for ||Q_l^T Q_l - I||_2 < 2,
+                        Sec. 4.3.4; the solve returns MPJ_EPREMISE when the estimate is 2 or
+                        more)                                                                */
 } mpj_info;
 
 /* Fills `o` with the defaults described in mpj_opts. */

@@ -70,13 +70,14 @@ class _Opts(ctypes.Structure):
     _fields_ = [("tol", _d), ("tol32", _d), ("skip_tol", _d), ("skip_tol32", _d),
                 ("max_sweeps64", _i), ("max_sweeps32", _i), ("ns_steps", _i),
                 ("ordering32", _i), ("ordering64", _i), ("polish", _i), ("sort", _i), ("threshold", _i),
-                ("precond_passes", _i)]
+                ("precond_passes", _i), ("stage1_half", _i)]
 
 
 class _Info(ctypes.Structure):
     _fields_ = [("sweeps32", _i), ("sweeps64", _i), ("capped32", _i), ("capped64", _i),
                 ("rotations32", ctypes.c_longlong), ("rotations64", ctypes.c_longlong),
-                ("normA_fro", _d), ("off32", _d), ("off_cond", _d), ("off_final", _d), ("sweeps32_pass2", _i)]
+                ("normA_fro", _d), ("off32", _d), ("off_cond", _d), ("off_final", _d), ("sweeps32_pass2", _i),
+                ("ns_steps", _i), ("ns_e0", _d)]
 
 
 def _declare(L):
@@ -109,6 +110,12 @@ def _declare(L):
     L.orc_eigh_backward.argtypes = [_i, _dp, _dp, _i, _dp, _dp, _i, _dp, _i]
     L.orc_eigh_backward.restype = _i
     L.orc_sample_rotations.argtypes = [_i, ctypes.c_void_p, _i, ctypes.c_void_p, _i, ctypes.c_longlong, _i]
+    L.orc_round_half.argtypes = [ctypes.c_float]
+    L.orc_round_half.restype = ctypes.c_float
+    L.orc_ns_steps.argtypes = [_i, _i]
+    L.orc_ns_steps.restype = _i
+    L.orc_jacobi_h.argtypes = [_i, _fp, _i, _fp, _i, _i, _d, ctypes.c_float, _i, _ip, _llp, _dp]
+    L.orc_jacobi_h.restype = _i
 
 
 def _f64(a) -> np.ndarray:
@@ -135,18 +142,25 @@ class Info:
     off_cond: float
     off_final: float
     sweeps32_pass2: int = 0
+    ns_steps: int = 0
+    ns_e0: float = 0.0
 
 
 def _info(ci: _Info) -> Info:
     return Info(ci.sweeps32, ci.sweeps64, bool(ci.capped32), bool(ci.capped64), ci.rotations32,
-                ci.rotations64, ci.normA_fro, ci.off32, ci.off_cond, ci.off_final, ci.sweeps32_pass2)
+                ci.rotations64, ci.normA_fro, ci.off32, ci.off_cond, ci.off_final, ci.sweeps32_pass2,
+                ci.ns_steps, ci.ns_e0)
+
+
+class PremiseError(ArithmeticError):
+    """Q_l violates the Newton-Schulz premise ||Q_l^T Q_l - I||_2 < 2."""
 
 
 def _opts(n, tol=0.0, tol32=0.0, skip_tol=0.0, skip_tol32=0.0, max_sweeps64=0, max_sweeps32=0, ns_steps=0,
           ordering32=CYCLIC, ordering64=CYCLIC, polish=False, sort=True, threshold=False,
-          precond_passes=1) -> _Opts:
+          precond_passes=1, stage1_half=False) -> _Opts:
     return _Opts(tol, tol32, skip_tol, skip_tol32, max_sweeps64, max_sweeps32, ns_steps, ordering32, ordering64,
-                 int(polish), int(sort), int(threshold), int(precond_passes))
+                 int(polish), int(sort), int(threshold), int(precond_passes), int(stage1_half))
 
 
 # ---------------------------------------------------------------- primitives
@@ -216,6 +230,16 @@ def block_schedule(n: int):
     return out
 
 
+def round_half(x: float) -> float:
+    """The oracle's rounding of an FP32 value to IEEE binary16 (as a float)."""
+    return float(_load().orc_round_half(x))
+
+
+def ns_steps(n: int, half: bool = False) -> int:
+    """Newton-Schulz steps the oracle takes for size n (single or half stage 1)."""
+    return int(_load().orc_ns_steps(n, int(half)))
+
+
 def jacobi(A, V=None, *, ordering=CYCLIC, tol=0.0, skip_tol=U_D, max_sweeps=30, paper_mode=False,
            dtype=np.float64, skip_abs=0.0):
     """Cyclic Jacobi sweeps (Algorithm 4) on a copy of A; returns (A_final, V, sweeps, rotations, off, capped).
@@ -224,6 +248,12 @@ def jacobi(A, V=None, *, ordering=CYCLIC, tol=0.0, skip_tol=U_D, max_sweeps=30, 
     L = _load()
     n = np.asarray(A).shape[0]
     sw, rot, of = ctypes.c_int(), ctypes.c_longlong(), _d()
+    if dtype == np.float16:
+        a = np.array(np.asarray(A, dtype=np.float16), dtype=np.float32, order="F")
+        v = np.array(np.eye(n) if V is None else V, dtype=np.float32, order="F")
+        capped = L.orc_jacobi_h(n, _ptr(a, _fp), n, _ptr(v, _fp), n, ordering, tol, skip_tol, max_sweeps,
+                                ctypes.byref(sw), ctypes.byref(rot), ctypes.byref(of))
+        return a, v, sw.value, rot.value, of.value, bool(capped)
     if dtype == np.float32:
         a = np.array(A, dtype=np.float32, order="F")
         v = np.array(np.eye(n) if V is None else V, dtype=np.float32, order="F")
@@ -294,6 +324,10 @@ def stage1(A, **kw):
 def syev_mixed(A, *, return_intermediates=False, **kw):
     """Algorithm 9 with an FP32 Jacobi stage 1.  Returns (W, Q, Info[, dict of Q_l, Q_d, A_cond]).
 
+    stage1_half=True runs stage 1 in half precision (binary16) with the
+    Newton-Schulz step count of orc_ns_steps; raises PremiseError when
+    ||Q_l^T Q_l - I||_2 >= 2 (the iteration's convergence premise).
+
     precond_passes=2 applies stages 1-3 a second time to A_cond before the
     FP64 sweeps (not in the paper; see orc_syev_mixed)."""
     a = _f64(A)
@@ -302,9 +336,12 @@ def syev_mixed(A, *, return_intermediates=False, **kw):
     Q = np.zeros((n, n), order="F")
     ci = _Info()
     inter = {k: np.zeros((n, n), order="F") for k in ("Ql", "Qd", "Acond")} if return_intermediates else None
-    _load().orc_syev_mixed(n, _ptr(a), n, _ptr(W), _ptr(Q), n, ctypes.byref(_opts(n, **kw)), ctypes.byref(ci),
-                           _ptr(inter["Ql"]) if inter else _ptr(None), _ptr(inter["Qd"]) if inter else _ptr(None),
-                           _ptr(inter["Acond"]) if inter else _ptr(None))
+    rc = _load().orc_syev_mixed(n, _ptr(a), n, _ptr(W), _ptr(Q), n, ctypes.byref(_opts(n, **kw)), ctypes.byref(ci),
+                                _ptr(inter["Ql"]) if inter else _ptr(None),
+                                _ptr(inter["Qd"]) if inter else _ptr(None),
+                                _ptr(inter["Acond"]) if inter else _ptr(None))
+    if rc == 2:
+        raise PremiseError(f"||Q_l^T Q_l - I||_2 = {ci.ns_e0:.3g} >= 2")
     if return_intermediates:
         return W, Q, _info(ci), inter
     return W, Q, _info(ci)

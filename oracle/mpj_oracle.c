@@ -28,6 +28,14 @@
 
 #define AT(M, ld, i, j) ((M)[(size_t)(i) + (size_t)(j) * (size_t)(ld)])
 
+/* Rounding of an FP32 value to the nearest IEEE binary16 value (ties to
+ * even), for the half-precision stage 1 (Ch. 6, further work item 3: "these
+ * theories can apply to half precision as well").  Reading: a half-precision
+ * Jacobi keeps A, V and the rotation parameters in binary16 and rounds every
+ * update, computed in FP32 from binary16 operands, once to binary16.        */
+float orc_round_half(float x) { return (float)(_Float16)x; }
+static float rq(float x, int half) { return half ? orc_round_half(x) : x; }
+
 /* ------------------------------------------------------------------------ */
 /* Algorithm 2 (jacobi_pair, Sec. 3.1.1-3.1.2) in the stable form the paper
  * prefers (Sec. 3.1.2 and Appendix A, approach 2): tau = (a_qq - a_pp) / (2 a_pq),
@@ -118,21 +126,21 @@ static void rotate_d(int n, double* A, int lda, double* V, int ldv, int p, int q
   }
 }
 
-static void rotate_f(int n, float* A, int lda, float* V, int ldv, int p, int q, float c, float s) {
+static void rotate_f(int n, float* A, int lda, float* V, int ldv, int p, int q, float c, float s, int half) {
   for (int k = 0; k < n; ++k) {
     float ap = AT(A, lda, p, k), aq = AT(A, lda, q, k);
-    AT(A, lda, p, k) = c * ap - s * aq;
-    AT(A, lda, q, k) = s * ap + c * aq;
+    AT(A, lda, p, k) = rq(c * ap - s * aq, half);
+    AT(A, lda, q, k) = rq(s * ap + c * aq, half);
   }
   for (int k = 0; k < n; ++k) {
     float ap = AT(A, lda, k, p), aq = AT(A, lda, k, q);
-    AT(A, lda, k, p) = c * ap - s * aq;
-    AT(A, lda, k, q) = s * ap + c * aq;
+    AT(A, lda, k, p) = rq(c * ap - s * aq, half);
+    AT(A, lda, k, q) = rq(s * ap + c * aq, half);
   }
   for (int k = 0; k < n; ++k) {
     float vp = AT(V, ldv, k, p), vq = AT(V, ldv, k, q);
-    AT(V, ldv, k, p) = c * vp - s * vq;
-    AT(V, ldv, k, q) = s * vp + c * vq;
+    AT(V, ldv, k, p) = rq(c * vp - s * vq, half);
+    AT(V, ldv, k, q) = rq(s * vp + c * vq, half);
   }
 }
 
@@ -197,10 +205,10 @@ static void symmetrize_d(int n, double* A, int lda) {
       AT(A, lda, j, i) = v;
     }
 }
-static void symmetrize_f(int n, float* A, int lda) {
+static void symmetrize_f(int n, float* A, int lda, int half) {
   for (int j = 0; j < n; ++j)
     for (int i = j + 1; i < n; ++i) {
-      float v = (AT(A, lda, i, j) + AT(A, lda, j, i)) / 2.0f;
+      float v = rq((AT(A, lda, i, j) + AT(A, lda, j, i)) / 2.0f, half);
       AT(A, lda, i, j) = v;
       AT(A, lda, j, i) = v;
     }
@@ -223,7 +231,7 @@ void orc_sample_rotations(int n, void* A, int lda, void* V, int ldv, long long n
         float* a = (float*)A;
         float c, s;
         orc_jacobi_pair_f(AT(a, lda, p, p), AT(a, lda, q, q), AT(a, lda, p, q), &c, &s);
-        rotate_f(n, a, lda, (float*)V, ldv, p, q, c, s);
+        rotate_f(n, a, lda, (float*)V, ldv, p, q, c, s, 0);
       }
     }
 }
@@ -321,8 +329,24 @@ int orc_jacobi_d(int n, double* A, int lda, double* V, int ldv, int ordering, do
 /* The same loop in FP32 (stage 1 of the mixed algorithm, where the paper
  * calls eig(single(A)) and this library runs an FP32 Jacobi instead).
  * off(A) and tol are evaluated in double from the float entries.          */
+static int jacobi_low(int n, float* A, int lda, float* V, int ldv, int ordering, double tol, float skip_tol,
+                      int max_sweeps, int* sweeps_out, long long* rotations_out, double* off_out, int half);
+
 int orc_jacobi_f(int n, float* A, int lda, float* V, int ldv, int ordering, double tol, float skip_tol,
                  int max_sweeps, int* sweeps_out, long long* rotations_out, double* off_out) {
+  return jacobi_low(n, A, lda, V, ldv, ordering, tol, skip_tol, max_sweeps, sweeps_out, rotations_out, off_out, 0);
+}
+
+/* The same loop in half precision: A and V hold binary16 values, the
+ * rotation parameters are rounded to binary16, and every update is rounded
+ * once to binary16 (see orc_round_half). */
+int orc_jacobi_h(int n, float* A, int lda, float* V, int ldv, int ordering, double tol, float skip_tol,
+                 int max_sweeps, int* sweeps_out, long long* rotations_out, double* off_out) {
+  return jacobi_low(n, A, lda, V, ldv, ordering, tol, skip_tol, max_sweeps, sweeps_out, rotations_out, off_out, 1);
+}
+
+static int jacobi_low(int n, float* A, int lda, float* V, int ldv, int ordering, double tol, float skip_tol,
+                      int max_sweeps, int* sweeps_out, long long* rotations_out, double* off_out, int half) {
   int sweeps = 0;
   long long rot = 0;
   int capped = 0;
@@ -342,7 +366,9 @@ int orc_jacobi_f(int n, float* A, int lda, float* V, int ldv, int ordering, doub
           if (fabsf(apq) > skip_tol * sqrtf(fabsf(AT(A, lda, p, p) * AT(A, lda, q, q)))) {
             float c, s;
             orc_jacobi_pair_f(AT(A, lda, p, p), AT(A, lda, q, q), apq, &c, &s);
-            rotate_f(n, A, lda, V, ldv, p, q, c, s);
+            c = rq(c, half);
+            s = rq(s, half);
+            rotate_f(n, A, lda, V, ldv, p, q, c, s, half);
             done_rot = 1;
             ++rot;
           }
@@ -359,7 +385,9 @@ int orc_jacobi_f(int n, float* A, int lda, float* V, int ldv, int ordering, doub
               if (fabsf(apq) > skip_tol * sqrtf(fabsf(AT(A, lda, p, p) * AT(A, lda, q, q)))) {
                 float c, s;
                 orc_jacobi_pair_f(AT(A, lda, p, p), AT(A, lda, q, q), apq, &c, &s);
-                rotate_f(n, A, lda, V, ldv, p, q, c, s);
+            c = rq(c, half);
+            s = rq(s, half);
+                rotate_f(n, A, lda, V, ldv, p, q, c, s, half);
                 done_rot = 1;
                 ++rot;
               }
@@ -373,7 +401,9 @@ int orc_jacobi_f(int n, float* A, int lda, float* V, int ldv, int ordering, doub
           if (fabsf(apq) > skip_tol * sqrtf(fabsf(AT(A, lda, p, p) * AT(A, lda, q, q)))) {
             float c, s;
             orc_jacobi_pair_f(AT(A, lda, p, p), AT(A, lda, q, q), apq, &c, &s);
-            rotate_f(n, A, lda, V, ldv, p, q, c, s);
+            c = rq(c, half);
+            s = rq(s, half);
+            rotate_f(n, A, lda, V, ldv, p, q, c, s, half);
             done_rot = 1;
             ++rot;
           }
@@ -384,7 +414,7 @@ int orc_jacobi_f(int n, float* A, int lda, float* V, int ldv, int ordering, doub
       off = orc_off_f(n, A, lda);
       break;
     }
-    symmetrize_f(n, A, lda);
+    symmetrize_f(n, A, lda, half);
     off = orc_off_f(n, A, lda);
   }
   *sweeps_out = sweeps;
@@ -471,6 +501,7 @@ typedef struct {
   int threshold;    /* 1: FP64 sweeps also skip pairs with |a_pq| <= tol / n     */
   int precond_passes; /* 2: Algorithm 9's stages 1-3 applied a second time to
                          A_cond before the FP64 sweeps (not in the paper)        */
+  int stage1_half;    /* 1: stage 1 in half precision (binary16, u = 2^-11)      */
 } orc_opts;
 
 typedef struct {
@@ -478,7 +509,27 @@ typedef struct {
   long long rotations32, rotations64;
   double normA_fro, off32, off_cond, off_final;
   int sweeps32_pass2;
+  int ns_steps;     /* Newton-Schulz steps applied                                   */
+  double ns_e0;     /* ||Q_l^T Q_l - I||_2 before Newton-Schulz (power estimate)     */
 } orc_info;
+
+/* Newton-Schulz steps for a low-precision Q_l with unit roundoff ul: the paper
+ * bounds ||X_k - U|| by (sqrt(1 + n ul) - 1)^(2^k) (Sec. 4.3.4, the analysis
+ * behind Algorithm 8) and stops once that is at most n u_d.  For single
+ * precision the paper's code uses 2 steps below n = 52000 and 3 above; for
+ * half precision (ul = 2^-11) the same bound is evaluated here.            */
+int orc_ns_steps(int n, int half) {
+  if (!half) return n < 52000 ? 2 : 3;
+  const double ud = ldexp(1.0, -53), ul = ldexp(1.0, -11);
+  const double e0 = sqrt(1.0 + (double)n * ul) - 1.0;
+  double e = e0;
+  int k = 0;
+  while (e > (double)n * ud && k < 8) {
+    e = e * e;
+    ++k;
+  }
+  return k < 1 ? 1 : k;
+}
 
 static void sort_eig(int n, double* W, double* Q, int ldq) {
   /* insertion sort on (value, index): ascending, ties by original index */
@@ -510,13 +561,14 @@ static void sort_eig(int n, double* W, double* Q, int ldq) {
 
 static void defaults(int n, double normA, const orc_opts* o, orc_opts* r) {
   *r = *o;
+  const int lowbits = r->stage1_half ? 11 : 24;  /* unit roundoff 2^-11 or 2^-24 */
   if (r->tol <= 0) r->tol = (double)n * ldexp(1.0, -53) * normA;
-  if (r->tol32 <= 0) r->tol32 = (double)n * ldexp(1.0, -24) * normA;
+  if (r->tol32 <= 0) r->tol32 = (double)n * ldexp(1.0, -lowbits) * normA;
   if (r->skip_tol <= 0) r->skip_tol = ldexp(1.0, -53);
-  if (r->skip_tol32 <= 0) r->skip_tol32 = ldexp(1.0, -24);
+  if (r->skip_tol32 <= 0) r->skip_tol32 = ldexp(1.0, -lowbits);
   if (r->max_sweeps64 <= 0) r->max_sweeps64 = 30;
   if (r->max_sweeps32 <= 0) r->max_sweeps32 = 15;
-  if (r->ns_steps <= 0) r->ns_steps = (n < 52000) ? 2 : 3;
+  if (r->ns_steps <= 0) r->ns_steps = orc_ns_steps(n, r->stage1_half);
 }
 
 /* Stage 1 alone: A32 = fl32(A), FP32 Jacobi from V32 = I, Q_l = double(V32).
@@ -530,11 +582,14 @@ int orc_stage1(int n, const double* A, int lda, double* Ql, int ldq, const orc_o
   float* V32 = (float*)malloc(sizeof(float) * (size_t)n * n);
   for (int j = 0; j < n; ++j)
     for (int i = 0; i < n; ++i) {
-      AT(A32, n, i, j) = (float)AT(A, lda, i, j);
+      AT(A32, n, i, j) = rq((float)AT(A, lda, i, j), d.stage1_half);
       AT(V32, n, i, j) = (i == j) ? 1.0f : 0.0f;
     }
-  int capped = orc_jacobi_f(n, A32, n, V32, n, d.ordering32, d.tol32, (float)d.skip_tol32, d.max_sweeps32,
-                            &info->sweeps32, &info->rotations32, &info->off32);
+  int capped = d.stage1_half
+                   ? orc_jacobi_h(n, A32, n, V32, n, d.ordering32, d.tol32, (float)d.skip_tol32, d.max_sweeps32,
+                                  &info->sweeps32, &info->rotations32, &info->off32)
+                   : orc_jacobi_f(n, A32, n, V32, n, d.ordering32, d.tol32, (float)d.skip_tol32, d.max_sweeps32,
+                                  &info->sweeps32, &info->rotations32, &info->off32);
   info->capped32 = capped;
   info->normA_fro = normA;
   for (int j = 0; j < n; ++j)
@@ -550,7 +605,8 @@ int orc_stage1(int n, const double* A, int lda, double* Ql, int ldq, const orc_o
  *   3. A_cond = Q_d^T A Q_d;  4. FP64 Jacobi on A_cond from V = I;
  *   5. W = diag(A_cond after the sweeps), Q = Q_d V  (optionally polished, sorted).
  * Intermediates (each n x n, may be NULL): Ql_out, Qd_out, Acond_out (with
- * two passes: Q_d = Q_d1 Q_d2 and the second A_cond).
+ * two passes: Q_d = Q_d1 Q_d2 and the second A_cond).  Returns 2 (and no
+ * results) when Q_l violates the Newton-Schulz premise.
  * Returns 0, or 1 when the FP64 stage hit its sweep cap.                     */
 int orc_syev_mixed(int n, const double* A, int lda, double* W, double* Q, int ldq, const orc_opts* o, orc_info* info,
                    double* Ql_out, double* Qd_out, double* Acond_out) {
@@ -563,6 +619,47 @@ int orc_syev_mixed(int n, const double* A, int lda, double* W, double* Q, int ld
   double* V = (double*)malloc(sizeof(double) * (size_t)n * n);
   orc_stage1(n, A, lda, X, n, &d, info, NULL);
   if (Ql_out) memcpy(Ql_out, X, sizeof(double) * (size_t)n * n);
+  /* The Newton-Schulz iteration converges when the singular values of Q_l lie
+   * in (0, sqrt(3)) (Sec. 4.3.4), i.e. ||Q_l^T Q_l - I||_2 < 2.  The 2-norm of
+   * the symmetric E = Q_l^T Q_l - I is its largest |eigenvalue|, estimated by
+   * 200 steps of the power iteration. */
+  {
+    double* E = (double*)malloc(sizeof(double) * (size_t)n * n);
+    double* x = (double*)malloc(sizeof(double) * (size_t)n);
+    double* y = (double*)malloc(sizeof(double) * (size_t)n);
+    for (int j = 0; j < n; ++j)
+      for (int i = 0; i < n; ++i) {
+        double g = (i == j) ? -1.0 : 0.0;
+        for (int k = 0; k < n; ++k) g += AT(X, n, k, i) * AT(X, n, k, j);
+        AT(E, n, i, j) = g;
+      }
+    for (int i = 0; i < n; ++i) x[i] = 1.0 + 0.5 * sin((double)i);
+    double lam = 0.0;
+    for (int it = 0; it < 200; ++it) {
+      double nx = 0.0, ny = 0.0;
+      for (int i = 0; i < n; ++i) nx += x[i] * x[i];
+      nx = sqrt(nx);
+      for (int i = 0; i < n; ++i) {
+        double t = 0.0;
+        for (int j = 0; j < n; ++j) t += AT(E, n, i, j) * x[j];
+        y[i] = t / nx;
+        ny += y[i] * y[i];
+      }
+      lam = sqrt(ny);
+      for (int i = 0; i < n; ++i) x[i] = y[i];
+    }
+    info->ns_e0 = lam;
+    free(E);
+    free(x);
+    free(y);
+  }
+  info->ns_steps = d.ns_steps;
+  if (!(info->ns_e0 < 2.0)) {
+    free(X);
+    free(Ac);
+    free(V);
+    return 2;
+  }
   orc_newton_schulz_d(n, X, n, d.ns_steps);
   orc_precondition_d(n, A, lda, X, n, Ac, n);
   if (d.precond_passes >= 2) {
@@ -577,6 +674,8 @@ int orc_syev_mixed(int n, const double* A, int lda, double* W, double* Q, int ld
     memset(&i2, 0, sizeof i2);
     d2.tol32 = (double)n * ldexp(1.0, -24) * orc_off_d(n, Ac, n);
     d2.max_sweeps32 = d.max_sweeps32 < 8 ? d.max_sweeps32 : 8;
+    d2.stage1_half = 0; /* the second pass runs in single precision */
+    d2.skip_tol32 = ldexp(1.0, -24);
     double* X2 = (double*)malloc(sizeof(double) * (size_t)n * n);
     double* T = (double*)malloc(sizeof(double) * (size_t)n * n);
     orc_stage1(n, Ac, n, X2, n, &d2, &i2, NULL);

@@ -18,6 +18,7 @@
 // blocked update (FP32 FMA), which touch A32 and V32 once per round instead of
 // once per pair step.  off(A32) is reduced after each sweep; stop at
 // off(A32) <= tol32 or the sweep cap.
+#include <cuda_fp16.h>
 #include <stdlib.h>
 
 #include "common.cuh"
@@ -40,13 +41,17 @@ MPJ_DEV void block_pair(int nb, int R, int slot, int& I, int& J) {
   J = x < y ? y : x;
 }
 
+// hq: the half-precision stage (binary16 values; Ch. 6 further work item 3):
+// every stored value and rotation parameter is rounded to binary16.
+MPJ_DEV float qh(float v, bool hq) { return hq ? __half2float(__float2half_rn(v)) : v; }
+
 __global__ void init32(const double* __restrict__ A, int lda, int n, int N, float* __restrict__ A32,
-                       float* __restrict__ V32) {
+                       float* __restrict__ V32, bool hq) {
   size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   size_t total = (size_t)N * N;
   for (; idx < total; idx += (size_t)gridDim.x * blockDim.x) {
     int i = (int)(idx % N), j = (int)(idx / N);
-    A32[idx] = (i < n && j < n) ? (float)A[(size_t)j * lda + i] : 0.0f;
+    A32[idx] = (i < n && j < n) ? qh((float)A[(size_t)j * lda + i], hq) : 0.0f;
     V32[idx] = (i == j) ? 1.0f : 0.0f;
   }
 }
@@ -63,7 +68,7 @@ __global__ void widen(const float* __restrict__ V32, int N, int n, double* __res
 // One CTA per block pair of outer round R: inner round-robin sweep on the
 // 32 x 32 subproblem; writes the rotated subproblem S and the accumulated U.
 __global__ void __launch_bounds__(256) solve32(const float* __restrict__ A32, int N, int nb, int R,
-                                               float* __restrict__ Sbuf, float* __restrict__ Ubuf) {
+                                               float* __restrict__ Sbuf, float* __restrict__ Ubuf, bool hq) {
   __shared__ float S[W2][LD];
   __shared__ float U[W2][LD];
   __shared__ RotRec<float> rec[W2 / 2];
@@ -79,13 +84,19 @@ __global__ void __launch_bounds__(256) solve32(const float* __restrict__ A32, in
     U[li][lj] = (li == lj) ? 1.0f : 0.0f;
   }
   __syncthreads();
-  const float skip = 0x1p-24f;
+  const float skip = hq ? 0x1p-11f : 0x1p-24f;
   for (int rho = 0; rho < W2 - 1; ++rho) {
     if (tid < W2 / 2) {
       int x, y;
       rr_slot(W2, rho, tid, x, y);
       RotRec<float> rr;
       rr_make_rec<float>(W2, W2, rho, x, y, S[x][x], S[y][y], S[y][x], skip, rr);
+      if (hq && rec_rotated(rr.cm1, rr.sig)) {  // c and s as binary16, new diagonal rounded
+        rr.cm1 = qh(1.0f + rr.cm1, true) - 1.0f;
+        rr.sig = qh(rr.sig, true);
+        rr.dx = qh(rr.dx, true);
+        rr.dy = qh(rr.dy, true);
+      }
       rec[tid] = rr;
     }
     __syncthreads();
@@ -114,6 +125,10 @@ __global__ void __launch_bounds__(256) solve32(const float* __restrict__ A32, in
             rot_apply(rb.cm1, rb.sig, vxx, vxy);
             rot_apply(rb.cm1, rb.sig, vyx, vyy);
           }
+          vxx = qh(vxx, hq);
+          vxy = qh(vxy, hq);
+          vyx = qh(vyx, hq);
+          vyy = qh(vyy, hq);
           S[xa][xb] = vxx;
           S[xb][xa] = vxx;
           S[xa][yb] = vxy;
@@ -133,8 +148,8 @@ __global__ void __launch_bounds__(256) solve32(const float* __restrict__ A32, in
         rr_slot(W2, rho, sb, xb, yb);
         float ux = U[row][xb], uy = U[row][yb];
         rot_apply(rb.cm1, rb.sig, ux, uy);
-        U[row][xb] = ux;
-        U[row][yb] = uy;
+        U[row][xb] = qh(ux, hq);
+        U[row][yb] = qh(uy, hq);
       }
     }
     __syncthreads();
@@ -188,7 +203,7 @@ MPJ_DEV void tile_mm(const float (*Lt)[LD4], const float (*R)[LD4], float acc[4]
 // all tile loads unrolled (48 in flight per thread): 127 registers, 8 CTAs/SM
 __global__ void __launch_bounds__(UT, 8) update32(float* __restrict__ A32, float* __restrict__ V32, int N, int nb, int R,
                                                const float* __restrict__ Sbuf, const float* __restrict__ Ubuf,
-                                               int n_atiles) {
+                                               int n_atiles, bool hq) {
   // three 32 x 32 buffers (13.5 KB): the tile (later X^T), U_P, U_Q
   __shared__ __align__(16) float T[W2][LD4];
   __shared__ __align__(16) float UP[W2][LD4];  // U_P[l][i]
@@ -239,7 +254,7 @@ __global__ void __launch_bounds__(UT, 8) update32(float* __restrict__ A32, float
 #pragma unroll
     for (int a = 0; a < 4; ++a)
 #pragma unroll
-      for (int b = 0; b < 4; ++b) T[i4 + a][j4 + b] = acc[a][b];
+      for (int b = 0; b < 4; ++b) T[i4 + a][j4 + b] = qh(acc[a][b], hq);
     __syncthreads();
     #pragma unroll
     for (int it = 0; it < W2 * W2 / UT; ++it) {
@@ -270,7 +285,7 @@ __global__ void __launch_bounds__(UT, 8) update32(float* __restrict__ A32, float
 #pragma unroll
   for (int a = 0; a < 4; ++a)
 #pragma unroll
-    for (int b = 0; b < 4; ++b) T[i4 + a][j4 + b] = acc[a][b];
+    for (int b = 0; b < 4; ++b) T[i4 + a][j4 + b] = qh(acc[a][b], hq);
   __syncthreads();
   #pragma unroll
   for (int it = 0; it < W2 * W2 / UT; ++it) {
@@ -312,18 +327,18 @@ static int stage1_tensor_cores() {
 cudaError_t mpj_sumsq32(const float* A, int lda, int n, double* partial, double* out, cudaStream_t s);
 
 int mpj_stage1_run(int n, const double* A, int lda, double* Ql, int ldq, double tol32, int max_sweeps, int* sweeps_out,
-                   double* off_out, void* work, double* partial, double* dscal, cudaStream_t s) {
+                   double* off_out, void* work, double* partial, double* dscal, cudaStream_t s, bool half) {
   const int N = mpj_stage1_padded(n);
   const int nb = N / BS;
   float* A32 = (float*)work;
   float* V32 = A32 + (size_t)N * N;
   float* Sbuf = V32 + (size_t)N * N;
   float* Ubuf = Sbuf + (size_t)(nb / 2) * W2 * W2;
-  const int tc = stage1_tensor_cores();
   float* Bt = Ubuf + (size_t)(nb / 2) * W2 * W2;
-  unsigned* tflag = (unsigned*)(Bt + (tc ? (size_t)N * N : 0));
+  unsigned* tflag = (unsigned*)(Bt + (stage1_tensor_cores() ? (size_t)N * N : 0));
   MPJ_CUDA_TRY(cudaMemsetAsync(tflag, 0, sizeof(unsigned), s));
-  init32<<<1024, 256, 0, s>>>(A, lda, n, N, A32, V32);
+  const int tc = stage1_tensor_cores() && !half;
+  init32<<<1024, 256, 0, s>>>(A, lda, n, N, A32, V32, half);
   mpj_count_launch();
   MPJ_CUDA_TRY(cudaGetLastError());
   double off2 = 0.0;
@@ -341,17 +356,17 @@ int mpj_stage1_run(int n, const double* A, int lda, double* Ql, int ldq, double 
       break;
     }
     for (int R = 0; R < nb - 1; ++R) {
-      solve32<<<npairs, 256, 0, s>>>(A32, N, nb, R, Sbuf, Ubuf);
+      solve32<<<npairs, 256, 0, s>>>(A32, N, nb, R, Sbuf, Ubuf, half);
       mpj_count_launch();
       if (tc == 1) {
         // A' = U^T A U = (A U)^T U (A symmetric): B^T = (A U)^T, then
         // A' = (B^T)(:, I_q) U_q on the tensor cores; V U on the FP32 pipe
         MPJ_CUDA_TRY(mpj_tc_panel(N, nb, R, Ubuf, A32, Bt, 1, nullptr, nullptr, tflag, s));
         MPJ_CUDA_TRY(mpj_tc_panel(N, nb, R, Ubuf, Bt, A32, 0, nullptr, nullptr, tflag, s));
-        update32<<<(N / W2) * npairs, UT, 0, s>>>(A32, V32, N, nb, R, Sbuf, Ubuf, 0);
+        update32<<<(N / W2) * npairs, UT, 0, s>>>(A32, V32, N, nb, R, Sbuf, Ubuf, 0, false);
         mpj_count_launch();
       } else {
-        update32<<<grid_u, UT, 0, s>>>(A32, V32, N, nb, R, Sbuf, Ubuf, n_atiles);
+        update32<<<grid_u, UT, 0, s>>>(A32, V32, N, nb, R, Sbuf, Ubuf, n_atiles, half);
         mpj_count_launch();
       }
     }

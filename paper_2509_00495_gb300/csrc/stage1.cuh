@@ -9,5 +9,8 @@ size_t mpj_stage1_bytes(int n);   // workspace bytes for mpj_stage1_run
 // Q_l = double(V32) from an FP32 Jacobi on fl32(A).  `work` holds
 // mpj_stage1_bytes(n); `partial` (256 doubles) and `dscal` (1 double) are
 // device scratch for the off(A32) reduction.  Synchronizes `s` once per sweep.
+// half: the half-precision stage (values and rotation parameters rounded to
+// binary16, skip test at 2^-11).
 int mpj_stage1_run(int n, const double* A, int lda, double* Ql, int ldq, double tol32, int max_sweeps,
-                   int* sweeps_out, double* off_out, void* work, double* partial, double* dscal, cudaStream_t s);
+                   int* sweeps_out, double* off_out, void* work, double* partial, double* dscal, cudaStream_t s,
+                   bool half = false);

@@ -75,8 +75,9 @@ Layout layout(int n, int passes, int ordering) {
   L.scratch = off;
   off += al(mpj_jacobi64_scratch_bytes_ordering(n, ordering));
   L.small = off;
-  // flags + scalar (256 B), partials (2048 B), ranks (4n B, then rounded up to 256), w (8n B)
-  off += al(2560 + 256 + (size_t)n * (sizeof(int) + sizeof(double)));
+  // flags + scalar (256 B), partials (2048 B), ranks (4n B, then rounded up to 256), w (8n B),
+  // two n-vectors of the premise check
+  off += al(2560 + 256 + (size_t)n * (sizeof(int) + sizeof(double))) + al((size_t)2 * n * sizeof(double));
   L.total = off;
   return L;
 }
@@ -89,6 +90,7 @@ struct Small {
   double* partial;
   int* rank;
   double* w;
+  double* vec;
 };
 
 Small small_ptrs(char* base, int n) {
@@ -98,6 +100,7 @@ Small small_ptrs(char* base, int n) {
   s.partial = (double*)(base + 256);
   s.rank = (int*)(base + 256 + 256 * sizeof(double));
   s.w = (double*)(base + al(256 + 256 * sizeof(double) + (size_t)n * sizeof(int)));
+  s.vec = (double*)(base + al(2560 + 256 + (size_t)n * (sizeof(int) + sizeof(double))));
   return s;
 }
 
@@ -220,6 +223,22 @@ struct Timer {
   }
 };
 
+// Newton-Schulz steps for a Q_l with unit roundoff ul: the paper bounds
+// ||X_k - U|| by (sqrt(1 + n ul) - 1)^(2^k) (Sec. 4.3.4) and its code takes 2
+// steps below n = 52000 for single precision, 3 above; the half-precision
+// stage takes the smallest k whose bound is at most n 2^-53.
+int ns_steps_for(int n, bool half) {
+  if (!half) return n < 52000 ? 2 : 3;
+  const double e0 = std::sqrt(1.0 + (double)n * 0x1p-11) - 1.0, target = (double)n * 0x1p-53;
+  double e = e0;
+  int k = 0;
+  while (e > target && k < 8) {
+    e *= e;
+    ++k;
+  }
+  return k < 1 ? 1 : k;
+}
+
 int fill_opts(int n, const mpj_opts* in, mpj_opts* o) {
   if (in)
     *o = *in;
@@ -227,10 +246,65 @@ int fill_opts(int n, const mpj_opts* in, mpj_opts* o) {
     mpj_opts_default(o);
   if (o->max_sweeps64 <= 0) o->max_sweeps64 = 30;
   if (o->max_sweeps32 <= 0) o->max_sweeps32 = 15;
-  if (o->ns_steps <= 0) o->ns_steps = (n < 52000) ? 2 : 3;
+  if (o->ns_steps <= 0) o->ns_steps = ns_steps_for(n, o->stage1_half != 0);
   if (o->ordering != MPJ_ORDER_CYCLIC && o->ordering != MPJ_ORDER_ROUND_ROBIN && o->ordering != MPJ_ORDER_BLOCK)
     return MPJ_EINVAL;
   if (o->method != MPJ_METHOD_MIXED && o->method != MPJ_METHOD_PLAIN) return MPJ_EINVAL;
+  return MPJ_OK;
+}
+
+// y = E x / ||x|| for the symmetric n x n E (column i of E dotted with x, one
+// warp per column); partial[0..n) is y, the norm of x comes from *nrm.
+__global__ void pow_step(const double* __restrict__ E, int n, const double* __restrict__ x,
+                         const double* __restrict__ nrm, double* __restrict__ y) {
+  const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (i >= n) return;
+  double t = 0.0;
+  for (int j = lane; j < n; j += 32) t = fma(E[(size_t)i * n + j], x[j], t);
+  for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+  if (lane == 0) y[i] = t / *nrm;
+}
+
+// *nrm = ||y|| (one CTA, fixed order)
+__global__ void pow_norm(const double* __restrict__ y, int n, double* __restrict__ nrm) {
+  __shared__ double sh[256];
+  double s = 0.0;
+  for (int i = threadIdx.x; i < n; i += 256) s = fma(y[i], y[i], s);
+  sh[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *nrm = sqrt(sh[0]);
+}
+
+__global__ void pow_init(double* __restrict__ x, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) x[i] = 1.0 + 0.5 * sin((double)i);
+}
+
+// Estimate of ||E||_2 for symmetric E by 30 steps of the power iteration on
+// two n-vectors in `vec` (2n doubles) and one scalar.
+int premise_norm(int n, const double* E, double* vec, double* scal, double* out, cudaStream_t s) {
+  double* x = vec;
+  double* y = vec + n;
+  pow_init<<<(n + 255) / 256, 256, 0, s>>>(x, n);
+  mpj_count_launch();
+  pow_norm<<<1, 256, 0, s>>>(x, n, scal);
+  mpj_count_launch();
+  for (int it = 0; it < 30; ++it) {
+    pow_step<<<(n + 7) / 8, 256, 0, s>>>(E, n, x, scal, y);
+    mpj_count_launch();
+    pow_norm<<<1, 256, 0, s>>>(y, n, scal);
+    mpj_count_launch();
+    double* t = x;
+    x = y;
+    y = t;
+  }
+  MPJ_CUDA_TRY(cudaGetLastError());
+  MPJ_CUDA_TRY(cudaMemcpyAsync(out, scal, sizeof(double), cudaMemcpyDeviceToHost, s));
+  MPJ_CUDA_TRY(cudaStreamSynchronize(s));
   return MPJ_OK;
 }
 
@@ -269,9 +343,11 @@ int product_run(bool ta, bool tb, int n, double alpha, const double* A, int lda,
 // tiles mirrored), E in FP64, then X E either in FP32 when
 // max|E| <= 2^-31 / sqrt(n) (ns_fast.cu) or as an FP64-accurate product.
 // X, M, Y are n x n with ld n; `fp32work` holds mpj_ns_fast_bytes(n).  The
-// result ends in *X.
+// result ends in *X.  With e0_out set, the first step also estimates
+// ||E||_2 (premise_norm on `vec`, 2n doubles, and `dscal`) and stops with
+// MPJ_EPREMISE when it is 2 or more.
 int ns_steps_run(int n, double** X, double* M, double** Y, int steps, void* fp32work, const OzWork& w,
-                 cudaStream_t s) {
+                 cudaStream_t s, double* e0_out = nullptr, double* vec = nullptr, double* dscal = nullptr) {
   const bool tc = gemm_tensor_cores();
   for (int k = 0; k < steps; ++k) {
     if (tc) {
@@ -284,6 +360,15 @@ int ns_steps_run(int n, double** X, double* M, double** Y, int steps, void* fp32
     }
     int r = mpj_ns_fp32_correction(n, *X, M, *Y, fp32work, nullptr, s);
     if (r < 0) return r;
+    if (k == 0 && e0_out) {
+      // M now holds E = I - X^T X: the premise ||E||_2 < 2 (Sec. 4.3.4), its
+      // largest |eigenvalue|, estimated by 30 power-iteration steps
+      double lam = 0.0;
+      int rp = premise_norm(n, M, vec, dscal, &lam, s);
+      if (rp != MPJ_OK) return rp;
+      *e0_out = lam;
+      if (!(lam < 2.0)) return MPJ_EPREMISE;
+    }
     if (r == 1 && tc) {  // Y = X + X E / 2
       MPJ_CUDA_TRY(cudaMemcpyAsync(*Y, *X, (size_t)n * n * sizeof(double), cudaMemcpyDeviceToDevice, s));
       int rt = product_run(false, false, n, 0.5, *X, n, M, n, 1.0, *Y, *Y, w, s);
@@ -348,6 +433,7 @@ const char* mpj_status_str(int st) {
     case MPJ_EWORKSPACE: return "MPJ_EWORKSPACE";
     case MPJ_ETIMEOUT: return "MPJ_ETIMEOUT";
     case MPJ_ETOOLARGE: return "MPJ_ETOOLARGE";
+    case MPJ_EPREMISE: return "MPJ_EPREMISE";
     default: return "MPJ_UNKNOWN";
   }
 }
@@ -403,7 +489,7 @@ int mpj_syev_ex(int n, const double* A, int lda, double* W, double* Q, int ldq, 
   unsigned flags = 0;
   double tol = 0.0;
   int sweeps32 = 0, sweeps32b = 0, sweeps64 = 0;
-  double off32 = 0.0, offc = 0.0, offf = 0.0;
+  double off32 = 0.0, offc = 0.0, offf = 0.0, ns_e0 = 0.0;
   double* Ac = nullptr;
   double* V = nullptr;
   double* Qd = nullptr;
@@ -438,14 +524,15 @@ int mpj_syev_ex(int n, const double* A, int lda, double* W, double* Q, int ldq, 
   {
     double normA = std::sqrt(norm2);
     tol = o.tol > 0 ? o.tol : (double)n * 0x1p-53 * normA;
-    double tol32 = o.tol32 > 0 ? o.tol32 : (double)n * 0x1p-24 * normA;
+    double tol32 = o.tol32 > 0 ? o.tol32 : (double)n * (o.stage1_half ? 0x1p-11 : 0x1p-24) * normA;
     if (info) {
       info->norm_fro = normA;
       info->tol = tol;
     }
     if (o.method == MPJ_METHOD_MIXED) {
       // stage 1 -> X = Q_l
-      int r1 = mpj_stage1_run(n, A, lda, X, n, tol32, o.max_sweeps32, &sweeps32, &off32, S1, sm.partial, sm.dscal, s);
+      int r1 = mpj_stage1_run(n, A, lda, X, n, tol32, o.max_sweeps32, &sweeps32, &off32, S1, sm.partial, sm.dscal, s,
+                              o.stage1_half != 0);
       if (r1 < 0) {
         st = r1;
         goto done;
@@ -454,7 +541,8 @@ int mpj_syev_ex(int n, const double* A, int lda, double* W, double* Q, int ldq, 
       // stage 2: Newton-Schulz -> X = Q_d
       double* Xp = X;
       double* Yp = Y;
-      if ((st = ns_steps_run(n, &Xp, M, &Yp, o.ns_steps, S1, ozw, s)) != MPJ_OK) goto done;
+      if ((st = ns_steps_run(n, &Xp, M, &Yp, o.ns_steps, S1, ozw, s, &ns_e0, sm.vec, sm.dscal)) != MPJ_OK)
+        goto done;
       tm.mark(2);
       // stage 3: A_cond = Q_d^T (A Q_d) -> M (symmetric), Yp = A Q_d
       if ((st = transform_run(n, A, lda, Xp, n, Yp, M, n, ozw, s)) != MPJ_OK) goto done;
@@ -582,6 +670,7 @@ done:
     info->off32 = off32;
     info->off_final = offf;
     info->off_cond = offc;
+    info->ns_e0 = ns_e0;
   }
   return st;
 }

@@ -31,6 +31,8 @@ MPJ_ENOMEM = -5
 MPJ_EDEGENERATE = -6
 MPJ_EWORKSPACE = -7
 MPJ_ETIMEOUT = -8
+MPJ_ETOOLARGE = -9
+MPJ_EPREMISE = -10
 
 ORDER_CYCLIC = 0
 ORDER_ROUND_ROBIN = 1
@@ -48,13 +50,14 @@ _dp = ctypes.POINTER(ctypes.c_double)
 class Opts(ctypes.Structure):
     _fields_ = [("tol", _d), ("tol32", _d), ("max_sweeps64", _i), ("max_sweeps32", _i), ("ns_steps", _i),
                 ("ordering", _i), ("method", _i), ("polish", _i), ("sort", _i), ("check_symmetry", _i),
-                ("threshold", _i), ("precond_passes", _i)]
+                ("threshold", _i), ("precond_passes", _i), ("stage1_half", _i)]
 
 
 class Info(ctypes.Structure):
     _fields_ = [("status", _i), ("sweeps32", _i), ("sweeps32_pass2", _i), ("sweeps64", _i), ("ns_steps", _i),
                 ("norm_fro", _d),
-                ("tol", _d), ("off32", _d), ("off_cond", _d), ("off_final", _d), ("ms_stage", ctypes.c_float * 6)]
+                ("tol", _d), ("off32", _d), ("off_cond", _d), ("off_final", _d), ("ms_stage", ctypes.c_float * 6),
+                ("ns_e0", _d)]
 
     def as_dict(self) -> dict:
         d = {k: getattr(self, k) for k, _ in self._fields_ if k != "ms_stage"}

@@ -351,3 +351,34 @@ def test_block_plain_solve_vs_oracle():
     assert np.abs(host(r.W) - Wr).max() <= 1e-12 * np.linalg.norm(A, 2)
     be, orF = triple(A, host(r.W), host(r.Q))
     assert be <= 4 and orF <= 4
+
+
+# ---------------------------------------------------------------- half-precision stage 1 (Sec. 4.3.4)
+@pytest.mark.parametrize("n", [96, 257])
+def test_half_stage1_solve_vs_oracle(n):
+    """stage1_half: binary16 storage in stage 1, the half-precision
+    Newton-Schulz step count, premise estimate ns_e0 of the same size as the
+    oracle's (the two stage-1 runs round in different orders), and the same
+    FP64-accurate solve."""
+    A, lam = inputs.geo_matrix(n, 1e3, seed=1)
+    r = mpj().syev_ex(dev(A), stage1_half=1)
+    Wr, _, info = oracle.syev_mixed(A, ordering64=oracle.BLOCK_ROUND_ROBIN, threshold=True, stage1_half=True)
+    nA = np.linalg.norm(A, 2)
+    W, Q = host(r.W), host(r.Q)
+    assert r.status == 0
+    assert r.info["ns_steps"] == info.ns_steps == oracle.ns_steps(n, half=True)
+    assert info.ns_e0 / 3 <= r.info["ns_e0"] <= 3 * info.ns_e0
+    assert abs(r.info["sweeps64"] - info.sweeps64) <= 2
+    assert np.abs(W - Wr).max() <= 1e-12 * nA
+    assert np.abs(W - np.sort(lam)).max() <= 1e-12 * nA
+    assert np.linalg.norm(Q.T @ Q - np.eye(n), 2) <= 8 * n * U
+    assert np.linalg.norm(A - (Q * W) @ Q.T) / np.linalg.norm(A) <= 8 * n * U
+
+
+def test_premise_estimate_single_stage_gpu():
+    """With the FP32 stage 1, ns_e0 is of the size n u_l."""
+    n = 1024
+    A, _ = inputs.geo_matrix(n, 1e3, seed=5)
+    r = mpj().syev_ex(dev(A))
+    assert r.status == 0
+    assert 1e-3 * n * 2.0 ** -24 <= r.info["ns_e0"] <= 4 * n * 2.0 ** -24

@@ -40,6 +40,10 @@ MUTATIONS = {
     "float_pair_tau": ("float tau = (aqq - app) / (2.0f * apq);", "float tau = (aqq - app) / (apq);"),
     "two_pass_product_order": ("orc_gemm_nn_d(n, n, n, X, n, X2, n, T, n);", "orc_gemm_nn_d(n, n, n, X2, n, X, n, T, n);"),
     "two_pass_transform_on_A": ("orc_precondition_d(n, Ac, n, X2, n, T, n);", "orc_precondition_d(n, A, lda, X2, n, T, n);"),
+    "half_not_rounded": ("static float rq(float x, int half) { return half ? orc_round_half(x) : x; }",
+                         "static float rq(float x, int half) { return x; }"),
+    "half_ns_steps_single": ("if (!half) return n < 52000 ? 2 : 3;", "return n < 52000 ? 2 : 3;"),
+    "premise_one_power_step": ("for (int it = 0; it < 200; ++it) {", "for (int it = 0; it < 1; ++it) {"),
 }
 
 

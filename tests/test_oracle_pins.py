@@ -523,3 +523,86 @@ def test_two_pass_intermediates_compose():
 
 def nA_(A):
     return np.linalg.norm(A, 2)
+
+
+# ---------------------------------------------------------------- half-precision stage 1 (Sec. 4.3.4)
+def test_round_half_is_ieee_binary16_round_to_nearest_even():
+    """orc_round_half against numpy's IEEE binary16 conversion (round to
+    nearest, ties to even) on random values of every magnitude and on the
+    edges: largest finite value, overflow, subnormals, ties."""
+    rng = np.random.default_rng(5)
+    xs = (rng.standard_normal(4000) * np.exp2(rng.uniform(-30, 17, 4000))).astype(np.float32)
+    edge = np.array([0.0, -0.0, 1.0, 65504.0, 65519.0, 65520.0, -65520.0, 2.0 ** -24, 2.0 ** -25,
+                     3 * 2.0 ** -25, 2.0 ** -14, 1 + 2.0 ** -11, 1 + 3 * 2.0 ** -11, 1e-8], dtype=np.float32)
+    for x in np.concatenate([xs, edge]):
+        with np.errstate(over="ignore"):
+            want = float(np.float16(x))
+        got = oracle.round_half(float(x))
+        assert got == want or (np.isinf(want) and np.isinf(got) and np.sign(got) == np.sign(want)), x
+    assert oracle.round_half(2.0 ** -25) == 0.0                 # tie between 0 and the smallest subnormal
+    assert oracle.round_half(3 * 2.0 ** -25) == 2.0 ** -23      # tie resolved to the even subnormal
+    assert np.isinf(oracle.round_half(65520.0))
+
+
+def test_ns_steps_single_and_half():
+    """Single precision: 2 steps below n = 52000, 3 from there on (the step
+    counts the paper's code uses).  Half precision: more steps than single
+    at every n and non-decreasing in n."""
+    assert oracle.ns_steps(51999) == 2 and oracle.ns_steps(52000) == 3
+    prev = 0
+    for n in (1, 2, 71, 72, 200, 665, 666, 2000, 4096, 10000, 60000):
+        k = oracle.ns_steps(n, half=True)
+        assert k > oracle.ns_steps(n) and k >= prev
+        prev = k
+
+
+def test_half_stage1_stores_binary16_and_diagonalises():
+    """The binary16 Jacobi keeps every entry of A and V representable in
+    binary16, and its diagonal approximates the spectrum to the accuracy of
+    the half-precision input (n u_h ||A||)."""
+    n = 40
+    A, lam = inputs.geo_matrix(n, 1e2, seed=8)
+    a, v, sw, rot, of, cap = oracle.jacobi(A, ordering=oracle.ROUND_ROBIN, dtype=np.float16,
+                                           tol=n * 2.0 ** -11 * np.linalg.norm(A))
+    assert not cap and sw >= 2
+    assert np.array_equal(np.float16(a).astype(np.float32), a)
+    assert np.array_equal(np.float16(v).astype(np.float32), v)
+    nA = np.linalg.norm(A, 2)
+    assert np.abs(np.sort(np.diag(a)) - np.sort(lam)).max() <= 4 * n * 2.0 ** -11 * nA
+    assert np.linalg.norm(v.T.astype(np.float64) @ v - np.eye(n), 2) <= 4 * n * 2.0 ** -11
+
+
+@pytest.mark.parametrize("n", [96, 200])
+def test_half_stage1_mixed_solve_is_fp64_accurate(n):
+    """Algorithm 9 with a binary16 stage 1: Q_l is only half-precision
+    orthogonal, the Newton-Schulz step count for half precision brings Q_d to
+    FP64 orthogonality and the result is an FP64-accurate eigendecomposition;
+    ns_e0 is ||Q_l^T Q_l - I||_2 (against LAPACK's 2-norm; the power
+    iteration approaches it from below)."""
+    A, lam = inputs.geo_matrix(n, 1e3, seed=1)
+    W, Q, info, it = oracle.syev_mixed(A, ordering64=oracle.BLOCK_ROUND_ROBIN, threshold=True, stage1_half=True,
+                                       return_intermediates=True)
+    Ql = it["Ql"]
+    e = np.linalg.norm(Ql.T @ Ql - np.eye(n), 2)
+    assert (1 - 1e-3) * e <= info.ns_e0 <= (1 + 1e-12) * e
+    assert 0.02 * n * 2.0 ** -11 <= e <= 4 * n * 2.0 ** -11
+    assert info.ns_steps == oracle.ns_steps(n, half=True) >= 4
+    nA = np.linalg.norm(A, 2)
+    assert np.abs(W - np.sort(lam)).max() <= 1e-12 * nA
+    # the FP64 sweeps start from an A_cond whose off-diagonal part is of size
+    # u_h ||A|| instead of u_l ||A||: more sweeps, and the final errors are a
+    # few times those of the FP32 stage 1, still O(n u_d)
+    assert np.linalg.norm(Q.T @ Q - np.eye(n), 2) <= 8 * n * U_D
+    assert np.linalg.norm(A - (Q * W) @ Q.T) / np.linalg.norm(A) <= 8 * n * U_D
+    _, _, info32 = oracle.syev_mixed(A, ordering64=oracle.BLOCK_ROUND_ROBIN, threshold=True)
+    assert info.sweeps64 > info32.sweeps64
+
+
+def test_premise_estimate_single_stage_matches_2norm():
+    """ns_e0 for the FP32 stage 1 is the 2-norm of Q_l^T Q_l - I too."""
+    n = 64
+    A, _ = inputs.geo_matrix(n, 1e3, seed=2)
+    W, Q, info, it = oracle.syev_mixed(A, return_intermediates=True)
+    Ql = it["Ql"]
+    e = np.linalg.norm(Ql.T @ Ql - np.eye(n), 2)
+    assert (1 - 1e-3) * e <= info.ns_e0 <= (1 + 1e-12) * e and e < 1e-4
