@@ -639,6 +639,10 @@ int orc_syev_mixed(int n, const double* A, int lda, double* W, double* Q, int ld
       double nx = 0.0, ny = 0.0;
       for (int i = 0; i < n; ++i) nx += x[i] * x[i];
       nx = sqrt(nx);
+      if (nx == 0.0) { /* E x = 0 exactly: the estimate is 0 */
+        lam = 0.0;
+        break;
+      }
       for (int i = 0; i < n; ++i) {
         double t = 0.0;
         for (int j = 0; j < n; ++j) t += AT(E, n, i, j) * x[j];

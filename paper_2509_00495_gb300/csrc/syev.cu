@@ -262,7 +262,8 @@ __global__ void pow_step(const double* __restrict__ E, int n, const double* __re
   double t = 0.0;
   for (int j = lane; j < n; j += 32) t = fma(E[(size_t)i * n + j], x[j], t);
   for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-  if (lane == 0) y[i] = t / *nrm;
+  const double nx = *nrm;
+  if (lane == 0) y[i] = nx > 0.0 ? t / nx : 0.0;  // E x = 0 exactly: the estimate stays 0
 }
 
 // *nrm = ||y|| (one CTA, fixed order)

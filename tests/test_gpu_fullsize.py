@@ -382,3 +382,14 @@ def test_premise_estimate_single_stage_gpu():
     r = mpj().syev_ex(dev(A))
     assert r.status == 0
     assert 1e-3 * n * 2.0 ** -24 <= r.info["ns_e0"] <= 4 * n * 2.0 ** -24
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 17])
+def test_half_stage1_small_sizes(n):
+    A, lam = inputs.geo_matrix(n, 1e3, seed=11 * n) if n > 1 else (np.array([[-0.7]]), np.array([-0.7]))
+    r = mpj().syev_ex(dev(A), stage1_half=1)
+    Wr, _, info = oracle.syev_mixed(A, ordering64=oracle.BLOCK_ROUND_ROBIN, threshold=True, stage1_half=True)
+    assert r.status == 0
+    assert np.abs(host(r.W) - Wr).max() <= 1e-12 * np.linalg.norm(A, 2)
+    if n == 1:
+        assert r.info["ns_e0"] == 0.0 and info.ns_e0 == 0.0

@@ -606,3 +606,13 @@ def test_premise_estimate_single_stage_matches_2norm():
     Ql = it["Ql"]
     e = np.linalg.norm(Ql.T @ Ql - np.eye(n), 2)
     assert (1 - 1e-3) * e <= info.ns_e0 <= (1 + 1e-12) * e and e < 1e-4
+
+
+@pytest.mark.parametrize("half", [False, True])
+def test_premise_estimate_zero_when_ql_orthogonal(half):
+    """n = 1 and a diagonal A give Q_l = I exactly: the estimate is 0 and the
+    solve proceeds."""
+    for A in (np.array([[-0.7]]), np.diag([3.0, -1.0, 0.5])):
+        W, Q, info = oracle.syev_mixed(A, stage1_half=half)
+        assert info.ns_e0 == 0.0
+        assert np.array_equal(W, np.sort(np.diag(A)))
