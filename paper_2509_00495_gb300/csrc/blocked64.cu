@@ -409,29 +409,99 @@ struct __align__(1024) RmulSmem {
 
 enum { XMODE_COLS = 0, XMODE_ROWS = 1 };
 
-// Y[r, g_P(c)] = sum_k X_P(r, k) U_P(k, c) for the CTA's 128 rows r and block
-// pair P = blockIdx.y; X_P(r, k) = X[r + g_P(k) ldx] (XMODE_COLS) or
-// X[g_P(k) + r ldx] (XMODE_ROWS).  Y may alias X in XMODE_COLS (each CTA reads
-// and writes only its own rows of its own panel).  256 threads: thread t
-// digitizes row t/2 over block half t%2 (the 16 indices of block I or J);
-// warp w reads the TMEM lanes of rows 32 (w mod 4) .. +31 and the 16 output
-// columns 16 (w / 4) .. +15 of each level.
+// Y[r, g_Q(c)] = sum_k X_Q(r, k) U_Q(k, c) for block pair Q = blockIdx.y and
+// the CTA's 128 rows r: the 32 indices of each of the block pairs
+// a = 4 blockIdx.x .. +3 (rows 32 j .. +31 of the tile are pair 4 blockIdx.x + j,
+// so epilogue warp w handles exactly pair 4 blockIdx.x + (w mod 4)).
+// X_Q(r, k) = X[r + g_Q(k) ldx] (XMODE_COLS) or X[g_Q(k) + r ldx] (XMODE_ROWS).
+// Y may alias X in XMODE_COLS (each CTA reads and writes only its own rows of
+// its own panel).  Which tiles (a, Q) are formed:
+//   TRI_ALL   every tile (V <- V U~);
+//   TRI_FIRST tiles a <= Q (B = A U~: only the tiles the second step reads);
+//   TRI_SECOND tiles a >= Q of C = B^T U~, written to Y and to the mirror
+//             tile (Q, a); in the diagonal tile a = Q the entries on and below
+//             the diagonal, mirrored.  So Y = U~^T A U~ stays exactly
+//             symmetric, and the second step reads B only in tiles (Q, a),
+//             Q <= a, the ones TRI_FIRST formed.
+// 256 threads: thread t digitizes tile row t/2 over block half t%2 (the 16
+// indices of block I or J of Q); warp w reads the TMEM lanes of rows
+// 32 (w mod 4) .. +31 and the 16 output columns 16 (w / 4) .. +15 of each level.
 constexpr int RM_THREADS = 256;
+enum { TRI_ALL = 0, TRI_FIRST = 1, TRI_SECOND = 2 };
+
+// The 16 values X_Q(row, k), k = g0 .. g0 + 15 (block I or J of Q); zeros for
+// row < 0 (no such block pair or a tile that is not formed), row >= n, or
+// indices >= n.
+MPJ_DEV void load_xrow(const double* X, int ldx, int xmode, int n, int row, int g0, double x[BS]) {
+  if (row < 0) {
+#pragma unroll
+    for (int k = 0; k < BS; ++k) x[k] = 0.0;
+  } else if (xmode == XMODE_COLS) {
+#pragma unroll
+    for (int k = 0; k < BS; ++k) x[k] = (row < n && g0 + k < n) ? X[(size_t)(g0 + k) * ldx + row] : 0.0;
+  } else if (row < n && g0 + BS <= n && ((((size_t)row * ldx + g0) & 1) == 0)) {
+    const double2* src = reinterpret_cast<const double2*>(X + (size_t)row * ldx + g0);
+#pragma unroll
+    for (int k = 0; k < BS / 2; ++k) {
+      const double2 v = src[k];
+      x[2 * k] = v.x;
+      x[2 * k + 1] = v.y;
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < BS; ++k) x[k] = (row < n && g0 + k < n) ? X[(size_t)row * ldx + g0 + k] : 0.0;
+  }
+}
+
+// the global index of tile row rl (pair 4 gx + rl / 32, index rl mod 32), or
+// -1 when that pair does not exist
+MPJ_DEV int tile_row(int nb, int R, int gx, int rl) {
+  const int a = 4 * gx + (rl >> 5);
+  if (a >= nb / 2) return -1;
+  int I, J;
+  block_pair(nb, R, a, I, J);
+  return gidx(I, J, rl & 31);
+}
+
+MPJ_DEV bool tile_needed(int tri, int a, int Q) {
+  return tri == TRI_ALL || (tri == TRI_FIRST ? a <= Q : a >= Q);
+}
 
 __global__ void __launch_bounds__(RM_THREADS, 2)
     blk_rmul(const double* X, int ldx, int xmode, double* Y, int ldy, int n, int nb, int R,
-             const __nv_bfloat16* __restrict__ Usl, const int* __restrict__ Uexp, unsigned* __restrict__ flags,
-             int lower) {
+             const __nv_bfloat16* __restrict__ Usl, const int* __restrict__ Uexp, const int* __restrict__ rotated,
+             unsigned* __restrict__ flags, int tri) {
   extern __shared__ __align__(1024) unsigned char dsm_raw[];
   RmulSmem& sm = *reinterpret_cast<RmulSmem*>(dsm_raw + ((1024 - (smem_u32(dsm_raw) & 1023)) & 1023));
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int P = blockIdx.y;
+  const int Q = blockIdx.y, gx = blockIdx.x;
+  const int a0 = 4 * gx, a1 = min(4 * gx + 3, nb / 2 - 1);
+  if (tri == TRI_FIRST && a0 > Q) return;
+  if (tri == TRI_SECOND && a1 < Q) return;
   int I, J;
-  block_pair(nb, R, P, I, J);
-  // lower: Y is symmetric; only entries on or below the diagonal are formed,
-  // each also written to its mirror, so a CTA whose rows all lie above both
-  // blocks' columns has nothing to do
-  if (lower && (int)(blockIdx.x * TM) + TM - 1 < I * BS) return;
+  block_pair(nb, R, Q, I, J);
+  if (!rotated[Q]) {
+    // no rotation in this block pair: U_Q = I exactly, Y_Q = X_Q (nothing to
+    // do in place)
+    if (X == Y && xmode == XMODE_COLS) return;
+    const int rl = tid >> 1, half = tid & 1;
+    const int a = a0 + (rl >> 5);
+    const int row = tile_row(nb, R, gx, rl);
+    const int g0 = (half ? J : I) * BS;
+    if (row >= 0 && row < n && tile_needed(tri, a, Q)) {
+      double x[BS];
+      load_xrow(X, ldx, xmode, n, row, g0, x);
+#pragma unroll
+      for (int c = 0; c < BS; ++c) {
+        const int g = g0 + c;
+        if (g < n && (tri != TRI_SECOND || a > Q || row >= g)) {
+          Y[(size_t)g * ldy + row] = x[c];
+          if (tri == TRI_SECOND && (a > Q || row > g)) Y[(size_t)row * ldy + g] = x[c];
+        }
+      }
+    }
+    return;
+  }
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&sm.tmem)),
                  "r"(TMEM_COLS)
@@ -439,34 +509,21 @@ __global__ void __launch_bounds__(RM_THREADS, 2)
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
   if (tid == 0) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&sm.mbar)) : "memory");
-  // U_P digits (contiguous, NSL x 2 KB) and column exponents
+  // U_Q digits (contiguous, NSL x 2 KB) and column exponents
   {
-    const uint4* src = reinterpret_cast<const uint4*>(Usl + (size_t)P * NSL * (USL_BYTES / 2));
+    const uint4* src = reinterpret_cast<const uint4*>(Usl + (size_t)Q * NSL * (USL_BYTES / 2));
     uint4* dst = reinterpret_cast<uint4*>(sm.us[0]);
     for (int i = tid; i < NSL * USL_BYTES / 16; i += RM_THREADS) dst[i] = src[i];
-    if (tid < W2) sm.uexp[tid] = Uexp[P * W2 + tid];
+    if (tid < W2) sm.uexp[tid] = Uexp[Q * W2 + tid];
   }
-  // digits of X_P: this thread's row, 16 values of one block
+  // digits of X_Q: this thread's tile row, 16 values of one block (zeros for
+  // rows of tiles that are not formed)
   {
     const int rl = tid >> 1, half = tid & 1;
-    const int row = blockIdx.x * TM + rl;
-    const int g0 = (half ? J : I) * BS;  // first global index of this block
+    const int row = tile_row(nb, R, gx, rl);
+    const int g0 = (half ? J : I) * BS;
     double x[BS];
-    if (xmode == XMODE_COLS) {
-#pragma unroll
-      for (int k = 0; k < BS; ++k) x[k] = (row < n && g0 + k < n) ? X[(size_t)(g0 + k) * ldx + row] : 0.0;
-    } else if (row < n && g0 + BS <= n && ((((size_t)row * ldx + g0) & 1) == 0)) {
-      const double2* src = reinterpret_cast<const double2*>(X + (size_t)row * ldx + g0);
-#pragma unroll
-      for (int k = 0; k < BS / 2; ++k) {
-        const double2 v = src[k];
-        x[2 * k] = v.x;
-        x[2 * k + 1] = v.y;
-      }
-    } else {
-#pragma unroll
-      for (int k = 0; k < BS; ++k) x[k] = (row < n && g0 + k < n) ? X[(size_t)row * ldx + g0 + k] : 0.0;
-    }
+    load_xrow(X, ldx, xmode, n, tile_needed(tri, a0 + (rl >> 5), Q) ? row : -1, g0, x);
     unsigned long long maxbits = 0;
 #pragma unroll
     for (int k = 0; k < BS; ++k) {
@@ -532,10 +589,11 @@ __global__ void __launch_bounds__(RM_THREADS, 2)
     }
   }
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  if (ok) {
-    const int quad = warp & 3, ch = warp >> 2;
+  const int quad = warp & 3, ch = warp >> 2;
+  const int a = a0 + quad;  // this warp's block pair (warp-uniform)
+  if (ok && a < nb / 2 && tile_needed(tri, a, Q)) {
     const int rl = quad * 32 + lane;
-    const int row = blockIdx.x * TM + rl;
+    const int row = tile_row(nb, R, gx, rl);
     // Z = sum_L s_L 2^(8 (6 - L)) = hi 2^32 + lo, hi = s0 2^16 + (s1 2^8 + s2),
     // lo = (s3 2^8 + s4) 2^16 + (s5 2^8 + s6); the bracketed pairs fit 32 bits
     // (|s_L| < 2^22.2), so levels are read in pairs and combined in int32
@@ -559,13 +617,14 @@ __global__ void __launch_bounds__(RM_THREADS, 2)
         t[slot][c] = (l & 1) ? (q << 8) : t[slot][c] + q;
       }
     }
-    if (row < n) {
+    if (row >= 0 && row < n) {
       const int er = sm.rexp[rl];
       const int g0 = (ch ? J : I) * BS;
+      const bool diag = tri == TRI_SECOND && a == Q;
 #pragma unroll
       for (int c = 0; c < BS; ++c) {
         const int g = g0 + c;
-        if (g < n && (!lower || row >= g)) {
+        if (g < n && (!diag || row >= g)) {
           // hi 2^32 + lo from the partials, both exact as doubles (|hi| < 2^39, |lo| < 2^47);
           // one FP64 add rounds the sum once (the same as rounding Z)
           const int E = er + sm.uexp[ch * BS + c] - 64;
@@ -575,7 +634,7 @@ __global__ void __launch_bounds__(RM_THREADS, 2)
           const double v = (bexp > 60 && bexp < 2000) ? exact_scaled(hi, 32 + E) + exact_scaled(lo, E)
                                                       : z_to_double(hi, lo, E);
           Y[(size_t)g * ldy + row] = v;
-          if (lower && row > g) Y[(size_t)row * ldy + g] = v;  // 16 consecutive entries of column `row`
+          if (tri == TRI_SECOND && (!diag || row > g)) Y[(size_t)row * ldy + g] = v;  // the mirror entry
         }
       }
     }
@@ -652,10 +711,12 @@ cudaError_t mpj_blocked_update_A(double* A, int lda, double* B, int n, int R, vo
   const USet u = uset(scratch, n, R & 1);
   cudaError_t e = rmul_attr();
   if (e != cudaSuccess) return e;
-  const dim3 grid((n + TM - 1) / TM, nb / 2);
-  blk_rmul<<<grid, RM_THREADS, rmul_smem(), s>>>(A, lda, XMODE_COLS, B, n, n, nb, R, u.sl, u.ex, flags, 0);
+  const dim3 grid((nb / 2 + 3) / 4, nb / 2);
+  blk_rmul<<<grid, RM_THREADS, rmul_smem(), s>>>(A, lda, XMODE_COLS, B, n, n, nb, R, u.sl, u.ex, u.rot, flags,
+                                                  TRI_FIRST);
   mpj_count_launch();
-  blk_rmul<<<grid, RM_THREADS, rmul_smem(), s>>>(B, n, XMODE_ROWS, A, lda, n, nb, R, u.sl, u.ex, flags, 1);
+  blk_rmul<<<grid, RM_THREADS, rmul_smem(), s>>>(B, n, XMODE_ROWS, A, lda, n, nb, R, u.sl, u.ex, u.rot, flags,
+                                                  TRI_SECOND);
   mpj_count_launch();
   return cudaGetLastError();
 }
@@ -667,8 +728,9 @@ cudaError_t mpj_blocked_update_V(double* V, int ldv, int n, int R, void* scratch
   const USet u = uset(scratch, n, R & 1);
   cudaError_t e = rmul_attr();
   if (e != cudaSuccess) return e;
-  const dim3 grid((n + TM - 1) / TM, nb / 2);
-  blk_rmul<<<grid, RM_THREADS, rmul_smem(), s>>>(V, ldv, XMODE_COLS, V, ldv, n, nb, R, u.sl, u.ex, flags, 0);
+  const dim3 grid((nb / 2 + 3) / 4, nb / 2);
+  blk_rmul<<<grid, RM_THREADS, rmul_smem(), s>>>(V, ldv, XMODE_COLS, V, ldv, n, nb, R, u.sl, u.ex, u.rot, flags,
+                                                  TRI_ALL);
   mpj_count_launch();
   return cudaGetLastError();
 }
