@@ -390,19 +390,26 @@ def main():
     st = info["ms_stage"]
     if sweeps64 > 0:
         N32 = (n + 31) // 32 * 32
+        npairs = N32 // 32
         rounds = sweeps64 * (N32 // 16 - 1)
         round_s = st[3] / 1000.0 / rounds
         # one outer round of the block ordering: blk_solve (FP64 subproblems), then three
-        # block-diagonal right multiplications on the tensor cores (A U~ into B, B^T U~ into A,
-        # V U~), each reading and writing an n x n FP64 matrix: 48 n^2 algorithmic bytes
-        bytes_round = 48.0 * n * n
+        # block-diagonal right multiplications on the tensor cores (V U~, A U~ into B, B^T U~
+        # into A).  Algorithmic bytes: a round must read and write the column panels of A and
+        # V that its rotations change, 32 n^2 bytes when every block pair rotates (one pass
+        # over A and V, the fused lower bound); block pairs without rotations need nothing,
+        # so the bytes are 32 n^2 x (rotated block pairs / block pairs), summed over rounds.
+        rb = int(info.get("rotated_blocks64") or 0)
+        bytes_total = 32.0 * n * n * rb / npairs
+        bytes_round = bytes_total / rounds
         peak, peak_src = hbm_peak_gbs()
-        achieved = bytes_round / round_s / 1e9
+        achieved = bytes_total / (st[3] / 1000.0) / 1e9
         out["roofline"] = {"kernel": "blk_rmul x3 + blk_solve (one outer round of the block ordering)",
                            "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                            "frac": achieved / peak,
                            "traffic": traffic_per_round(BLOCK_TRAFFIC_PROFILE) if n == 4096 else None,
                            "peak_source": peak_src, "algorithmic_bytes_per_round": bytes_round,
+                           "rotated_block_fraction": rb / (rounds * npairs),
                            "avg_round_ms": round_s * 1e3, "rounds": rounds, "dominant_stage": "fp64_sweeps",
                            "share_of_step": st[3] / st[5] if st[5] else None,
                            "note": "integer-ALU and latency bound (digit slicing and the exact epilogue); "

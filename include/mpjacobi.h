@@ -113,6 +113,8 @@ typedef struct {
                         estimate (the iteration converges for ||Q_l^T Q_l - I||_2 < 2,
                         Sec. 4.3.4; the solve returns MPJ_EPREMISE when the estimate is 2 or
                         more)                                                                */
+  long long rotated_blocks64; /* block ordering: block-pair subproblems (32 x 32) that rotated,
+                        summed over all rounds of all FP64 sweeps (0 for the other orderings) */
 } mpj_info;
 
 /* Fills `o` with the defaults described in mpj_opts. */

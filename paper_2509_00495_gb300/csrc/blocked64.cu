@@ -196,7 +196,8 @@ MPJ_DEV double z_to_double(long long hi, long long lo, int E) {
 // any rotation happened.
 __global__ void __launch_bounds__(256) blk_solve(const double* __restrict__ A, int lda, int n, int nb, int R,
                                                  double skip, double skip_abs, __nv_bfloat16* __restrict__ Usl,
-                                                 int* __restrict__ Uexp, int* __restrict__ rotated) {
+                                                 int* __restrict__ Uexp, int* __restrict__ rotated,
+                                                 unsigned* __restrict__ nrot) {
   __shared__ double S[W2][LDS];
   __shared__ double U[W2][LDS];
   __shared__ double cs[W2 / 2][2];
@@ -352,7 +353,10 @@ __global__ void __launch_bounds__(256) blk_solve(const double* __restrict__ A, i
       }
     }
   }
-  if (tid == 0) rotated[P] = any;
+  if (tid == 0) {
+    rotated[P] = any;
+    if (any && nrot) atomicAdd(nrot, 1u);
+  }
 }
 
 // ---------------------------------------------------------------- right multiplication
@@ -692,13 +696,14 @@ cudaError_t rmul_attr() {
 }
 }  // namespace
 
-// Round R, step 1: the subproblems of the block pairs, U_P into set R mod 2.
+// Round R, step 1: the subproblems of the block pairs, U_P into set R mod 2;
+// *nrot (if not null) counts the block pairs that rotated.
 cudaError_t mpj_blocked_solve(const double* A, int lda, int n, int R, double skip, double skip_abs, void* scratch,
-                              cudaStream_t s) {
+                              unsigned* nrot, cudaStream_t s) {
   const int N = (n + 2 * BS - 1) / (2 * BS) * (2 * BS);
   const int nb = N / BS;
   const USet u = uset(scratch, n, R & 1);
-  blk_solve<<<nb / 2, 256, 0, s>>>(A, lda, n, nb, R, skip, skip_abs, u.sl, u.ex, u.rot);
+  blk_solve<<<nb / 2, 256, 0, s>>>(A, lda, n, nb, R, skip, skip_abs, u.sl, u.ex, u.rot, nrot);
   mpj_count_launch();
   return cudaGetLastError();
 }

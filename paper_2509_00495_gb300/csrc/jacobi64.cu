@@ -781,7 +781,7 @@ bool overlap_enabled(int n) {
 
 int mpj_jacobi64_run(int n, double* A, int lda, double* V, int ldv, double tol, int ordering, int max_sweeps,
                      int* sweeps_out, double* off_out, double* off_initial, void* scratch, size_t scratch_bytes,
-                     cudaStream_t s, double skip_abs, bool side_stream) {
+                     cudaStream_t s, double skip_abs, bool side_stream, long long* rotated_blocks_out) {
   const double skip = 0x1p-53;
   const int m = n + (n & 1);
   const int half = m / 2;
@@ -894,8 +894,9 @@ int mpj_jacobi64_run(int n, double* A, int lda, double* V, int ldv, double tol, 
     double* B = (double*)(base + scratch_fixed(n));
     void* bscratch = base + scratch_fixed(n) + align256((size_t)n * n * sizeof(double));
     unsigned* bflags = (unsigned*)(iscal + 1);
-    unsigned hflags = 0;
-    MPJ_CUDA_TRY(cudaMemsetAsync(bflags, 0, sizeof(unsigned), s));
+    unsigned* nrot = (unsigned*)(iscal + 2);
+    unsigned hflags = 0, hnrot = 0;
+    MPJ_CUDA_TRY(cudaMemsetAsync(bflags, 0, 2 * sizeof(unsigned), s));
     const int rounds = mpj_blocked_rounds_per_sweep(n);
     // V <- V U~ of round R runs on a private side stream, overlapping round
     // R+1's subproblems and A update; the U_P sets alternate between rounds,
@@ -915,7 +916,7 @@ int mpj_jacobi64_run(int n, double* A, int lda, double* V, int ldv, double tol, 
       for (int R = 0; R < rounds; ++R) {
         const int par = R & 1;
         if (side && vpending[par]) MPJ_CUDA_TRY(cudaStreamWaitEvent(s, side->done[par], 0));
-        MPJ_CUDA_TRY(mpj_blocked_solve(A, lda, n, R, skip, skip_abs, bscratch, s));
+        MPJ_CUDA_TRY(mpj_blocked_solve(A, lda, n, R, skip, skip_abs, bscratch, nrot, s));
         if (side) {
           MPJ_CUDA_TRY(cudaEventRecord(side->ready, s));
           MPJ_CUDA_TRY(cudaStreamWaitEvent(side->sv, side->ready, 0));
@@ -937,8 +938,10 @@ int mpj_jacobi64_run(int n, double* A, int lda, double* V, int ldv, double tol, 
       MPJ_CUDA_TRY(mpj_sumsq(A, lda, n, true, partial, dscal, nullptr, s));
       MPJ_CUDA_TRY(cudaMemcpyAsync(&off2, dscal, sizeof(double), cudaMemcpyDeviceToHost, s));
       MPJ_CUDA_TRY(cudaMemcpyAsync(&hflags, bflags, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+      MPJ_CUDA_TRY(cudaMemcpyAsync(&hnrot, nrot, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
       MPJ_CUDA_TRY(cudaStreamSynchronize(s));
       off = sqrt(off2);
+      if (rotated_blocks_out) *rotated_blocks_out = hnrot;
       if (hflags & MPJ_FLAG_TIMEOUT) {
         status = MPJ_ETIMEOUT;
         break;

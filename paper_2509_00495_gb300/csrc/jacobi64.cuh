@@ -18,7 +18,7 @@ size_t mpj_jacobi64_scratch_bytes_ordering(int n, int ordering);
 // per sweep, and the end-of-sweep symmetrization.
 size_t mpj_blocked_scratch_bytes(int n);
 cudaError_t mpj_blocked_solve(const double* A, int lda, int n, int R, double skip, double skip_abs, void* scratch,
-                              cudaStream_t s);
+                              unsigned* nrot, cudaStream_t s);
 cudaError_t mpj_blocked_update_A(double* A, int lda, double* B, int n, int R, void* scratch, unsigned* flags,
                                  cudaStream_t s);
 cudaError_t mpj_blocked_update_V(double* V, int ldv, int n, int R, void* scratch, unsigned* flags, cudaStream_t s);
@@ -32,10 +32,13 @@ cudaError_t mpj_blocked_symmetrize(double* A, int lda, int n, cudaStream_t s);
 // room for two V batches, MPJ_JACOBI_OVERLAP not "0"), the batched V updates
 // run on a private non-blocking stream, overlapping the next rounds; it is
 // joined back into `s` before every scale fold, so V is complete in `s` order
-// on return.  Returns MPJ_OK / MPJ_NOT_CONVERGED / MPJ_ECUDA / MPJ_EWORKSPACE.
+// on return.  rotated_blocks_out (block ordering, if not null) receives the
+// number of block-pair subproblems that rotated, summed over all rounds.
+// Returns MPJ_OK / MPJ_NOT_CONVERGED / MPJ_ECUDA / MPJ_EWORKSPACE.
 int mpj_jacobi64_run(int n, double* A, int lda, double* V, int ldv, double tol, int ordering, int max_sweeps,
                      int* sweeps_out, double* off_out, double* off_initial, void* scratch, size_t scratch_bytes,
-                     cudaStream_t s, double skip_abs = 0.0, bool side_stream = true);
+                     cudaStream_t s, double skip_abs = 0.0, bool side_stream = true,
+                     long long* rotated_blocks_out = nullptr);
 
 // Sum of squares of A's entries (off_only: off-diagonal entries) into *out,
 // through 256 per-CTA partials summed in a fixed order; sets

@@ -606,8 +606,10 @@ int mpj_syev_ex(int n, const double* A, int lda, double* W, double* Q, int ldq, 
     }
     {
       const bool thr = o.threshold > 0 || (o.threshold < 0 && o.ordering != MPJ_ORDER_CYCLIC);
+      long long rb = 0;
       int r4 = mpj_jacobi64_run(n, Ac, n, V, n, tol, o.ordering, o.max_sweeps64, &sweeps64, &offf, &offc, scratch,
-                                mpj_jacobi64_scratch_bytes_ordering(n, o.ordering), s, thr ? tol / n : 0.0);
+                                mpj_jacobi64_scratch_bytes_ordering(n, o.ordering), s, thr ? tol / n : 0.0, true, &rb);
+      if (info) info->rotated_blocks64 = rb;
       if (r4 < 0) {
         st = r4;
         goto done;

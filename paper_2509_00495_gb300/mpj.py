@@ -57,7 +57,7 @@ class Info(ctypes.Structure):
     _fields_ = [("status", _i), ("sweeps32", _i), ("sweeps32_pass2", _i), ("sweeps64", _i), ("ns_steps", _i),
                 ("norm_fro", _d),
                 ("tol", _d), ("off32", _d), ("off_cond", _d), ("off_final", _d), ("ms_stage", ctypes.c_float * 6),
-                ("ns_e0", _d)]
+                ("ns_e0", _d), ("rotated_blocks64", ctypes.c_longlong)]
 
     def as_dict(self) -> dict:
         d = {k: getattr(self, k) for k, _ in self._fields_ if k != "ms_stage"}
