@@ -4,11 +4,14 @@
 //   M = Q^T dQ,  G_ii = dW_i,  G_ij = M_ij / (w_j - w_i) (i != j),
 //   dA = sym(Q G Q^T) = Q sym(G) Q^T,  sym(X) = (X + X^T)/2.
 // Symmetrizing G first makes the last product symmetric in exact arithmetic,
-// so it runs as a lower-tile product with mirrored writes (exactly symmetric
-// dA, half the flops): 2n^3 + 2n^3 + n^3 FP64 flops per matrix on the DMMA
-// kernel, batched over blockIdx.z.
+// so dA is written exactly symmetric (its lower triangle mirrored).  The three
+// products run, matrix after matrix, as FP64-accurate products on the tensor
+// cores (exact bf16 slices, ozaki.cu; Q sliced once per matrix for the two
+// products it enters from the same side), or with MPJ_GEMM_TC=0 on the FP64
+// DMMA kernel, batched over blockIdx.z (the last one as a lower-tile product).
 #include "common.cuh"
 #include "gemm64.cuh"
+#include "ozaki.cuh"
 
 namespace {
 
@@ -42,6 +45,16 @@ __global__ void adjoint_core(const double* __restrict__ M, const double* __restr
   }
 }
 
+// B(j, i) = B(i, j) for i > j (the lower triangle mirrored), batched over blockIdx.y
+__global__ void bwd_mirror(double* __restrict__ B, int ldb, long long sb, int n) {
+  double* Bb = B + (size_t)blockIdx.y * sb;
+  const size_t total = (size_t)n * n;
+  for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)(idx % n), j = (int)(idx / n);
+    if (i > j) Bb[(size_t)i * ldb + j] = Bb[(size_t)j * ldb + i];
+  }
+}
+
 }  // namespace
 
 extern "C" int mpj_syev_backward(int batch, int n, const double* W, const double* Q, int ldq, const double* dW,
@@ -51,20 +64,32 @@ extern "C" int mpj_syev_backward(int batch, int n, const double* W, const double
   if (batch == 0 || n == 0) return MPJ_OK;
   if (!W || !Q || !dA) return MPJ_EINVAL;
   size_t sq = (size_t)n * n;
+  const bool tc = mpj_gemm_tc_enabled();
+  const size_t ob = tc ? (mpj_oz_operand_bytes(n, n) + 255) / 256 * 256 : 0;
   void* w = nullptr;
-  size_t bytes = 2 * (size_t)batch * sq * sizeof(double) + 256;
+  size_t bytes = 2 * (size_t)batch * sq * sizeof(double) + 256 + 3 * ob;
   if (cudaMallocAsync(&w, bytes, s) != cudaSuccess) return MPJ_ENOMEM;
   mpj_count_alloc();
   double* M = (double*)w;
   double* T = M + (size_t)batch * sq;
   unsigned* flags = (unsigned*)(T + (size_t)batch * sq);
+  char* obuf = (char*)flags + 256;  // three sliced operands (tensor-core products)
   int st = MPJ_OK;
   unsigned hflags = 0;
   cudaError_t e = cudaMemsetAsync(flags, 0, sizeof(unsigned), s);
   long long sQ = (long long)ldq * n, sdQ = (long long)lddq * n, sA = (long long)ldda * n, sN = (long long)sq;
   if (e == cudaSuccess && dQ) {  // M = Q^T dQ
-    GemmArgs g{n, n, n, 1.0, 0.0, Q, ldq, sQ, dQ, lddq, sdQ, nullptr, n, 0, M, n, sN, 0};
-    e = mpj_gemm64_launch(g, true, false, batch, s);
+    if (tc) {
+      for (int b = 0; b < batch && e == cudaSuccess; ++b) {
+        OzOperand oq, od;  // rows of Q^T (columns of Q) and columns of dQ, over the row index
+        e = mpj_oz_prepare(Q + b * sQ, ldq, 1, n, n, obuf, &oq, s);
+        if (e == cudaSuccess) e = mpj_oz_prepare(dQ + b * sdQ, lddq, 1, n, n, obuf + ob, &od, s);
+        if (e == cudaSuccess) e = mpj_oz_gemm(oq, od, n, n, 1.0, 0.0, nullptr, n, M + b * sN, n, flags, s);
+      }
+    } else {
+      GemmArgs g{n, n, n, 1.0, 0.0, Q, ldq, sQ, dQ, lddq, sdQ, nullptr, n, 0, M, n, sN, 0};
+      e = mpj_gemm64_launch(g, true, false, batch, s);
+    }
   }
   if (e == cudaSuccess) {  // T = sym(G) (into T), then M = Q T, then dA = M Q^T (symmetric)
     dim3 grid((n + 255) / 256 > 8 ? 8 : (n + 255) / 256, n, batch);
@@ -72,13 +97,28 @@ extern "C" int mpj_syev_backward(int batch, int n, const double* W, const double
     mpj_count_launch();
     e = cudaGetLastError();
   }
-  if (e == cudaSuccess) {
+  if (e == cudaSuccess && tc) {
+    for (int b = 0; b < batch && e == cudaSuccess; ++b) {
+      OzOperand oq, ot, om;  // rows of Q (left of Q T, right of M Q^T), columns of T, rows of M
+      e = mpj_oz_prepare(Q + b * sQ, 1, ldq, n, n, obuf, &oq, s);
+      if (e == cudaSuccess) e = mpj_oz_prepare(T + b * sN, n, 1, n, n, obuf + ob, &ot, s);
+      if (e == cudaSuccess) e = mpj_oz_gemm(oq, ot, n, n, 1.0, 0.0, nullptr, n, M + b * sN, n, flags, s);
+      if (e == cudaSuccess) e = mpj_oz_prepare(M + b * sN, 1, n, n, n, obuf + 2 * ob, &om, s);
+      if (e == cudaSuccess) e = mpj_oz_gemm(om, oq, n, n, 1.0, 0.0, nullptr, n, dA + b * sA, ldda, flags, s);
+    }
+    if (e == cudaSuccess) {
+      const size_t blocks = (sq + 255) / 256;
+      bwd_mirror<<<dim3((unsigned)(blocks > 1024 ? 1024 : blocks), batch), 256, 0, s>>>(dA, ldda, sA, n);
+      mpj_count_launch();
+      e = cudaGetLastError();
+    }
+  } else if (e == cudaSuccess) {
     GemmArgs g{n, n, n, 1.0, 0.0, Q, ldq, sQ, T, n, sN, nullptr, n, 0, M, n, sN, 0};
     e = mpj_gemm64_launch(g, false, false, batch, s);
-  }
-  if (e == cudaSuccess) {
-    GemmArgs g{n, n, n, 1.0, 0.0, M, n, sN, Q, ldq, sQ, nullptr, n, 0, dA, ldda, sA, 1};
-    e = mpj_gemm64_launch(g, false, true, batch, s);
+    if (e == cudaSuccess) {
+      GemmArgs g2{n, n, n, 1.0, 0.0, M, n, sN, Q, ldq, sQ, nullptr, n, 0, dA, ldda, sA, 1};
+      e = mpj_gemm64_launch(g2, false, true, batch, s);
+    }
   }
   if (e == cudaSuccess) e = cudaMemcpyAsync(&hflags, flags, sizeof(unsigned), cudaMemcpyDeviceToHost, s);
   if (e != cudaSuccess) {
@@ -92,5 +132,6 @@ extern "C" int mpj_syev_backward(int batch, int n, const double* W, const double
     st = MPJ_ECUDA;
   }
   if (st == MPJ_OK && (hflags & MPJ_FLAG_DEGENERATE)) st = MPJ_EDEGENERATE;
+  if (st == MPJ_OK && (hflags & MPJ_FLAG_TIMEOUT)) st = MPJ_ETIMEOUT;
   return st;
 }

@@ -51,6 +51,8 @@
 #include <stdio.h>
 
 #include "common.cuh"
+#include <stdlib.h>
+
 #include "ozaki.cuh"
 
 namespace {
@@ -422,6 +424,15 @@ inline int pad_rows(int R) { return (R + OZ_TM - 1) / OZ_TM * OZ_TM; }
 inline int pad_k(int K) { return (K + OZ_KC - 1) / OZ_KC * OZ_KC; }
 
 }  // namespace
+
+bool mpj_gemm_tc_enabled() {
+  static int v = -1;
+  if (v < 0) {
+    const char* e = getenv("MPJ_GEMM_TC");
+    v = (e && e[0] == '0') ? 0 : 1;
+  }
+  return v == 1;
+}
 
 size_t mpj_oz_operand_bytes(int R, int K) {
   const size_t Rp = (size_t)pad_rows(R), Kp = (size_t)pad_k(K);

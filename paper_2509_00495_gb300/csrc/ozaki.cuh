@@ -32,3 +32,7 @@ cudaError_t mpj_oz_prepare(const double* X, long long rs, long long ks, int R, i
 // MPJ_FLAG_TIMEOUT in *flags (device word, may be null).
 cudaError_t mpj_oz_gemm(const OzOperand& a, const OzOperand& b, int m, int n, double alpha, double beta,
                         const double* Cin, int ldcin, double* C, int ldc, unsigned* flags, cudaStream_t s);
+
+// Whether the FP64 products of the solver and of the adjoint run on this
+// engine (default) or on the FP64 DMMA kernel (environment MPJ_GEMM_TC=0).
+bool mpj_gemm_tc_enabled();

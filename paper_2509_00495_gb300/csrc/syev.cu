@@ -134,14 +134,7 @@ __global__ void mirror_lower(double* __restrict__ B, int ldb, int n) {
 
 // The Newton-Schulz and A_cond products run on the tensor cores (exact bf16
 // slices, ozaki.cu) unless MPJ_GEMM_TC=0 selects the FP64 DMMA kernel.
-bool gemm_tensor_cores() {
-  static int v = -1;
-  if (v < 0) {
-    const char* e = getenv("MPJ_GEMM_TC");
-    v = (e && e[0] == '0') ? 0 : 1;
-  }
-  return v == 1;
-}
+bool gemm_tensor_cores() { return mpj_gemm_tc_enabled(); }
 
 // rank_i = #{j : w_j < w_i or (w_j == w_i and j < i)}  (ascending, stable)
 __global__ void rank_diag(const double* __restrict__ Ac, int ldc, int n, int sort, int* __restrict__ rank,
