@@ -114,12 +114,6 @@ MPJ_DEV void digits_f32(double x, int e, uint32_t d[NSL]) {
 // Two FP32 digit patterns packed as two bf16 (a in the low half).
 MPJ_DEV uint32_t pack_bf16x2(uint32_t a, uint32_t b) { return __byte_perm(a, b, 0x7632); }
 
-MPJ_DEV int exp_of_max(double m) {
-  int e = 0;
-  if (m > 0.0) frexp(m, &e);
-  return e;
-}
-
 // The same from the bit pattern of max|x| (a non-negative double), with
 // integer instructions only: the smallest e with max|x| < 2^e (0 for zero).
 MPJ_DEV int exp_of_maxbits(unsigned long long b) {
@@ -194,14 +188,13 @@ MPJ_DEV double z_to_double(long long hi, long long lo, int E) {
 // Writes per block pair: NSL digit tiles (32 x 32 bf16, K-major over the
 // rows of U_P, one "row" per column of U_P), 32 column exponents, and whether
 // any rotation happened.
-__global__ void __launch_bounds__(256) blk_solve(const double* __restrict__ A, int lda, int n, int nb, int R,
+constexpr int SOLVE_THREADS = 512;
+__global__ void __launch_bounds__(SOLVE_THREADS) blk_solve(const double* __restrict__ A, int lda, int n, int nb, int R,
                                                  double skip, double skip_abs, __nv_bfloat16* __restrict__ Usl,
                                                  int* __restrict__ Uexp, int* __restrict__ rotated,
                                                  unsigned* __restrict__ nrot) {
   __shared__ double S[W2][LDS];
   __shared__ double U[W2][LDS];
-  __shared__ double cs[W2 / 2][2];
-  __shared__ int rot[W2 / 2];
   __shared__ int any;
   const int P = blockIdx.x, tid = threadIdx.x;
   int I, J;
@@ -214,65 +207,116 @@ __global__ void __launch_bounds__(256) blk_solve(const double* __restrict__ A, i
     U[li][lj] = (li == lj) ? 1.0 : 0.0;
   }
   __syncthreads();
-  // Each inner round: the 16 rotation records, then every 2 x 2 block of S
+  // Each inner round applies its 16 rotations to every 2 x 2 block of S
   // between two pairs a <= b once (rows by J_a, then columns by J_b, as the
   // sequential order does for a before b; the mirror block is the same values
-  // transposed) and the two columns of U of every pair.
-  __shared__ int pq[W2 / 2][2];
-  for (int rho = 0; rho < W2 - 1; ++rho) {
-    if (tid < W2 / 2) {
-      int x, y;
-      rr_slot(W2, rho, tid, x, y);
-      const int p = x < y ? x : y, q = x < y ? y : x;
-      double t = 0.0, cm1 = 0.0, s = 0.0;
-      // Algorithm 2 (stable form) with the skip test of Algorithm 4
-      const int r = gidx(I, J, q) < n && jacobi_pair<double>(S[p][p], S[q][q], S[p][q], skip, t, cm1, s, skip_abs);
-      if (r) any = 1;
-      cs[tid][0] = cm1;
-      cs[tid][1] = s;
-      rot[tid] = r;
-      pq[tid][0] = p;
-      pq[tid][1] = q;
+  // transposed) and to the two columns of U of every pair.  The next round's
+  // rotations read only the blocks (a, a) and the blocks (a, b) that hold one
+  // of its pairs: warp 0 updates those "critical" blocks first and then
+  // computes the next round's rotations, while warps 1-7 update the other
+  // blocks and U.  Each block is updated by exactly one thread with the same
+  // arithmetic as in sequential order, so the result does not depend on this
+  // division of the work.
+  __shared__ double cs[2][W2 / 2][2];
+  __shared__ int rot[2][W2 / 2];
+  __shared__ int pq[2][W2 / 2][2];
+  __shared__ int slot_of[2][W2];  // pair slot of each local index in the round
+  const int warp = tid >> 5, lane = tid & 31;
+  // Algorithm 2 with the skip test of Algorithm 4 for pair `k` of inner round rho
+  auto rotation = [&](int rho, int k, int buf) {
+    int x, y;
+    rr_slot(W2, rho, k, x, y);
+    const int p = x < y ? x : y, q = x < y ? y : x;
+    double t = 0.0, cm1 = 0.0, sn = 0.0;
+    const int r = gidx(I, J, q) < n && jacobi_pair<double>(S[p][p], S[q][q], S[p][q], skip, t, cm1, sn, skip_abs);
+    if (r) any = 1;
+    cs[buf][k][0] = cm1;
+    cs[buf][k][1] = sn;
+    rot[buf][k] = r;
+    pq[buf][k][0] = p;
+    pq[buf][k][1] = q;
+    slot_of[buf][p] = k;
+    slot_of[buf][q] = k;
+  };
+  // the 2 x 2 block between pairs a <= b of the round in buffer `buf`
+  auto block_update = [&](int a, int b, int buf) {
+    if (!rot[buf][a] && !rot[buf][b]) return;
+    const int pa = pq[buf][a][0], qa = pq[buf][a][1], pb = pq[buf][b][0], qb = pq[buf][b][1];
+    double b00 = S[pa][pb], b01 = S[pa][qb], b10 = S[qa][pb], b11 = S[qa][qb];
+    if (rot[buf][a]) {
+      rot_apply(cs[buf][a][0], cs[buf][a][1], b00, b10);  // rows pa, qa of column pb
+      rot_apply(cs[buf][a][0], cs[buf][a][1], b01, b11);  // of column qb
     }
-    __syncthreads();
-    for (int task = tid; task < 136 + (W2 / 2) * W2; task += blockDim.x) {
-      if (task < 136) {
-        // pair indices a <= b from the triangular task number
-        int a = 0, rem = task;
-        while (rem >= 16 - a) {
-          rem -= 16 - a;
-          ++a;
+    if (rot[buf][b]) {
+      rot_apply(cs[buf][b][0], cs[buf][b][1], b00, b01);  // columns pb, qb of row pa
+      rot_apply(cs[buf][b][0], cs[buf][b][1], b10, b11);  // of row qa
+    }
+    S[pa][pb] = b00;
+    S[pa][qb] = b01;
+    S[qa][pb] = b10;
+    S[qa][qb] = b11;
+    if (a != b) {
+      S[pb][pa] = b00;
+      S[qb][pa] = b01;
+      S[pb][qa] = b10;
+      S[qb][qa] = b11;
+    }
+  };
+  if (warp == 0 && lane < W2 / 2) rotation(0, lane, 0);
+  __syncthreads();
+  for (int rho = 0; rho < W2 - 1; ++rho) {
+    const int cur = rho & 1;
+    const bool more = rho + 1 < W2 - 1;
+    if (warp == 0) {
+      // lanes 0-15: the diagonal blocks; lanes 16-31: the block holding pair
+      // lane - 16 of the next round (once, when two next pairs share a block)
+      if (lane < W2 / 2) {
+        block_update(lane, lane, cur);
+      } else if (more) {
+        int x, y;
+        rr_slot(W2, rho + 1, lane - W2 / 2, x, y);
+        int a = slot_of[cur][x], b = slot_of[cur][y];
+        if (a > b) {
+          const int t = a;
+          a = b;
+          b = t;
+          const int tx = x;
+          x = y;
+          y = tx;
         }
-        const int b = a + rem;
-        if (!rot[a] && !rot[b]) continue;
-        const int pa = pq[a][0], qa = pq[a][1], pb = pq[b][0], qb = pq[b][1];
-        double b00 = S[pa][pb], b01 = S[pa][qb], b10 = S[qa][pb], b11 = S[qa][qb];
-        if (rot[a]) {
-          rot_apply(cs[a][0], cs[a][1], b00, b10);  // rows pa, qa of column pb
-          rot_apply(cs[a][0], cs[a][1], b01, b11);  // of column qb
+        // x is in pair a: the other index of a, if its next partner is in b,
+        // gives the same block; the smaller of the two indices takes it
+        const int o = pq[cur][a][0] == x ? pq[cur][a][1] : pq[cur][a][0];
+        const bool dup = slot_of[cur][rr_partner(W2, rho + 1, o)] == b;
+        if (a != b && (!dup || x < o)) block_update(a, b, cur);
+      }
+      __syncwarp();
+      if (more && lane < W2 / 2) rotation(rho + 1, lane, cur ^ 1);
+    } else {
+      for (int task = tid - 32; task < 136 + (W2 / 2) * W2; task += blockDim.x - 32) {
+        if (task < 136) {
+          // pair indices a < b from the triangular task number (a == b: warp 0)
+          int a = 0, rem = task;
+          while (rem >= 16 - a) {
+            rem -= 16 - a;
+            ++a;
+          }
+          const int b = a + rem;
+          if (a == b) continue;
+          if (more) {  // a block that holds a pair of the next round: warp 0
+            const int na = rr_partner(W2, rho + 1, pq[cur][a][0]), nq = rr_partner(W2, rho + 1, pq[cur][a][1]);
+            if (slot_of[cur][na] == b || slot_of[cur][nq] == b) continue;
+          }
+          block_update(a, b, cur);
+        } else {
+          const int e = task - 136, k = e / W2, j = e % W2;
+          if (!rot[cur][k]) continue;
+          const int p = pq[cur][k][0], q = pq[cur][k][1];
+          double up = U[j][p], uq = U[j][q];
+          rot_apply(cs[cur][k][0], cs[cur][k][1], up, uq);
+          U[j][p] = up;
+          U[j][q] = uq;
         }
-        if (rot[b]) {
-          rot_apply(cs[b][0], cs[b][1], b00, b01);  // columns pb, qb of row pa
-          rot_apply(cs[b][0], cs[b][1], b10, b11);  // of row qa
-        }
-        S[pa][pb] = b00;
-        S[pa][qb] = b01;
-        S[qa][pb] = b10;
-        S[qa][qb] = b11;
-        if (a != b) {
-          S[pb][pa] = b00;
-          S[qb][pa] = b01;
-          S[pb][qa] = b10;
-          S[qb][qa] = b11;
-        }
-      } else {
-        const int e = task - 136, k = e / W2, j = e % W2;
-        if (!rot[k]) continue;
-        const int p = pq[k][0], q = pq[k][1];
-        double up = U[j][p], uq = U[j][q];
-        rot_apply(cs[k][0], cs[k][1], up, uq);
-        U[j][p] = up;
-        U[j][q] = uq;
       }
     }
     __syncthreads();
@@ -283,11 +327,12 @@ __global__ void __launch_bounds__(256) blk_solve(const double* __restrict__ A, i
   // sweeps, so each U_P is made orthogonal to working precision first.
   {
     // E is symmetric: the 528 entries i <= j, mirrored (S is free now: it holds E)
-    double e3[3];
-    int ij[3];
+    constexpr int NE = (528 + SOLVE_THREADS - 1) / SOLVE_THREADS;
+    double e3[NE];
+    int ij[NE];
 #pragma unroll
-    for (int t = 0; t < 3; ++t) {
-      const int idx = tid + t * 256;
+    for (int t = 0; t < NE; ++t) {
+      const int idx = tid + t * SOLVE_THREADS;
       e3[t] = 0.0;
       ij[t] = -1;
       if (idx < 528) {
@@ -305,7 +350,7 @@ __global__ void __launch_bounds__(256) blk_solve(const double* __restrict__ A, i
     }
     __syncthreads();
 #pragma unroll
-    for (int t = 0; t < 3; ++t)
+    for (int t = 0; t < NE; ++t)
       if (ij[t] >= 0) {
         const int i = ij[t] / W2, j = ij[t] % W2;
         S[i][j] = e3[t];
@@ -313,44 +358,55 @@ __global__ void __launch_bounds__(256) blk_solve(const double* __restrict__ A, i
       }
     __syncthreads();
     // |E| is at the rounding level, so U E is formed in FP32 (its relative
-    // error 2^-24 of a 1e-15 correction is far below FP64 rounding)
-    double u4[4];
+    // error 2^-24 of a 1e-15 correction is far below FP64 rounding); U and E
+    // are rounded to FP32 once (FP64 conversions issue on the slow FP64 pipe)
+    __shared__ float Uf[W2][W2 + 1], Ef[W2][W2 + 1];
+    for (int e = tid; e < W2 * W2; e += SOLVE_THREADS) {
+      const int i = e % W2, j = e / W2;
+      Uf[i][j] = (float)U[i][j];
+      Ef[i][j] = (float)S[i][j];
+    }
+    __syncthreads();
+    constexpr int NU = W2 * W2 / SOLVE_THREADS;
+    double u4[NU];
 #pragma unroll
-    for (int t = 0; t < 4; ++t) {
-      const int idx = tid + t * 256, i = idx % W2, j = idx / W2;
+    for (int t = 0; t < NU; ++t) {
+      const int idx = tid + t * SOLVE_THREADS, i = idx % W2, j = idx / W2;
       float acc = 0.0f;
-      for (int k = 0; k < W2; ++k) acc = fmaf((float)U[i][k], (float)S[k][j], acc);
+      for (int k = 0; k < W2; ++k) acc = fmaf(Uf[i][k], Ef[k][j], acc);
       u4[t] = fma(-0.5, (double)acc, U[i][j]);
     }
     __syncthreads();
 #pragma unroll
-    for (int t = 0; t < 4; ++t) {
-      const int idx = tid + t * 256, i = idx % W2, j = idx / W2;
+    for (int t = 0; t < NU; ++t) {
+      const int idx = tid + t * SOLVE_THREADS, i = idx % W2, j = idx / W2;
       U[i][j] = u4[t];
     }
     __syncthreads();
   }
-  // digits of U_P's columns: column c is "row" c of the right operand, over k = row of U_P
+  // digits of U_P's columns: column c is "row" c of the right operand, over
+  // k = row of U_P; four threads per column, eight values each
   __nv_bfloat16* dst = Usl + (size_t)P * NSL * (USL_BYTES / 2);
-  if (tid < W2) {
-    const int c = tid;
-    double m = 0.0;
-    for (int k = 0; k < W2; ++k) m = fmax(m, fabs(U[k][c]));
-    const int e = exp_of_max(m);
-    Uexp[P * W2 + c] = e;
-    for (int k0 = 0; k0 < W2; k0 += 8) {
-      uint32_t d[8][NSL];
+  if (tid < 4 * W2) {
+    const int c = tid >> 2, k0 = (tid & 3) * 8;
+    unsigned long long maxbits = 0;
+    for (int k = 0; k < W2; ++k) {
+      const unsigned long long b = (unsigned long long)__double_as_longlong(U[k][c]) & 0x7FFFFFFFFFFFFFFFULL;
+      maxbits = b > maxbits ? b : maxbits;
+    }
+    const int e = exp_of_maxbits(maxbits);
+    if ((tid & 3) == 0) Uexp[P * W2 + c] = e;
+    uint32_t d[8][NSL];
 #pragma unroll
-      for (int j = 0; j < 8; ++j) digits_f32(U[k0 + j][c], e, d[j]);
+    for (int j = 0; j < 8; ++j) digits_f32(U[k0 + j][c], e, d[j]);
 #pragma unroll
-      for (int s = 0; s < NSL; ++s) {
-        uint4 q;
-        q.x = pack_bf16x2(d[0][s], d[1][s]);
-        q.y = pack_bf16x2(d[2][s], d[3][s]);
-        q.z = pack_bf16x2(d[4][s], d[5][s]);
-        q.w = pack_bf16x2(d[6][s], d[7][s]);
-        *reinterpret_cast<uint4*>(reinterpret_cast<char*>(dst + (size_t)s * (USL_BYTES / 2)) + kmaj16(c, k0)) = q;
-      }
+    for (int sl = 0; sl < NSL; ++sl) {
+      uint4 q;
+      q.x = pack_bf16x2(d[0][sl], d[1][sl]);
+      q.y = pack_bf16x2(d[2][sl], d[3][sl]);
+      q.z = pack_bf16x2(d[4][sl], d[5][sl]);
+      q.w = pack_bf16x2(d[6][sl], d[7][sl]);
+      *reinterpret_cast<uint4*>(reinterpret_cast<char*>(dst + (size_t)sl * (USL_BYTES / 2)) + kmaj16(c, k0)) = q;
     }
   }
   if (tid == 0) {
@@ -703,7 +759,7 @@ cudaError_t mpj_blocked_solve(const double* A, int lda, int n, int R, double ski
   const int N = (n + 2 * BS - 1) / (2 * BS) * (2 * BS);
   const int nb = N / BS;
   const USet u = uset(scratch, n, R & 1);
-  blk_solve<<<nb / 2, 256, 0, s>>>(A, lda, n, nb, R, skip, skip_abs, u.sl, u.ex, u.rot, nrot);
+  blk_solve<<<nb / 2, SOLVE_THREADS, 0, s>>>(A, lda, n, nb, R, skip, skip_abs, u.sl, u.ex, u.rot, nrot);
   mpj_count_launch();
   return cudaGetLastError();
 }
