@@ -14,10 +14,11 @@
 // sets, so applying them to the rest of the matrix afterwards as products
 //   A[P,Q] <- U_P^T A[P,Q] U_Q,   V[:,Q] <- V[:,Q] U_Q
 // (P, Q = index sets of block pairs) gives the same iterates as applying them
-// one by one.  Each round is two launches: the subproblem solves and the
-// blocked update (FP32 FMA), which touch A32 and V32 once per round instead of
-// once per pair step.  off(A32) is reduced after each sweep; stop at
-// off(A32) <= tol32 or the sweep cap.
+// one by one.  Each round is the subproblem solves and three block-diagonal
+// right multiplications (FP32 FMA, rmul32): V U~, B = A U~ and A = B^T U~,
+// each restricted to the tiles the next step needs, so that A32 and V32 are
+// touched once or twice per round instead of once per pair step.  off(A32) is
+// reduced after each sweep; stop at off(A32) <= tol32 or the sweep cap.
 #include <cuda_fp16.h>
 #include <stdlib.h>
 
@@ -165,133 +166,145 @@ __global__ void __launch_bounds__(256) solve32(const float* __restrict__ A32, in
   }
 }
 
-__device__ __forceinline__ void tri_tile(int t, int nt, int& ti, int& tj) {
-  tj = 0;
-  while (t >= nt - tj) {
-    t -= nt - tj;
-    ++tj;
-  }
-  ti = tj + t;
-}
 
-// Blocked application of the round's U's: lower tiles of A32 (with mirror)
-// and 32-row tiles of V32.  One 64-thread CTA per 32 x 32 tile; each thread
-// owns a 4 x 4 block of the result, so every pair of float4 shared-memory
-// loads feeds 16 FMAs.
-constexpr int UT = 64;  // threads per update tile
-constexpr int LD4 = 36; // padded row length (keeps rows 16-byte aligned)
+// ---------------------------------------------------------------- block update
+// The round's rotations applied to the rest of A32 and to V32 as three
+// block-diagonal right multiplications Y[:, g_Q(c)] = X_Q U_Q (FP32 FMA, K = 32):
+//   V <- V U~ (every tile),  B = A U~ (tiles a < Q),  A = B^T U~ (tiles a > Q,
+//   written to both triangles; the diagonal tiles a = Q are the solved
+//   subproblems S),
+// over tiles (a, Q): block pair Q and the 128 rows that are the 32 indices of
+// each of the block pairs a = 4 gx .. 4 gx + 3.  In exact arithmetic this is
+// A <- U~^T A U~ (the second step reads B only in tiles (Q, a), Q < a, the
+// ones the first formed).  128 threads: the tile's 128 x 32 values of X_Q and
+// U_Q in shared memory, then thread t forms the 4 x 8 block of tile rows
+// 4 (t mod 32) .. +3 and columns 8 (t / 32) .. +7: per k one float4 of X (four
+// shared-memory wavefronts per warp) and two broadcast float4 of U_Q feed 32
+// FMAs, so the FP32 pipe, not shared memory, sets the pace.
+enum { R32_ALL = 0, R32_FIRST = 1, R32_SECOND = 2 };
+enum { X32_COLS = 0, X32_ROWS = 1 };
+constexpr int RT = 128;
+constexpr int XLD = 132;  // padded row length of the X tile (k-major), 16-byte aligned rows
+constexpr int ULD = 40;   // padded row length of U_Q, 16-byte aligned rows
 
-// acc[a][b] = sum_l Lt[l][i4 + a] * R[l][j4 + b]  (a 4 x 4 block of Lt^T R, both
-// operands 32 x 32 row-major in shared memory).
-MPJ_DEV void tile_mm(const float (*Lt)[LD4], const float (*R)[LD4], float acc[4][4], int i4, int j4) {
-#pragma unroll
-  for (int a = 0; a < 4; ++a)
-#pragma unroll
-    for (int b = 0; b < 4; ++b) acc[a][b] = 0.0f;
-#pragma unroll 8
-  for (int l = 0; l < W2; ++l) {
-    float4 x = *reinterpret_cast<const float4*>(&Lt[l][i4]);  // op(L)[i4..i4+3][l]
-    float4 y = *reinterpret_cast<const float4*>(&R[l][j4]);   // R[l][j4..j4+3]
-    float xa[4] = {x.x, x.y, x.z, x.w}, yb[4] = {y.x, y.y, y.z, y.w};
-#pragma unroll
-    for (int a = 0; a < 4; ++a)
-#pragma unroll
-      for (int b = 0; b < 4; ++b) acc[a][b] = fmaf(xa[a], yb[b], acc[a][b]);
-  }
-}
-
-// all tile loads unrolled (48 in flight per thread): 127 registers, 8 CTAs/SM
-__global__ void __launch_bounds__(UT, 8) update32(float* __restrict__ A32, float* __restrict__ V32, int N, int nb, int R,
-                                               const float* __restrict__ Sbuf, const float* __restrict__ Ubuf,
-                                               int n_atiles, bool hq) {
-  // three 32 x 32 buffers (13.5 KB): the tile (later X^T), U_P, U_Q
-  __shared__ __align__(16) float T[W2][LD4];
-  __shared__ __align__(16) float UP[W2][LD4];  // U_P[l][i]
-  __shared__ __align__(16) float UQ[W2][LD4];  // U_Q[l][j]
+__global__ void __launch_bounds__(RT) rmul32(const float* X, int xmode, float* Y, int N, int nb, int R,
+                                             const float* __restrict__ Sbuf, const float* __restrict__ Ubuf, int tri,
+                                             bool hq) {
+  __shared__ __align__(16) float Xs[W2][XLD];  // Xs[k][r] = X_Q(r, k)
+  __shared__ __align__(16) float Us[W2][ULD];  // Us[k][c] = U_Q(k, c)
   const int tid = threadIdx.x;
-  const int i4 = (tid % 8) * 4, j4 = (tid / 8) * 4;
-  const int npairs = nb / 2;
-  int item = blockIdx.x;
-  float acc[4][4];
-  if (item < n_atiles) {
-    int P, Q;
-    tri_tile(item, npairs, P, Q);
-    int IP, JP, IQ, JQ;
-    block_pair(nb, R, P, IP, JP);
-    block_pair(nb, R, Q, IQ, JQ);
-    if (P == Q) {
-      const float* Sp = Sbuf + (size_t)P * W2 * W2;
-      #pragma unroll
-      for (int it = 0; it < W2 * W2 / UT; ++it) {
-        const int e = tid + it * UT;
-        int li = e % W2, lj = e / W2;
-        A32[(size_t)gidx(IP, JP, lj) * N + gidx(IP, JP, li)] = Sp[e];
+  const int Q = blockIdx.y, gx = blockIdx.x, npairs = nb / 2;
+  const int a0 = 4 * gx, a1 = min(4 * gx + 3, npairs - 1);
+  if ((tri == R32_FIRST && a0 >= Q) || (tri == R32_SECOND && a1 < Q)) return;
+  int IQ, JQ;
+  block_pair(nb, R, Q, IQ, JQ);
+  const float* Uq = Ubuf + (size_t)Q * W2 * W2;  // column-major 32 x 32: U(k, c) at Uq[k + 32 c]
+#pragma unroll
+  for (int it = 0; it < W2 * W2 / (4 * RT); ++it) {
+    const int e = 4 * (tid + it * RT), k = e % W2, c = e / W2;
+    const float4 v = *reinterpret_cast<const float4*>(Uq + e);
+    Us[k][c] = v.x;
+    Us[k + 1][c] = v.y;
+    Us[k + 2][c] = v.z;
+    Us[k + 3][c] = v.w;
+  }
+  if (xmode == X32_COLS) {
+    // thread t: tile rows 4 (t mod 32) .. +3 (consecutive rows of one block),
+    // contraction indices k = t / 32 + 4 i
+    const int rq = tid & 31, a = a0 + (rq >> 3);
+    int row = -1;
+    if (a < npairs) {
+      int I, J;
+      block_pair(nb, R, a, I, J);
+      row = gidx(I, J, (4 * rq) & 31);
+    }
+#pragma unroll
+    for (int i = 0; i < W2 / 4; ++i) {
+      const int k = (tid >> 5) + 4 * i;
+      const float4 v = row >= 0 ? *reinterpret_cast<const float4*>(X + (size_t)gidx(IQ, JQ, k) * N + row)
+                                : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+      *reinterpret_cast<float4*>(&Xs[k][4 * rq]) = v;
+    }
+  } else {
+    // X tile: thread t loads tile row t (pair a0 + t / 32, index t mod 32)
+    const int r = tid, a = a0 + (r >> 5);
+    if (a < npairs) {
+      int I, J;
+      block_pair(nb, R, a, I, J);
+      const int row = gidx(I, J, r & 31);
+      {
+#pragma unroll
+        for (int kh = 0; kh < 2; ++kh) {
+          const float4* src = reinterpret_cast<const float4*>(X + (size_t)row * N + (kh ? JQ : IQ) * BS);
+#pragma unroll
+          for (int q = 0; q < BS / 4; ++q) {
+            const float4 v = src[q];
+            Xs[kh * BS + 4 * q + 0][r] = v.x;
+            Xs[kh * BS + 4 * q + 1][r] = v.y;
+            Xs[kh * BS + 4 * q + 2][r] = v.z;
+            Xs[kh * BS + 4 * q + 3][r] = v.w;
+          }
+        }
       }
-      return;
+    } else {
+#pragma unroll
+      for (int k = 0; k < W2; ++k) Xs[k][r] = 0.0f;
     }
-    const float* Up = Ubuf + (size_t)P * W2 * W2;  // column-major 32 x 32: Up[li + 32 lj] = U_P(li, lj)
-    const float* Uq = Ubuf + (size_t)Q * W2 * W2;
-    #pragma unroll
-    for (int it = 0; it < W2 * W2 / UT; ++it) {
-      const int e = tid + it * UT;
-      int li = e % W2, lj = e / W2;
-      T[li][lj] = A32[(size_t)gidx(IQ, JQ, lj) * N + gidx(IP, JP, li)];
-      UP[li][lj] = Up[e];
-      UQ[li][lj] = Uq[e];
-    }
-    __syncthreads();
-    // X = U_P^T T: X[i][j] = sum_l U_P[l][i] T[l][j]
-    tile_mm(UP, T, acc, i4, j4);
-    __syncthreads();  // every thread is done reading T
+  }
+  __syncthreads();
+  const int r0 = 4 * (tid & 31), c0 = 8 * (tid >> 5);
+  const int a = a0 + (r0 >> 5);  // the pair of this thread's four rows
+  if (a >= npairs) return;
+  if (tri == R32_FIRST && a >= Q) return;
+  if (tri == R32_SECOND && a < Q) return;
+  int I, J;
+  block_pair(nb, R, a, I, J);
+  const int row0 = gidx(I, J, r0 & 31);  // rows row0 .. row0 + 3 (one block)
+  const int col0 = gidx(IQ, JQ, c0);     // columns col0 .. col0 + 7 (one block)
+  if (tri == R32_SECOND && a == Q) {
+    // the diagonal tile: the solved subproblem
+    const float* Sq = Sbuf + (size_t)Q * W2 * W2;
 #pragma unroll
-    for (int a = 0; a < 4; ++a)
-#pragma unroll
-      for (int b = 0; b < 4; ++b) T[j4 + b][i4 + a] = acc[a][b];  // T now holds X^T
-    __syncthreads();
-    // Y = X U_Q: Y[i][j] = sum_l X^T[l][i] U_Q[l][j]
-    tile_mm(T, UQ, acc, i4, j4);
-    __syncthreads();
-#pragma unroll
-    for (int a = 0; a < 4; ++a)
-#pragma unroll
-      for (int b = 0; b < 4; ++b) T[i4 + a][j4 + b] = qh(acc[a][b], hq);
-    __syncthreads();
-    #pragma unroll
-    for (int it = 0; it < W2 * W2 / UT; ++it) {
-      const int e = tid + it * UT;
-      int li = e % W2, lj = e / W2;
-      A32[(size_t)gidx(IQ, JQ, lj) * N + gidx(IP, JP, li)] = T[li][lj];
-      // mirror: entry (cols(Q)[li], rows(P)[lj]) = T[lj][li]
-      A32[(size_t)gidx(IP, JP, lj) * N + gidx(IQ, JQ, li)] = T[lj][li];
+    for (int cc = 0; cc < 8; ++cc) {
+      const float4 o = *reinterpret_cast<const float4*>(Sq + (r0 & 31) + W2 * (c0 + cc));
+      *reinterpret_cast<float4*>(Y + (size_t)(col0 + cc) * N + row0) = o;
     }
     return;
   }
-  // V tile: rows [rc*32, rc*32+32), column set of pair Q:  Y = T U_Q
-  int v = item - n_atiles;
-  int nrc = N / W2;
-  int rc = v % nrc, Q = v / nrc;
-  int IQ, JQ;
-  block_pair(nb, R, Q, IQ, JQ);
-  const float* Uq = Ubuf + (size_t)Q * W2 * W2;
-  #pragma unroll
-  for (int it = 0; it < W2 * W2 / UT; ++it) {
-    const int e = tid + it * UT;
-    int li = e % W2, lj = e / W2;
-    UP[lj][li] = V32[(size_t)gidx(IQ, JQ, lj) * N + rc * W2 + li];  // UP holds the chunk transposed
-    UQ[li][lj] = Uq[e];
+  float acc[4][8];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 8; ++j) acc[i][j] = 0.0f;
+#pragma unroll 4
+  for (int k = 0; k < W2; ++k) {
+    const float4 x = *reinterpret_cast<const float4*>(&Xs[k][r0]);
+    const float4 u0 = *reinterpret_cast<const float4*>(&Us[k][c0]);
+    const float4 u1 = *reinterpret_cast<const float4*>(&Us[k][c0 + 4]);
+    const float xa[4] = {x.x, x.y, x.z, x.w};
+    const float ub[8] = {u0.x, u0.y, u0.z, u0.w, u1.x, u1.y, u1.z, u1.w};
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(xa[i], ub[j], acc[i][j]);
   }
-  __syncthreads();
-  tile_mm(UP, UQ, acc, i4, j4);
+  const bool rq = hq && tri != R32_FIRST;
 #pragma unroll
-  for (int a = 0; a < 4; ++a)
+  for (int i = 0; i < 4; ++i)
 #pragma unroll
-    for (int b = 0; b < 4; ++b) T[i4 + a][j4 + b] = qh(acc[a][b], hq);
-  __syncthreads();
-  #pragma unroll
-  for (int it = 0; it < W2 * W2 / UT; ++it) {
-    const int e = tid + it * UT;
-    int li = e % W2, lj = e / W2;
-    V32[(size_t)gidx(IQ, JQ, lj) * N + rc * W2 + li] = T[li][lj];
+    for (int j = 0; j < 8; ++j) acc[i][j] = qh(acc[i][j], rq);
+#pragma unroll
+  for (int j = 0; j < 8; ++j)
+    *reinterpret_cast<float4*>(Y + (size_t)(col0 + j) * N + row0) =
+        make_float4(acc[0][j], acc[1][j], acc[2][j], acc[3][j]);
+  if (tri == R32_SECOND) {  // the mirror: rows col0 .. +7 of columns row0 .. +3
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      *reinterpret_cast<float4*>(Y + (size_t)(row0 + i) * N + col0) =
+          make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
+      *reinterpret_cast<float4*>(Y + (size_t)(row0 + i) * N + col0 + 4) =
+          make_float4(acc[i][4], acc[i][5], acc[i][6], acc[i][7]);
+    }
   }
 }
 
@@ -306,7 +319,7 @@ static int stage1_tensor_cores();
 size_t mpj_stage1_bytes(int n) {
   size_t N = (size_t)mpj_stage1_padded(n);
   size_t nb = N / BS;
-  return (stage1_tensor_cores() ? 3 : 2) * N * N * sizeof(float) + 2 * (nb / 2) * W2 * W2 * sizeof(float) + 4096;
+  return 3 * N * N * sizeof(float) + 2 * (nb / 2) * W2 * W2 * sizeof(float) + 4096;
 }
 
 // MPJ_STAGE1_TC=1 runs the A update of each block round on the tcgen05
@@ -335,7 +348,7 @@ int mpj_stage1_run(int n, const double* A, int lda, double* Ql, int ldq, double 
   float* Sbuf = V32 + (size_t)N * N;
   float* Ubuf = Sbuf + (size_t)(nb / 2) * W2 * W2;
   float* Bt = Ubuf + (size_t)(nb / 2) * W2 * W2;
-  unsigned* tflag = (unsigned*)(Bt + (stage1_tensor_cores() ? (size_t)N * N : 0));
+  unsigned* tflag = (unsigned*)(Bt + (size_t)N * N);
   MPJ_CUDA_TRY(cudaMemsetAsync(tflag, 0, sizeof(unsigned), s));
   const int tc = stage1_tensor_cores() && !half;
   init32<<<1024, 256, 0, s>>>(A, lda, n, N, A32, V32, half);
@@ -348,8 +361,6 @@ int mpj_stage1_run(int n, const double* A, int lda, double* Ql, int ldq, double 
   double off = sqrt(off2);
   int sweeps = 0, status = MPJ_OK;
   const int npairs = nb / 2;
-  const int n_atiles = npairs * (npairs + 1) / 2;
-  const int grid_u = n_atiles + (N / W2) * npairs;
   while (off > tol32) {
     if (sweeps >= max_sweeps) {
       status = MPJ_NOT_CONVERGED;
@@ -363,10 +374,17 @@ int mpj_stage1_run(int n, const double* A, int lda, double* Ql, int ldq, double 
         // A' = (B^T)(:, I_q) U_q on the tensor cores; V U on the FP32 pipe
         MPJ_CUDA_TRY(mpj_tc_panel(N, nb, R, Ubuf, A32, Bt, 1, nullptr, nullptr, tflag, s));
         MPJ_CUDA_TRY(mpj_tc_panel(N, nb, R, Ubuf, Bt, A32, 0, nullptr, nullptr, tflag, s));
-        update32<<<(N / W2) * npairs, UT, 0, s>>>(A32, V32, N, nb, R, Sbuf, Ubuf, 0, false);
+        rmul32<<<dim3((npairs + 3) / 4, npairs), RT, 0, s>>>(V32, X32_COLS, V32, N, nb, R, Sbuf, Ubuf, R32_ALL,
+                                                              false);
         mpj_count_launch();
       } else {
-        update32<<<grid_u, UT, 0, s>>>(A32, V32, N, nb, R, Sbuf, Ubuf, n_atiles, half);
+        // V <- V U~, B = A U~ (tiles a < Q), A = B^T U~ (tiles a > Q, mirrored; S on the diagonal)
+        const dim3 g32((npairs + 3) / 4, npairs);
+        rmul32<<<g32, RT, 0, s>>>(V32, X32_COLS, V32, N, nb, R, Sbuf, Ubuf, R32_ALL, half);
+        mpj_count_launch();
+        rmul32<<<g32, RT, 0, s>>>(A32, X32_COLS, Bt, N, nb, R, Sbuf, Ubuf, R32_FIRST, half);
+        mpj_count_launch();
+        rmul32<<<g32, RT, 0, s>>>(Bt, X32_ROWS, A32, N, nb, R, Sbuf, Ubuf, R32_SECOND, half);
         mpj_count_launch();
       }
     }

@@ -50,7 +50,7 @@ _dp = ctypes.POINTER(ctypes.c_double)
 class Opts(ctypes.Structure):
     _fields_ = [("tol", _d), ("tol32", _d), ("max_sweeps64", _i), ("max_sweeps32", _i), ("ns_steps", _i),
                 ("ordering", _i), ("method", _i), ("polish", _i), ("sort", _i), ("check_symmetry", _i),
-                ("threshold", _i), ("precond_passes", _i), ("stage1_half", _i)]
+                ("threshold", _i), ("precond_passes", _i), ("stage1_half", _i), ("max_sweeps32_pass2", _i)]
 
 
 class Info(ctypes.Structure):
