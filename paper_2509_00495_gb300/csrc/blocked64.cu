@@ -200,6 +200,7 @@ __global__ void __launch_bounds__(SOLVE_THREADS) blk_solve(const double* __restr
   int I, J;
   block_pair(nb, R, P, I, J);
   if (tid == 0) any = 0;
+  pdl_wait();
   for (int e = tid; e < W2 * W2; e += blockDim.x) {
     const int li = e % W2, lj = e / W2;
     const int gi = gidx(I, J, li), gj = gidx(I, J, lj);
@@ -536,19 +537,22 @@ __global__ void __launch_bounds__(RM_THREADS, 2)
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int Q = blockIdx.y, gx = blockIdx.x;
   const int a0 = 4 * gx, a1 = min(4 * gx + 3, nb / 2 - 1);
+  pdl_wait();
   if (tri == TRI_FIRST && a0 > Q) return;
   if (tri == TRI_SECOND && a1 < Q) return;
   int I, J;
   block_pair(nb, R, Q, I, J);
   if (!rotated[Q]) {
     // no rotation in this block pair: U_Q = I exactly, Y_Q = X_Q (nothing to
-    // do in place)
+    // do in place).  For A, a tile between two block pairs without rotations
+    // keeps its values: the second step leaves it alone, so the first need not
+    // copy it to B.
     if (X == Y && xmode == XMODE_COLS) return;
     const int rl = tid >> 1, half = tid & 1;
     const int a = a0 + (rl >> 5);
     const int row = tile_row(nb, R, gx, rl);
     const int g0 = (half ? J : I) * BS;
-    if (row >= 0 && row < n && tile_needed(tri, a, Q)) {
+    if (row >= 0 && row < n && tile_needed(tri, a, Q) && (tri == TRI_ALL || rotated[a])) {
       double x[BS];
       load_xrow(X, ldx, xmode, n, row, g0, x);
 #pragma unroll
@@ -759,9 +763,8 @@ cudaError_t mpj_blocked_solve(const double* A, int lda, int n, int R, double ski
   const int N = (n + 2 * BS - 1) / (2 * BS) * (2 * BS);
   const int nb = N / BS;
   const USet u = uset(scratch, n, R & 1);
-  blk_solve<<<nb / 2, SOLVE_THREADS, 0, s>>>(A, lda, n, nb, R, skip, skip_abs, u.sl, u.ex, u.rot, nrot);
-  mpj_count_launch();
-  return cudaGetLastError();
+  return mpj_launch_pdl(blk_solve, dim3(nb / 2), dim3(SOLVE_THREADS), 0, s, A, lda, n, nb, R, skip, skip_abs, u.sl,
+                        u.ex, u.rot, nrot);
 }
 
 // Round R, step 2: A <- U~^T A U~ through B (two right multiplications).
@@ -773,13 +776,12 @@ cudaError_t mpj_blocked_update_A(double* A, int lda, double* B, int n, int R, vo
   cudaError_t e = rmul_attr();
   if (e != cudaSuccess) return e;
   const dim3 grid((nb / 2 + 3) / 4, nb / 2);
-  blk_rmul<<<grid, RM_THREADS, rmul_smem(), s>>>(A, lda, XMODE_COLS, B, n, n, nb, R, u.sl, u.ex, u.rot, flags,
-                                                  TRI_FIRST);
-  mpj_count_launch();
-  blk_rmul<<<grid, RM_THREADS, rmul_smem(), s>>>(B, n, XMODE_ROWS, A, lda, n, nb, R, u.sl, u.ex, u.rot, flags,
-                                                  TRI_SECOND);
-  mpj_count_launch();
-  return cudaGetLastError();
+  e = mpj_launch_pdl(blk_rmul, grid, dim3(RM_THREADS), rmul_smem(), s, (const double*)A, lda, (int)XMODE_COLS, B, n,
+                     n, nb, R, (const __nv_bfloat16*)u.sl, (const int*)u.ex, (const int*)u.rot, flags, (int)TRI_FIRST);
+  if (e != cudaSuccess) return e;
+  return mpj_launch_pdl(blk_rmul, grid, dim3(RM_THREADS), rmul_smem(), s, (const double*)B, n, (int)XMODE_ROWS, A,
+                        lda, n, nb, R, (const __nv_bfloat16*)u.sl, (const int*)u.ex, (const int*)u.rot, flags,
+                        (int)TRI_SECOND);
 }
 
 // Round R, step 3: V <- V U~ (in place); independent of step 2.
@@ -790,10 +792,9 @@ cudaError_t mpj_blocked_update_V(double* V, int ldv, int n, int R, void* scratch
   cudaError_t e = rmul_attr();
   if (e != cudaSuccess) return e;
   const dim3 grid((nb / 2 + 3) / 4, nb / 2);
-  blk_rmul<<<grid, RM_THREADS, rmul_smem(), s>>>(V, ldv, XMODE_COLS, V, ldv, n, nb, R, u.sl, u.ex, u.rot, flags,
-                                                  TRI_ALL);
-  mpj_count_launch();
-  return cudaGetLastError();
+  return mpj_launch_pdl(blk_rmul, grid, dim3(RM_THREADS), rmul_smem(), s, (const double*)V, ldv, (int)XMODE_COLS, V,
+                        ldv, n, nb, R, (const __nv_bfloat16*)u.sl, (const int*)u.ex, (const int*)u.rot, flags,
+                        (int)TRI_ALL);
 }
 
 int mpj_blocked_rounds_per_sweep(int n) {

@@ -177,6 +177,34 @@ MPJ_DEV float ld_cg(const float* p) { return __ldcg(p); }
 void mpj_set_cuda_error(cudaError_t e, const char* what, int line);
 // Counts every kernel this library enqueues (diagnostic, mpj_kernel_launches).
 void mpj_count_launch();
+
+// Programmatic dependent launch.  A kernel launched by mpj_launch_pdl may have
+// its CTAs scheduled while the previous kernel in the stream drains (once all
+// of that kernel's CTAs have started); it calls pdl_wait() before touching
+// global memory, which returns when the previous kernel has completed and its
+// writes are visible.  pdl_wait() also lets the next such kernel start early.
+MPJ_DEV void pdl_wait() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+
+template <typename... KArgs, typename... Args>
+cudaError_t mpj_launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                           Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  const cudaError_t e = cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+  mpj_count_launch();
+  return e;
+}
 // Counts every device (or pinned host) allocation the library makes
 // (diagnostic, mpj_device_allocations).
 void mpj_count_alloc();

@@ -77,6 +77,7 @@ __global__ void __launch_bounds__(256) solve32(const float* __restrict__ A32, in
   int I, J;
   block_pair(nb, R, slot, I, J);
   const int tid = threadIdx.x;
+  pdl_wait();
   #pragma unroll
   for (int it = 0; it < W2 * W2 / 256; ++it) {
     const int e = tid + it * 256;
@@ -195,6 +196,7 @@ __global__ void __launch_bounds__(RT) rmul32(const float* X, int xmode, float* Y
   const int tid = threadIdx.x;
   const int Q = blockIdx.y, gx = blockIdx.x, npairs = nb / 2;
   const int a0 = 4 * gx, a1 = min(4 * gx + 3, npairs - 1);
+  pdl_wait();
   if ((tri == R32_FIRST && a0 >= Q) || (tri == R32_SECOND && a1 < Q)) return;
   int IQ, JQ;
   block_pair(nb, R, Q, IQ, JQ);
@@ -367,8 +369,7 @@ int mpj_stage1_run(int n, const double* A, int lda, double* Ql, int ldq, double 
       break;
     }
     for (int R = 0; R < nb - 1; ++R) {
-      solve32<<<npairs, 256, 0, s>>>(A32, N, nb, R, Sbuf, Ubuf, half);
-      mpj_count_launch();
+      MPJ_CUDA_TRY(mpj_launch_pdl(solve32, dim3(npairs), dim3(256), 0, s, A32, N, nb, R, Sbuf, Ubuf, half));
       if (tc == 1) {
         // A' = U^T A U = (A U)^T U (A symmetric): B^T = (A U)^T, then
         // A' = (B^T)(:, I_q) U_q on the tensor cores; V U on the FP32 pipe
@@ -380,12 +381,12 @@ int mpj_stage1_run(int n, const double* A, int lda, double* Ql, int ldq, double 
       } else {
         // V <- V U~, B = A U~ (tiles a < Q), A = B^T U~ (tiles a > Q, mirrored; S on the diagonal)
         const dim3 g32((npairs + 3) / 4, npairs);
-        rmul32<<<g32, RT, 0, s>>>(V32, X32_COLS, V32, N, nb, R, Sbuf, Ubuf, R32_ALL, half);
-        mpj_count_launch();
-        rmul32<<<g32, RT, 0, s>>>(A32, X32_COLS, Bt, N, nb, R, Sbuf, Ubuf, R32_FIRST, half);
-        mpj_count_launch();
-        rmul32<<<g32, RT, 0, s>>>(Bt, X32_ROWS, A32, N, nb, R, Sbuf, Ubuf, R32_SECOND, half);
-        mpj_count_launch();
+        MPJ_CUDA_TRY(mpj_launch_pdl(rmul32, g32, dim3(RT), 0, s, (const float*)V32, (int)X32_COLS, V32, N, nb, R,
+                                    (const float*)Sbuf, (const float*)Ubuf, (int)R32_ALL, half));
+        MPJ_CUDA_TRY(mpj_launch_pdl(rmul32, g32, dim3(RT), 0, s, (const float*)A32, (int)X32_COLS, Bt, N, nb, R,
+                                    (const float*)Sbuf, (const float*)Ubuf, (int)R32_FIRST, half));
+        MPJ_CUDA_TRY(mpj_launch_pdl(rmul32, g32, dim3(RT), 0, s, (const float*)Bt, (int)X32_ROWS, A32, N, nb, R,
+                                    (const float*)Sbuf, (const float*)Ubuf, (int)R32_SECOND, half));
       }
     }
     MPJ_CUDA_TRY(cudaGetLastError());
