@@ -68,9 +68,9 @@ def hbm_peak_gbs() -> tuple[float, str]:
         return 6800.0, "fallback 6.8 TB/s"
 
 
-def oracle_record(which: str) -> dict | None:
-    """The oracle's full run on the n = 4096 input (oracle/record_geo4096.py)."""
-    path = os.path.join(ROOT, "oracle", f"geo4096_{which}.json")
+def oracle_record(which: str, workload: str = "geo4096") -> dict | None:
+    """The oracle's full run on a recorded workload (oracle/record_geo4096.py)."""
+    path = os.path.join(ROOT, "oracle", f"{workload}_{which}.json")
     try:
         with open(path) as f:
             return json.load(f)
@@ -230,10 +230,26 @@ def oracle_full_runs() -> dict:
     t96 = (time.perf_counter() - t0) / reps
     out = {"n96_mixed": {"seconds_per_solve": t96, "solves_per_s": 1.0 / t96, "sweeps32": info.sweeps32,
                          "sweeps64": info.sweeps64, "cores": 1}}
+    # the differentiation workload (64 x n = 512): the oracle's adjoint on two
+    # of its matrices (eigenvectors from LAPACK as inputs), scaled to 64
+    mats, lams, dWs, dQs = inputs.backward_batch(count=2)
+    tb = 0.0
+    for Ab, dWb, dQb in zip(mats, dWs, dQs):
+        w, q = np.linalg.eigh(Ab)
+        t0 = time.perf_counter()
+        oracle.eigh_backward(w, np.asfortranarray(q), dWb, dQb)
+        tb += time.perf_counter() - t0
+    out["backward_64x512"] = {"seconds": tb * 32, "batches_per_s": 1.0 / (tb * 32), "cores": 1,
+                              "sample": "the oracle adjoint on 2 of the 64 matrices, scaled to 64"}
     for which in ("mixed", "plain"):
         rec = oracle_record(which)
         if rec is not None:
             out[f"n4096_{which}_recorded"] = {k: rec[k] for k in ("sweeps32", "sweeps64", "wall_seconds", "machine")
+                                              if k in rec}
+    for which in ("mixed", "plain"):
+        rec = oracle_record(which, "clustered1024")
+        if rec is not None:
+            out[f"n1024_{which}_recorded"] = {k: rec[k] for k in ("sweeps32", "sweeps64", "wall_seconds", "machine")
                                               if k in rec}
     return out
 

@@ -2,7 +2,9 @@
 record what it did (test infrastructure: calls only ``oracle`` and the seeded
 input generators).
 
-    python oracle/record_geo4096.py mixed|plain [out.json]
+    python oracle/record_geo4096.py mixed|plain [out.json] [clustered1024]
+
+(the optional third argument records the n = 1024 clustered case instead)
 
 The mixed run is Algorithm 9 as the oracle implements it (FP32 cyclic-by-row
 Jacobi, two Newton-Schulz steps, Q_d^T A Q_d, FP64 cyclic-by-row Jacobi, Q_d V);
@@ -34,8 +36,14 @@ from paper_2509_00495_gb300 import inputs  # noqa: E402
 
 def main() -> None:
     which = sys.argv[1]
-    out = sys.argv[2] if len(sys.argv) > 2 else os.path.join(HERE, f"geo4096_{which}.json")
-    A, lam = inputs.geo_4096(seed=0)
+    workload = sys.argv[3] if len(sys.argv) > 3 else "geo4096"
+    out = sys.argv[2] if len(sys.argv) > 2 else os.path.join(HERE, f"{workload}_{which}.json")
+    if workload == "clustered1024":
+        A, lam = inputs.clustered_1024(seed=0)
+        desc = "clustered1024 (n=1024, 992 eigenvalues linear in [-1,1] + 32 within 1e-8 of 0.5, seed 0)"
+    else:
+        A, lam = inputs.geo_4096(seed=0)
+        desc = "geo4096 (n=4096, |lam| geometric in [1e-6,1], random signs, Haar eigenvectors, seed 0)"
     n = A.shape[0]
     t0 = time.perf_counter()
     if which == "mixed":
@@ -49,7 +57,7 @@ def main() -> None:
     be = np.linalg.norm(A - (Q * W) @ Q.T) / np.linalg.norm(A)
     orth = np.linalg.norm(Q.T @ Q - np.eye(n))
     rec = {
-        "workload": "geo4096 (n=4096, |lam| geometric in [1e-6,1], random signs, Haar eigenvectors, seed 0)",
+        "workload": desc,
         "method": which, "orderings": "cyclic-by-row (FP32 and FP64)", "tol": "n 2^-53 ||A||_F",
         "sweeps32": info.sweeps32, "sweeps64": info.sweeps64, "rotations32": info.rotations32,
         "rotations64": info.rotations64, "capped64": info.capped64, "off_cond": info.off_cond,
