@@ -168,6 +168,20 @@ __global__ void __launch_bounds__(256) solve32(const float* __restrict__ A32, in
 }
 
 
+// Packed pairs of FP32 values (low word first) and the paired FMA
+// d = a * b + d, each half rounded to nearest like fmaf.
+MPJ_DEV unsigned long long pk2(float lo, float hi) {
+  unsigned long long r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+  return r;
+}
+MPJ_DEV void unpk2(unsigned long long v, float& lo, float& hi) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+MPJ_DEV void fma2(unsigned long long& d, unsigned long long a, unsigned long long b) {
+  asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(d) : "l"(a), "l"(b));
+}
+
 // ---------------------------------------------------------------- block update
 // The round's rotations applied to the rest of A32 and to V32 as three
 // block-diagonal right multiplications Y[:, g_Q(c)] = X_Q U_Q (FP32 FMA, K = 32):
@@ -273,23 +287,32 @@ __global__ void __launch_bounds__(RT) rmul32(const float* X, int xmode, float* Y
     }
     return;
   }
-  float acc[4][8];
+  // packed FP32 pairs: one fma.rn.f32x2 forms two of the thread's FMAs
+  // (columns 2jp, 2jp + 1 of row i), each rounded as fmaf would
+  unsigned long long acc2[4][4];
 #pragma unroll
   for (int i = 0; i < 4; ++i)
 #pragma unroll
-    for (int j = 0; j < 8; ++j) acc[i][j] = 0.0f;
+    for (int jp = 0; jp < 4; ++jp) acc2[i][jp] = 0ULL;
 #pragma unroll 4
   for (int k = 0; k < W2; ++k) {
     const float4 x = *reinterpret_cast<const float4*>(&Xs[k][r0]);
     const float4 u0 = *reinterpret_cast<const float4*>(&Us[k][c0]);
     const float4 u1 = *reinterpret_cast<const float4*>(&Us[k][c0 + 4]);
     const float xa[4] = {x.x, x.y, x.z, x.w};
-    const float ub[8] = {u0.x, u0.y, u0.z, u0.w, u1.x, u1.y, u1.z, u1.w};
+    const unsigned long long up[4] = {pk2(u0.x, u0.y), pk2(u0.z, u0.w), pk2(u1.x, u1.y), pk2(u1.z, u1.w)};
 #pragma unroll
-    for (int i = 0; i < 4; ++i)
+    for (int i = 0; i < 4; ++i) {
+      const unsigned long long xx = pk2(xa[i], xa[i]);
 #pragma unroll
-      for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(xa[i], ub[j], acc[i][j]);
+      for (int jp = 0; jp < 4; ++jp) fma2(acc2[i][jp], xx, up[jp]);
+    }
   }
+  float acc[4][8];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int jp = 0; jp < 4; ++jp) unpk2(acc2[i][jp], acc[i][2 * jp], acc[i][2 * jp + 1]);
   const bool rq = hq && tri != R32_FIRST;
 #pragma unroll
   for (int i = 0; i < 4; ++i)
