@@ -185,9 +185,9 @@ MPJ_DEV void fma2(unsigned long long& d, unsigned long long a, unsigned long lon
 // ---------------------------------------------------------------- block update
 // The round's rotations applied to the rest of A32 and to V32 as three
 // block-diagonal right multiplications Y[:, g_Q(c)] = X_Q U_Q (FP32 FMA, K = 32):
-//   V <- V U~ (every tile),  B = A U~ (tiles a < Q),  A = B^T U~ (tiles a > Q,
-//   written to both triangles; the diagonal tiles a = Q are the solved
-//   subproblems S),
+//   V <- V U~ (every tile),  B = A U~ (tiles a < Q, B stored transposed),
+//   A = B^T U~ (tiles a > Q, read as columns of the stored B^T, written to
+//   both triangles; the diagonal tiles a = Q are the solved subproblems S),
 // over tiles (a, Q): block pair Q and the 128 rows that are the 32 indices of
 // each of the block pairs a = 4 gx .. 4 gx + 3.  In exact arithmetic this is
 // A <- U~^T A U~ (the second step reads B only in tiles (Q, a), Q < a, the
@@ -197,12 +197,11 @@ MPJ_DEV void fma2(unsigned long long& d, unsigned long long a, unsigned long lon
 // shared-memory wavefronts per warp) and two broadcast float4 of U_Q feed 32
 // FMAs, so the FP32 pipe, not shared memory, sets the pace.
 enum { R32_ALL = 0, R32_FIRST = 1, R32_SECOND = 2 };
-enum { X32_COLS = 0, X32_ROWS = 1 };
 constexpr int RT = 128;
 constexpr int XLD = 132;  // padded row length of the X tile (k-major), 16-byte aligned rows
 constexpr int ULD = 40;   // padded row length of U_Q, 16-byte aligned rows
 
-__global__ void __launch_bounds__(RT) rmul32(const float* X, int xmode, float* Y, int N, int nb, int R,
+__global__ void __launch_bounds__(RT) rmul32(const float* X, float* Y, int N, int nb, int R,
                                              const float* __restrict__ Sbuf, const float* __restrict__ Ubuf, int tri,
                                              bool hq) {
   __shared__ __align__(16) float Xs[W2][XLD];  // Xs[k][r] = X_Q(r, k)
@@ -224,9 +223,9 @@ __global__ void __launch_bounds__(RT) rmul32(const float* X, int xmode, float* Y
     Us[k + 2][c] = v.z;
     Us[k + 3][c] = v.w;
   }
-  if (xmode == X32_COLS) {
-    // thread t: tile rows 4 (t mod 32) .. +3 (consecutive rows of one block),
-    // contraction indices k = t / 32 + 4 i
+  {
+    // X_Q(r, k) = X[g_Q(k) N + row(r)]; thread t: tile rows 4 (t mod 32) .. +3
+    // (consecutive rows of one block), contraction indices k = t / 32 + 4 i
     const int rq = tid & 31, a = a0 + (rq >> 3);
     int row = -1;
     if (a < npairs) {
@@ -240,31 +239,6 @@ __global__ void __launch_bounds__(RT) rmul32(const float* X, int xmode, float* Y
       const float4 v = row >= 0 ? *reinterpret_cast<const float4*>(X + (size_t)gidx(IQ, JQ, k) * N + row)
                                 : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
       *reinterpret_cast<float4*>(&Xs[k][4 * rq]) = v;
-    }
-  } else {
-    // X tile: thread t loads tile row t (pair a0 + t / 32, index t mod 32)
-    const int r = tid, a = a0 + (r >> 5);
-    if (a < npairs) {
-      int I, J;
-      block_pair(nb, R, a, I, J);
-      const int row = gidx(I, J, r & 31);
-      {
-#pragma unroll
-        for (int kh = 0; kh < 2; ++kh) {
-          const float4* src = reinterpret_cast<const float4*>(X + (size_t)row * N + (kh ? JQ : IQ) * BS);
-#pragma unroll
-          for (int q = 0; q < BS / 4; ++q) {
-            const float4 v = src[q];
-            Xs[kh * BS + 4 * q + 0][r] = v.x;
-            Xs[kh * BS + 4 * q + 1][r] = v.y;
-            Xs[kh * BS + 4 * q + 2][r] = v.z;
-            Xs[kh * BS + 4 * q + 3][r] = v.w;
-          }
-        }
-      }
-    } else {
-#pragma unroll
-      for (int k = 0; k < W2; ++k) Xs[k][r] = 0.0f;
     }
   }
   __syncthreads();
@@ -318,6 +292,18 @@ __global__ void __launch_bounds__(RT) rmul32(const float* X, int xmode, float* Y
   for (int i = 0; i < 4; ++i)
 #pragma unroll
     for (int j = 0; j < 8; ++j) acc[i][j] = qh(acc[i][j], rq);
+  if (tri == R32_FIRST) {
+    // B is stored transposed (B(r, c) at Y[r N + c]), so that the second
+    // product reads its rows of B^T as contiguous columns
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      *reinterpret_cast<float4*>(Y + (size_t)(row0 + i) * N + col0) =
+          make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
+      *reinterpret_cast<float4*>(Y + (size_t)(row0 + i) * N + col0 + 4) =
+          make_float4(acc[i][4], acc[i][5], acc[i][6], acc[i][7]);
+    }
+    return;
+  }
 #pragma unroll
   for (int j = 0; j < 8; ++j)
     *reinterpret_cast<float4*>(Y + (size_t)(col0 + j) * N + row0) =
@@ -398,17 +384,18 @@ int mpj_stage1_run(int n, const double* A, int lda, double* Ql, int ldq, double 
         // A' = (B^T)(:, I_q) U_q on the tensor cores; V U on the FP32 pipe
         MPJ_CUDA_TRY(mpj_tc_panel(N, nb, R, Ubuf, A32, Bt, 1, nullptr, nullptr, tflag, s));
         MPJ_CUDA_TRY(mpj_tc_panel(N, nb, R, Ubuf, Bt, A32, 0, nullptr, nullptr, tflag, s));
-        rmul32<<<dim3((npairs + 3) / 4, npairs), RT, 0, s>>>(V32, X32_COLS, V32, N, nb, R, Sbuf, Ubuf, R32_ALL,
+        rmul32<<<dim3((npairs + 3) / 4, npairs), RT, 0, s>>>(V32, V32, N, nb, R, Sbuf, Ubuf, R32_ALL,
                                                               false);
         mpj_count_launch();
       } else {
-        // V <- V U~, B = A U~ (tiles a < Q), A = B^T U~ (tiles a > Q, mirrored; S on the diagonal)
+        // V <- V U~, B = A U~ (tiles a < Q, stored transposed), A = B^T U~ (tiles a > Q, mirrored; S on
+        // the diagonal)
         const dim3 g32((npairs + 3) / 4, npairs);
-        MPJ_CUDA_TRY(mpj_launch_pdl(rmul32, g32, dim3(RT), 0, s, (const float*)V32, (int)X32_COLS, V32, N, nb, R,
+        MPJ_CUDA_TRY(mpj_launch_pdl(rmul32, g32, dim3(RT), 0, s, (const float*)V32, V32, N, nb, R,
                                     (const float*)Sbuf, (const float*)Ubuf, (int)R32_ALL, half));
-        MPJ_CUDA_TRY(mpj_launch_pdl(rmul32, g32, dim3(RT), 0, s, (const float*)A32, (int)X32_COLS, Bt, N, nb, R,
+        MPJ_CUDA_TRY(mpj_launch_pdl(rmul32, g32, dim3(RT), 0, s, (const float*)A32, Bt, N, nb, R,
                                     (const float*)Sbuf, (const float*)Ubuf, (int)R32_FIRST, half));
-        MPJ_CUDA_TRY(mpj_launch_pdl(rmul32, g32, dim3(RT), 0, s, (const float*)Bt, (int)X32_ROWS, A32, N, nb, R,
+        MPJ_CUDA_TRY(mpj_launch_pdl(rmul32, g32, dim3(RT), 0, s, (const float*)Bt, A32, N, nb, R,
                                     (const float*)Sbuf, (const float*)Ubuf, (int)R32_SECOND, half));
       }
     }
