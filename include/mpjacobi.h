@@ -96,7 +96,7 @@ typedef struct {
                         smallest k with (sqrt(1 + n 2^-11) - 1)^(2^k) <= n 2^-53 steps (the
                         paper's bound of Sec. 4.3.4 with the half unit roundoff)              */
   int max_sweeps32_pass2; /* stage-1 sweep cap of the second preconditioning pass; <= 0 selects
-                        min(10, the stage-1 cap)                                              */
+                        min(9, the stage-1 cap)                                               */
 } mpj_opts;
 
 typedef struct {

@@ -671,13 +671,13 @@ int orc_syev_mixed(int n, const double* A, int lda, double* W, double* Q, int ld
      * FP32 rounding is relative to A_cond's own entries, so the FP32 Jacobi
      * separates eigenvalues that stage 1 on A could not.  Reading: stage 1 of
      * this pass stops at off(A32) <= n 2^-24 off(A_cond) or after
-     * min(max_sweeps32, 10) sweeps; Q_d = Q_d1 Q_d2 and
+     * min(max_sweeps32, 9) sweeps; Q_d = Q_d1 Q_d2 and
      * A_cond <- Q_d2^T A_cond Q_d2.                                          */
     orc_opts d2 = d;
     orc_info i2;
     memset(&i2, 0, sizeof i2);
     d2.tol32 = (double)n * ldexp(1.0, -24) * orc_off_d(n, Ac, n);
-    d2.max_sweeps32 = d.max_sweeps32 < 10 ? d.max_sweeps32 : 10;
+    d2.max_sweeps32 = d.max_sweeps32 < 9 ? d.max_sweeps32 : 9;
     d2.stage1_half = 0; /* the second pass runs in single precision */
     d2.skip_tol32 = ldexp(1.0, -24);
     double* X2 = (double*)malloc(sizeof(double) * (size_t)n * n);

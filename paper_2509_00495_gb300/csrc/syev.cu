@@ -559,9 +559,9 @@ int mpj_syev_ex(int n, const double* A, int lda, double* W, double* Q, int ldq, 
         double* Ql2 = Yp;  // A Q_d (pass 1) is no longer needed
         // the second FP32 pass resolves the groups stage 1 could not separate;
         // each of its sweeps costs about a quarter of an FP64 sweep and saves
-        // about one, up to the point where two FP64 sweeps remain (about ten
-        // sweeps at n = 4096), hence the cap
-        int cap2 = o.max_sweeps32_pass2 > 0 ? o.max_sweeps32_pass2 : (o.max_sweeps32 < 10 ? o.max_sweeps32 : 10);
+        // about one, up to the point where two FP64 sweeps remain (nine sweeps
+        // at n = 4096), hence the cap
+        int cap2 = o.max_sweeps32_pass2 > 0 ? o.max_sweeps32_pass2 : (o.max_sweeps32 < 9 ? o.max_sweeps32 : 9);
         int r1b = mpj_stage1_run(n, M, n, Ql2, n, tol32b, cap2, &sweeps32b, nullptr, S1, sm.partial, sm.dscal, s);
         if (r1b < 0) {
           st = r1b;
