@@ -393,3 +393,34 @@ def test_half_stage1_small_sizes(n):
     assert np.abs(host(r.W) - Wr).max() <= 1e-12 * np.linalg.norm(A, 2)
     if n == 1:
         assert r.info["ns_e0"] == 0.0 and info.ns_e0 == 0.0
+
+
+@pytest.mark.parametrize("n", [257, 1030])
+def test_block_sweeps_with_unrotated_block_pairs_vs_oracle(n):
+    """Most block pairs never rotate (the coupling sits in two index ranges):
+    their V tiles are left alone, their A tiles copied, and A tiles between two
+    of them neither copied nor rewritten.  Against the oracle's block
+    round-robin ordering, and the rotated-pair count is small."""
+    rng = np.random.default_rng(n)
+    d = np.sort(rng.uniform(-1.0, 1.0, n))
+    A = np.diag(d)
+    idx = np.r_[0:20, n // 2:n // 2 + 20]
+    P = rng.standard_normal((idx.size, idx.size)) * 1e-3
+    A[np.ix_(idx, idx)] += P + P.T
+    A = np.asfortranarray(A)
+    tol = n * U * np.linalg.norm(A)
+    a_ref, v_ref, sw_ref, _, _, _ = oracle.jacobi(A, ordering=oracle.BLOCK_ROUND_ROBIN, tol=tol)
+    a, v, sw, off, st = mpj().jacobi64(dev(A), tol=tol, ordering="block")
+    a, v = host(a), host(v)
+    nA = np.linalg.norm(A, 2)
+    assert st == 0 and off <= tol and abs(sw - sw_ref) <= 1
+    assert np.abs(np.diag(a) - np.diag(a_ref)).max() <= 1e-12 * nA
+    assert np.linalg.norm(A @ v - v * np.diag(a)) <= tol + 4 * n * U * nA
+    assert np.linalg.norm(v.T @ v - np.eye(n)) <= 4 * n * U
+    # untouched rows and columns stay exactly as they were
+    rest = np.setdiff1d(np.arange(n), idx)
+    assert np.array_equal(a[np.ix_(rest, rest)], A[np.ix_(rest, rest)])
+    r = mpj().syev_ex(dev(A), ordering="block", method="plain")
+    N = (n + 31) // 32 * 32
+    # four of the N / 16 blocks carry all the coupling: at most 4 of the N / 32 block pairs rotate per round
+    assert 0 < r.info["rotated_blocks64"] <= 4 * r.info["sweeps64"] * (N // 16 - 1)
