@@ -65,27 +65,59 @@ extern "C" int mpj_syev_backward(int batch, int n, const double* W, const double
   if (!W || !Q || !dA) return MPJ_EINVAL;
   size_t sq = (size_t)n * n;
   const bool tc = mpj_gemm_tc_enabled();
+  // tensor-core products: matrices spread over up to BW side streams (one
+  // product of a small matrix does not fill the GPU), three sliced operands each
+  constexpr int BW = 8;
+  const int nw = tc ? (batch < BW ? batch : BW) : 0;
   const size_t ob = tc ? (mpj_oz_operand_bytes(n, n) + 255) / 256 * 256 : 0;
   void* w = nullptr;
-  size_t bytes = 2 * (size_t)batch * sq * sizeof(double) + 256 + 3 * ob;
+  size_t bytes = 2 * (size_t)batch * sq * sizeof(double) + 256 + 3 * ob * (size_t)nw;
   if (cudaMallocAsync(&w, bytes, s) != cudaSuccess) return MPJ_ENOMEM;
   mpj_count_alloc();
   double* M = (double*)w;
   double* T = M + (size_t)batch * sq;
   unsigned* flags = (unsigned*)(T + (size_t)batch * sq);
-  char* obuf = (char*)flags + 256;  // three sliced operands (tensor-core products)
+  char* obuf = (char*)flags + 256;  // three sliced operands per side stream (tensor-core products)
   int st = MPJ_OK;
   unsigned hflags = 0;
   cudaError_t e = cudaMemsetAsync(flags, 0, sizeof(unsigned), s);
+  cudaStream_t ws[BW] = {};
+  cudaEvent_t ev_fork = nullptr, ev_join[BW] = {};
+  if (e == cudaSuccess && tc) {
+    e = cudaEventCreateWithFlags(&ev_fork, cudaEventDisableTiming);
+    for (int i = 0; i < nw && e == cudaSuccess; ++i) {
+      e = cudaStreamCreateWithFlags(&ws[i], cudaStreamNonBlocking);
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev_join[i], cudaEventDisableTiming);
+    }
+  }
+  // side streams start after everything issued so far on s, and s continues
+  // after all of them
+  auto fork = [&]() -> cudaError_t {
+    cudaError_t r = cudaEventRecord(ev_fork, s);
+    for (int i = 0; i < nw && r == cudaSuccess; ++i) r = cudaStreamWaitEvent(ws[i], ev_fork, 0);
+    return r;
+  };
+  auto join = [&]() -> cudaError_t {
+    cudaError_t r = cudaSuccess;
+    for (int i = 0; i < nw && r == cudaSuccess; ++i) {
+      r = cudaEventRecord(ev_join[i], ws[i]);
+      if (r == cudaSuccess) r = cudaStreamWaitEvent(s, ev_join[i], 0);
+    }
+    return r;
+  };
   long long sQ = (long long)ldq * n, sdQ = (long long)lddq * n, sA = (long long)ldda * n, sN = (long long)sq;
   if (e == cudaSuccess && dQ) {  // M = Q^T dQ
     if (tc) {
+      e = fork();
       for (int b = 0; b < batch && e == cudaSuccess; ++b) {
+        cudaStream_t sb = ws[b % nw];
+        char* ob0 = obuf + 3 * ob * (size_t)(b % nw);
         OzOperand oq, od;  // rows of Q^T (columns of Q) and columns of dQ, over the row index
-        e = mpj_oz_prepare(Q + b * sQ, ldq, 1, n, n, obuf, &oq, s);
-        if (e == cudaSuccess) e = mpj_oz_prepare(dQ + b * sdQ, lddq, 1, n, n, obuf + ob, &od, s);
-        if (e == cudaSuccess) e = mpj_oz_gemm(oq, od, n, n, 1.0, 0.0, nullptr, n, M + b * sN, n, flags, s);
+        e = mpj_oz_prepare(Q + b * sQ, ldq, 1, n, n, ob0, &oq, sb);
+        if (e == cudaSuccess) e = mpj_oz_prepare(dQ + b * sdQ, lddq, 1, n, n, ob0 + ob, &od, sb);
+        if (e == cudaSuccess) e = mpj_oz_gemm(oq, od, n, n, 1.0, 0.0, nullptr, n, M + b * sN, n, flags, sb);
       }
+      if (e == cudaSuccess) e = join();
     } else {
       GemmArgs g{n, n, n, 1.0, 0.0, Q, ldq, sQ, dQ, lddq, sdQ, nullptr, n, 0, M, n, sN, 0};
       e = mpj_gemm64_launch(g, true, false, batch, s);
@@ -98,14 +130,18 @@ extern "C" int mpj_syev_backward(int batch, int n, const double* W, const double
     e = cudaGetLastError();
   }
   if (e == cudaSuccess && tc) {
+    e = fork();
     for (int b = 0; b < batch && e == cudaSuccess; ++b) {
+      cudaStream_t sb = ws[b % nw];
+      char* ob0 = obuf + 3 * ob * (size_t)(b % nw);
       OzOperand oq, ot, om;  // rows of Q (left of Q T, right of M Q^T), columns of T, rows of M
-      e = mpj_oz_prepare(Q + b * sQ, 1, ldq, n, n, obuf, &oq, s);
-      if (e == cudaSuccess) e = mpj_oz_prepare(T + b * sN, n, 1, n, n, obuf + ob, &ot, s);
-      if (e == cudaSuccess) e = mpj_oz_gemm(oq, ot, n, n, 1.0, 0.0, nullptr, n, M + b * sN, n, flags, s);
-      if (e == cudaSuccess) e = mpj_oz_prepare(M + b * sN, 1, n, n, n, obuf + 2 * ob, &om, s);
-      if (e == cudaSuccess) e = mpj_oz_gemm(om, oq, n, n, 1.0, 0.0, nullptr, n, dA + b * sA, ldda, flags, s);
+      e = mpj_oz_prepare(Q + b * sQ, 1, ldq, n, n, ob0, &oq, sb);
+      if (e == cudaSuccess) e = mpj_oz_prepare(T + b * sN, n, 1, n, n, ob0 + ob, &ot, sb);
+      if (e == cudaSuccess) e = mpj_oz_gemm(oq, ot, n, n, 1.0, 0.0, nullptr, n, M + b * sN, n, flags, sb);
+      if (e == cudaSuccess) e = mpj_oz_prepare(M + b * sN, 1, n, n, n, ob0 + 2 * ob, &om, sb);
+      if (e == cudaSuccess) e = mpj_oz_gemm(om, oq, n, n, 1.0, 0.0, nullptr, n, dA + b * sA, ldda, flags, sb);
     }
+    if (e == cudaSuccess) e = join();
     if (e == cudaSuccess) {
       const size_t blocks = (sq + 255) / 256;
       bwd_mirror<<<dim3((unsigned)(blocks > 1024 ? 1024 : blocks), batch), 256, 0, s>>>(dA, ldda, sA, n);
@@ -125,8 +161,20 @@ extern "C" int mpj_syev_backward(int batch, int n, const double* W, const double
     mpj_set_cuda_error(e, "mpj_syev_backward", __LINE__);
     st = MPJ_ECUDA;
   }
+  if (tc && ev_fork) {
+    // whatever the error path, s must not run ahead of the side streams'
+    // work before the workspace is released
+    for (int i = 0; i < nw; ++i)
+      if (ws[i] && ev_join[i] && cudaEventRecord(ev_join[i], ws[i]) == cudaSuccess)
+        cudaStreamWaitEvent(s, ev_join[i], 0);
+  }
   cudaFreeAsync(w, s);
   e = cudaStreamSynchronize(s);
+  for (int i = 0; i < nw; ++i) {
+    if (ws[i]) cudaStreamDestroy(ws[i]);
+    if (ev_join[i]) cudaEventDestroy(ev_join[i]);
+  }
+  if (ev_fork) cudaEventDestroy(ev_fork);
   if (e != cudaSuccess && st >= 0) {
     mpj_set_cuda_error(e, "mpj_syev_backward sync", __LINE__);
     st = MPJ_ECUDA;
