@@ -5,10 +5,11 @@
 //   dA = sym(Q G Q^T) = Q sym(G) Q^T,  sym(X) = (X + X^T)/2.
 // Symmetrizing G first makes the last product symmetric in exact arithmetic,
 // so dA is written exactly symmetric (its lower triangle mirrored).  The three
-// products run, matrix after matrix, as FP64-accurate products on the tensor
-// cores (exact bf16 slices, ozaki.cu; Q sliced once per matrix for the two
-// products it enters from the same side), or with MPJ_GEMM_TC=0 on the FP64
-// DMMA kernel, batched over blockIdx.z (the last one as a lower-tile product).
+// products run as FP64-accurate products on the tensor cores (exact bf16
+// slices, ozaki.cu; Q sliced once per matrix for the two products it enters
+// from the same side), the matrices spread over side streams so that several
+// small products share the GPU, or with MPJ_GEMM_TC=0 on the FP64 DMMA kernel,
+// batched over blockIdx.z (the last one as a lower-tile product).
 #include "common.cuh"
 #include "gemm64.cuh"
 #include "ozaki.cuh"
