@@ -424,3 +424,20 @@ def test_block_sweeps_with_unrotated_block_pairs_vs_oracle(n):
     N = (n + 31) // 32 * 32
     # four of the N / 16 blocks carry all the coupling: at most 4 of the N / 32 block pairs rotate per round
     assert 0 < r.info["rotated_blocks64"] <= 4 * r.info["sweeps64"] * (N // 16 - 1)
+
+
+def test_block_mixed_solve_n8192_properties():
+    """The default solve at n = 8192 (index arithmetic beyond 2^26 entries,
+    products with K = 8192 in two passes of the exact-slice engine): the
+    eigenvalues against the constructed spectrum and the accuracy bounds."""
+    n = 8192
+    A, lam = inputs.geo_matrix(n, 1e3, seed=8)
+    r = mpj().syev_ex(dev(A))
+    W, Q = r.W, r.Q
+    assert r.status == 0
+    Ad = dev(A)
+    nA = float(np.abs(lam).max())
+    assert float((W - dev(np.sort(lam))).abs().max()) <= 1e-12 * nA
+    be = float(torch.linalg.norm(Ad - (Q * W) @ Q.T) / torch.linalg.norm(Ad))
+    orth = float(torch.linalg.norm(Q.T @ Q - torch.eye(n, dtype=torch.float64, device=Q.device)))
+    assert be <= 4 * n * U and orth <= 4 * n * U
