@@ -215,7 +215,8 @@ def test_exact_slices_tiny_exponents():
 
 
 # ---------------------------------------------------------------- caller workspace: no allocation
-@pytest.mark.parametrize("opts", [{}, {"ordering": "cyclic"}, {"precond_passes": 2}, {"method": "plain"}])
+@pytest.mark.parametrize("opts", [{}, {"ordering": "cyclic"}, {"precond_passes": 2}, {"method": "plain"},
+                                  {"stage1_half": 1}, {"ordering": "round_robin"}])
 def test_solve_with_caller_workspace_allocates_nothing(opts):
     m = mpj()
     n = 300
