@@ -10,9 +10,10 @@
 //      off(A32) <= n 2^-24 ||A||_F (cap max32), Q_l = double(V32);
 //   2. Newton-Schulz X <- 1.5 X - 0.5 X (X^T X), ns_steps times (FP64 DMMA);
 //   3. A_cond = X^T (A X) (FP64 DMMA, lower tiles mirrored);
-//   4. FP64 round-robin Jacobi on A_cond from V = I until off <= tol (cap max64),
-//      also skipping pairs with |a_pq| <= tol/n (threshold Jacobi);
-//   5. W = sorted diag, Q = X V (columns permuted), written to the caller.
+//   4. FP64 round-robin Jacobi on A_cond until off <= tol (cap max64), also
+//      skipping pairs with |a_pq| <= tol/n (threshold Jacobi), its rotations
+//      applied to the columns of X = Q_d directly (Q = Q_d V by associativity);
+//   5. W = sorted diag, Q = the rotated X with its columns permuted.
 // Groups synchronize with named barriers (bar.sync id, G), so small matrices
 // share an SM.  The round-robin ordering, the rotation records and the
 // 2x2-block update are those of common.cuh; one round is one barrier-separated
@@ -59,7 +60,6 @@ struct Bufs {
   double* X;
   double* M;
   double* Y;
-  double* Vp;  // aliases A32/V32 after stage 1
 };
 
 MPJ_DEV double group_sum(const Grp& g, double v, double* red) {
@@ -384,7 +384,6 @@ __global__ void __launch_bounds__(NTH, 1)
   Bufs B;
   B.A32 = (float*)base;
   B.V32 = B.A32 + NMAX * NMAX;
-  B.Vp = (double*)base;
   B.X = (double*)(base + 2 * (size_t)NMAX * NMAX * sizeof(float));
   B.M = B.X + NMAX * NMAX;
   B.Y = B.M + NMAX * NMAX;
@@ -442,10 +441,9 @@ __global__ void __launch_bounds__(NTH, 1)
     // 3. A_cond = X^T (A X) -> M
     grp_gemm<false, false>(g, n, 1.0, A, X, 0.0, nullptr, Y, false);
     grp_gemm<true, false>(g, n, 1.0, X, Y, 0.0, nullptr, B.M, true);
-    // 4. FP64 sweeps, V = Y from I
-    double* V = Y;
-    for (int e = tid; e < n * n; e += G) V[e] = (e % n == e / n) ? 1.0 : 0.0;
-    gsync(g);
+    // 4. FP64 sweeps; their rotations are applied to Q_d's columns directly
+    // (Q = Q_d V by associativity, no final product)
+    double* V = X;
     int sweeps = 0;
     for (;;) {
       double off2 = grp_off2<double>(g, n, B.M, red[g.id]);
@@ -457,7 +455,7 @@ __global__ void __launch_bounds__(NTH, 1)
       grp_rr_sweep_fast(g, n, B.M, V, rec64[g.id], dsc[g.id], 0x1p-53, tol / n);  // threshold variant
       ++sweeps;
     }
-    // 5. sort, permute, Q = X Vp
+    // 5. sort; Q's columns are the rotated Q_d's, permuted
     for (int i = tid; i < n; i += G) {
       double wi = B.M[(size_t)i * n + i];
       int r = 0;
@@ -471,10 +469,8 @@ __global__ void __launch_bounds__(NTH, 1)
     gsync(g);
     for (int e = tid; e < n * n; e += G) {
       int i = e % n, j = e / n;
-      B.Vp[(size_t)rank_sh[g.id][j] * n + i] = V[e];
+      Q[(size_t)rank_sh[g.id][j] * n + i] = V[e];
     }
-    gsync(g);
-    grp_gemm<false, false>(g, n, 1.0, X, B.Vp, 0.0, nullptr, Q, false);
     if (tid == 0) sweeps_out[idx] = sweeps;
     gsync(g);
   }
