@@ -182,9 +182,9 @@ MPJ_DEV double z_to_double(long long hi, long long lo, int E) {
 // ---------------------------------------------------------------- subproblems
 // One CTA per block pair of round R: one inner round-robin sweep on the FP64
 // 32 x 32 subproblem (the paper's row update, column update and vector update
-// per rotation, with c - 1 carried separately so that tiny rotations keep U
-// orthogonal, see common.cuh; the 16 disjoint rotations of an inner round are
-// applied together), then U_P's columns cut into digits for the tensor products.
+// per rotation, in scaled form: one FMA per entry and side, the factors c kept
+// in a scale vector; the 16 disjoint rotations of an inner round are applied
+// together), then U_P's columns cut into digits for the tensor products.
 // Writes per block pair: NSL digit tiles (32 x 32 bf16, K-major over the
 // rows of U_P, one "row" per column of U_P), 32 column exponents, and whether
 // any rotation happened.
@@ -208,60 +208,107 @@ __global__ void __launch_bounds__(SOLVE_THREADS) blk_solve(const double* __restr
     U[li][lj] = (li == lj) ? 1.0 : 0.0;
   }
   __syncthreads();
+  // Scaled rotations (the scheme of the scalar round-robin sweeps): off the
+  // diagonal S = D S~ D and U = U~ D with one scale vector d (and e = 1/d);
+  // S's diagonal holds the true values.  A rotation (c, s = t c) of pair
+  // p < q then costs one FMA per entry and side:
+  //   x_p <- x_p - mx x_q,  x_q <- x_q + my x_p  (old values),
+  //   mx = t d_q / d_p,  my = t d_p / d_q,  d_p, d_q <- c d_p, c d_q,
+  // the pair's diagonal becomes a_pp - t a_pq, a_qq + t a_pq and a_pq 0.
   // Each inner round applies its 16 rotations to every 2 x 2 block of S
-  // between two pairs a <= b once (rows by J_a, then columns by J_b, as the
-  // sequential order does for a before b; the mirror block is the same values
-  // transposed) and to the two columns of U of every pair.  The next round's
-  // rotations read only the blocks (a, a) and the blocks (a, b) that hold one
-  // of its pairs: warp 0 updates those "critical" blocks first and then
-  // computes the next round's rotations, while warps 1-7 update the other
-  // blocks and U.  Each block is updated by exactly one thread with the same
-  // arithmetic as in sequential order, so the result does not depend on this
-  // division of the work.
-  __shared__ double cs[2][W2 / 2][2];
+  // between two pairs a < b once (rows by pair a, then columns by pair b; the
+  // mirror block is the same values transposed) and to the two columns of U~
+  // of every pair.  The next round's rotations read only the diagonal entries
+  // and the blocks (a, b) that hold one of its pairs: warp 0 sets the
+  // diagonal blocks and updates those blocks first and then computes the next
+  // round's rotations, while the other warps update the remaining blocks and
+  // U~.  Each block is updated by exactly one thread.
+  __shared__ double cs[2][W2 / 2][2];  // mx, my
+  __shared__ double dg[2][W2 / 2][2];  // the pair's new true diagonal
   __shared__ int rot[2][W2 / 2];
   __shared__ int pq[2][W2 / 2][2];
   __shared__ int slot_of[2][W2];  // pair slot of each local index in the round
+  __shared__ double dsc[W2], esc[W2];  // d and e = 1 / d
   const int warp = tid >> 5, lane = tid & 31;
-  // Algorithm 2 with the skip test of Algorithm 4 for pair `k` of inner round rho
+  if (tid < W2) {
+    dsc[tid] = 1.0;
+    esc[tid] = 1.0;
+  }
+  __syncthreads();
+  // Algorithm 2 with the skip test of Algorithm 4 for pair `k` of inner round
+  // rho, on the true coupling; the pair's scales are updated here (its lane
+  // is the only one that touches them this round)
   auto rotation = [&](int rho, int k, int buf) {
     int x, y;
     rr_slot(W2, rho, k, x, y);
     const int p = x < y ? x : y, q = x < y ? y : x;
+    const double app = S[p][p], aqq = S[q][q];
+    const double dp = dsc[p], dq = dsc[q];
+    const double apq = S[p][q] * dp * dq;
     double t = 0.0, cm1 = 0.0, sn = 0.0;
-    const int r = gidx(I, J, q) < n && jacobi_pair<double>(S[p][p], S[q][q], S[p][q], skip, t, cm1, sn, skip_abs);
-    if (r) any = 1;
-    cs[buf][k][0] = cm1;
-    cs[buf][k][1] = sn;
+    const int r = gidx(I, J, q) < n && jacobi_pair<double>(app, aqq, apq, skip, t, cm1, sn, skip_abs);
+    double mx = 0.0, my = 0.0;
+    if (r) {
+      any = 1;
+      const double ep = esc[p], eq = esc[q];
+      mx = t * dq * ep;
+      my = t * dp * eq;
+      const double h = sqrt(fma(t, t, 1.0));  // 1 / c
+      dsc[p] = fma(dp, cm1, dp);
+      dsc[q] = fma(dq, cm1, dq);
+      esc[p] = ep * h;
+      esc[q] = eq * h;
+      dg[buf][k][0] = app - t * apq;
+      dg[buf][k][1] = aqq + t * apq;
+    }
+    cs[buf][k][0] = mx;
+    cs[buf][k][1] = my;
     rot[buf][k] = r;
     pq[buf][k][0] = p;
     pq[buf][k][1] = q;
     slot_of[buf][p] = k;
     slot_of[buf][q] = k;
   };
-  // the 2 x 2 block between pairs a <= b of the round in buffer `buf`
+  // the pair's own 2 x 2 block: the new true diagonal and a zero coupling
+  auto diag_update = [&](int a, int buf) {
+    if (!rot[buf][a]) return;
+    const int pa = pq[buf][a][0], qa = pq[buf][a][1];
+    S[pa][pa] = dg[buf][a][0];
+    S[qa][qa] = dg[buf][a][1];
+    S[pa][qa] = 0.0;
+    S[qa][pa] = 0.0;
+  };
+  // the 2 x 2 block between pairs a < b of the round in buffer `buf`
   auto block_update = [&](int a, int b, int buf) {
     if (!rot[buf][a] && !rot[buf][b]) return;
     const int pa = pq[buf][a][0], qa = pq[buf][a][1], pb = pq[buf][b][0], qb = pq[buf][b][1];
     double b00 = S[pa][pb], b01 = S[pa][qb], b10 = S[qa][pb], b11 = S[qa][qb];
-    if (rot[buf][a]) {
-      rot_apply(cs[buf][a][0], cs[buf][a][1], b00, b10);  // rows pa, qa of column pb
-      rot_apply(cs[buf][a][0], cs[buf][a][1], b01, b11);  // of column qb
+    if (rot[buf][a]) {  // rows pa, qa
+      const double mx = cs[buf][a][0], my = cs[buf][a][1];
+      const double t00 = fma(-mx, b10, b00), t10 = fma(my, b00, b10);
+      const double t01 = fma(-mx, b11, b01), t11 = fma(my, b01, b11);
+      b00 = t00;
+      b10 = t10;
+      b01 = t01;
+      b11 = t11;
     }
-    if (rot[buf][b]) {
-      rot_apply(cs[buf][b][0], cs[buf][b][1], b00, b01);  // columns pb, qb of row pa
-      rot_apply(cs[buf][b][0], cs[buf][b][1], b10, b11);  // of row qa
+    if (rot[buf][b]) {  // columns pb, qb
+      const double mx = cs[buf][b][0], my = cs[buf][b][1];
+      const double t00 = fma(-mx, b01, b00), t01 = fma(my, b00, b01);
+      const double t10 = fma(-mx, b11, b10), t11 = fma(my, b10, b11);
+      b00 = t00;
+      b01 = t01;
+      b10 = t10;
+      b11 = t11;
     }
     S[pa][pb] = b00;
     S[pa][qb] = b01;
     S[qa][pb] = b10;
     S[qa][qb] = b11;
-    if (a != b) {
-      S[pb][pa] = b00;
-      S[qb][pa] = b01;
-      S[pb][qa] = b10;
-      S[qb][qa] = b11;
-    }
+    S[pb][pa] = b00;
+    S[qb][pa] = b01;
+    S[pb][qa] = b10;
+    S[qb][qa] = b11;
   };
   if (warp == 0 && lane < W2 / 2) rotation(0, lane, 0);
   __syncthreads();
@@ -269,10 +316,10 @@ __global__ void __launch_bounds__(SOLVE_THREADS) blk_solve(const double* __restr
     const int cur = rho & 1;
     const bool more = rho + 1 < W2 - 1;
     if (warp == 0) {
-      // lanes 0-15: the diagonal blocks; lanes 16-31: the block holding pair
+      // lanes 0-15: the pairs' own blocks; lanes 16-31: the block holding pair
       // lane - 16 of the next round (once, when two next pairs share a block)
       if (lane < W2 / 2) {
-        block_update(lane, lane, cur);
+        diag_update(lane, cur);
       } else if (more) {
         int x, y;
         rr_slot(W2, rho + 1, lane - W2 / 2, x, y);
@@ -294,34 +341,38 @@ __global__ void __launch_bounds__(SOLVE_THREADS) blk_solve(const double* __restr
       __syncwarp();
       if (more && lane < W2 / 2) rotation(rho + 1, lane, cur ^ 1);
     } else {
-      for (int task = tid - 32; task < 136 + (W2 / 2) * W2; task += blockDim.x - 32) {
-        if (task < 136) {
-          // pair indices a < b from the triangular task number (a == b: warp 0)
+      for (int task = tid - 32; task < 120 + (W2 / 2) * W2; task += blockDim.x - 32) {
+        if (task < 120) {
+          // pair indices a < b from the triangular task number
           int a = 0, rem = task;
-          while (rem >= 16 - a) {
-            rem -= 16 - a;
+          while (rem >= 15 - a) {
+            rem -= 15 - a;
             ++a;
           }
-          const int b = a + rem;
-          if (a == b) continue;
+          const int b = a + 1 + rem;
           if (more) {  // a block that holds a pair of the next round: warp 0
             const int na = rr_partner(W2, rho + 1, pq[cur][a][0]), nq = rr_partner(W2, rho + 1, pq[cur][a][1]);
             if (slot_of[cur][na] == b || slot_of[cur][nq] == b) continue;
           }
           block_update(a, b, cur);
         } else {
-          const int e = task - 136, k = e / W2, j = e % W2;
+          const int e = task - 120, k = e / W2, j = e % W2;
           if (!rot[cur][k]) continue;
           const int p = pq[cur][k][0], q = pq[cur][k][1];
-          double up = U[j][p], uq = U[j][q];
-          rot_apply(cs[cur][k][0], cs[cur][k][1], up, uq);
-          U[j][p] = up;
-          U[j][q] = uq;
+          const double up = U[j][p], uq = U[j][q];
+          U[j][p] = fma(-cs[cur][k][0], uq, up);
+          U[j][q] = fma(cs[cur][k][1], up, uq);
         }
       }
     }
     __syncthreads();
   }
+  // U = U~ D
+  for (int e = tid; e < W2 * W2; e += blockDim.x) {
+    const int i = e % W2, j = e / W2;
+    U[i][j] *= dsc[j];
+  }
+  __syncthreads();
   // One Newton-Schulz step on U_P (Sec. 4.3.4): U <- U - U E / 2, E = U^T U - I.
   // U_P carries the rounding of its 496 rotations; applied to all of A and V
   // every round, that departure from orthogonality would accumulate over the
