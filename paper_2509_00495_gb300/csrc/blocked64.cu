@@ -179,6 +179,22 @@ MPJ_DEV double z_to_double(long long hi, long long lo, int E) {
   return __longlong_as_double((long long)(sign | ((unsigned long long)biased << 52) | (mant & ((1ULL << 52) - 1ULL))));
 }
 
+// Algorithm 2 for the scaled subproblem rotations, with the skip test of
+// Algorithm 4 (|a_pq| > skip sqrt|a_pp a_qq|, compared in squares, and the
+// threshold |a_pq| > skip_abs): t as in the stable form, c = 1 / sqrt(1 + t^2)
+// and h = 1 / c = (1 + t^2) c for the scale vector and its reciprocal.
+MPJ_DEV bool rot_scaled(double app, double aqq, double apq, double skip, double skip_abs, double& t, double& c,
+                        double& h) {
+  if (!(apq * apq > (skip * skip) * fabs(app * aqq) && fabs(apq) > skip_abs)) return false;
+  const double tau = (aqq - app) / (2.0 * apq);
+  const double r = sqrt(fma(tau, tau, 1.0));
+  t = (tau >= 0.0) ? 1.0 / (tau + r) : 1.0 / (tau - r);
+  const double w = fma(t, t, 1.0);
+  c = rsqrt(w);
+  h = w * c;
+  return true;
+}
+
 // ---------------------------------------------------------------- subproblems
 // One CTA per block pair of round R: one inner round-robin sweep on the FP64
 // 32 x 32 subproblem (the paper's row update, column update and vector update
@@ -245,17 +261,16 @@ __global__ void __launch_bounds__(SOLVE_THREADS) blk_solve(const double* __restr
     const double app = S[p][p], aqq = S[q][q];
     const double dp = dsc[p], dq = dsc[q];
     const double apq = S[p][q] * dp * dq;
-    double t = 0.0, cm1 = 0.0, sn = 0.0;
-    const int r = gidx(I, J, q) < n && jacobi_pair<double>(app, aqq, apq, skip, t, cm1, sn, skip_abs);
+    double t = 0.0, c = 1.0, h = 1.0;
+    const int r = gidx(I, J, q) < n && rot_scaled(app, aqq, apq, skip, skip_abs, t, c, h);
     double mx = 0.0, my = 0.0;
     if (r) {
       any = 1;
       const double ep = esc[p], eq = esc[q];
       mx = t * dq * ep;
       my = t * dp * eq;
-      const double h = sqrt(fma(t, t, 1.0));  // 1 / c
-      dsc[p] = fma(dp, cm1, dp);
-      dsc[q] = fma(dq, cm1, dq);
+      dsc[p] = dp * c;
+      dsc[q] = dq * c;
       esc[p] = ep * h;
       esc[q] = eq * h;
       dg[buf][k][0] = app - t * apq;
