@@ -66,6 +66,32 @@ __global__ void widen(const float* __restrict__ V32, int N, int n, double* __res
   }
 }
 
+// The record of slot (x, y) (x the slot's first index) for the FP32 inner
+// sweep: Algorithm 2 with the skip test of Algorithm 4 (compared in squares),
+// t in the stable form, c = 1 / sqrt(1 + t^2) by rsqrtf, c - 1 = -t^2 c / (1 + h)
+// with h = 1 / c = (1 + t^2) c; the new diagonal a_pp - t a_pq, a_qq + t a_pq.
+MPJ_DEV void rec32(int x, int y, float dxx, float dyy, float axy, float skip, RotRec<float>& rr) {
+  const bool xp = x < y;
+  const float app = xp ? dxx : dyy, aqq = xp ? dyy : dxx;
+  rr.cm1 = 0.0f;
+  rr.sig = 0.0f;
+  rr.dx = dxx;
+  rr.dy = dyy;
+  if (!(axy * axy > (skip * skip) * fabsf(app * aqq)) || y >= W2 || x >= W2) return;
+  const float tau = (aqq - app) / (2.0f * axy);
+  const float r = sqrtf(fmaf(tau, tau, 1.0f));
+  const float t = (tau >= 0.0f) ? 1.0f / (tau + r) : 1.0f / (tau - r);
+  const float w = fmaf(t, t, 1.0f);
+  const float c = rsqrtf(w);
+  const float h = w * c;
+  const float s = t * c;
+  rr.cm1 = -(t * t) * c / (1.0f + h);
+  rr.sig = xp ? s : -s;
+  const float np = app - t * axy, nq = aqq + t * axy;
+  rr.dx = xp ? np : nq;
+  rr.dy = xp ? nq : np;
+}
+
 // One CTA per block pair of outer round R: inner round-robin sweep on the
 // 32 x 32 subproblem; writes the rotated subproblem S and the accumulated U.
 __global__ void __launch_bounds__(256) solve32(const float* __restrict__ A32, int N, int nb, int R,
@@ -92,7 +118,7 @@ __global__ void __launch_bounds__(256) solve32(const float* __restrict__ A32, in
       int x, y;
       rr_slot(W2, rho, tid, x, y);
       RotRec<float> rr;
-      rr_make_rec<float>(W2, W2, rho, x, y, S[x][x], S[y][y], S[y][x], skip, rr);
+      rec32(x, y, S[x][x], S[y][y], S[y][x], skip, rr);
       if (hq && rec_rotated(rr.cm1, rr.sig)) {  // c and s as binary16, new diagonal rounded
         rr.cm1 = qh(1.0f + rr.cm1, true) - 1.0f;
         rr.sig = qh(rr.sig, true);
