@@ -32,9 +32,10 @@
  *     has an iteration or clock limit.
  *
  * Environment switches (read once per process):
- *   MPJ_JACOBI_OVERLAP=0  keep the batched V updates of the round-robin FP64
- *                         sweeps on `stream` (by default they run on a
- *                         private side stream joined back into `stream`);
+ *   MPJ_JACOBI_OVERLAP=0  keep the V updates of the FP32 stage-1 rounds and
+ *                         of the FP64 sweeps on `stream` (by default they
+ *                         run on a private side stream joined back into
+ *                         `stream`);
  *   MPJ_STAGE1_TC=1       run the stage-1 A update on the tcgen05 tensor
  *                         cores (3xTF32; slower on GB300, off by default);
  *   MPJ_GEMM_TC=0         run the Newton-Schulz and Q_d^T A Q_d products on

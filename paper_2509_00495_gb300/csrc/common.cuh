@@ -205,6 +205,37 @@ cudaError_t mpj_launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size
   mpj_count_launch();
   return e;
 }
+
+// Side stream and events for overlapping the V updates with the rotation
+// rounds; released when the solve returns.  On every exit (also an early
+// error return) the owner stream is first made to wait for the side stream,
+// so stream-ordered reuse or freeing of the scratch stays after the last V
+// update.
+struct SideStream {
+  cudaStream_t owner = nullptr;
+  cudaStream_t sv = nullptr;
+  cudaEvent_t ready = nullptr, done[2] = {nullptr, nullptr};
+  bool ok = false;
+  explicit SideStream(cudaStream_t s) : owner(s) {
+    ok = cudaStreamCreateWithFlags(&sv, cudaStreamNonBlocking) == cudaSuccess &&
+         cudaEventCreateWithFlags(&ready, cudaEventDisableTiming) == cudaSuccess &&
+         cudaEventCreateWithFlags(&done[0], cudaEventDisableTiming) == cudaSuccess &&
+         cudaEventCreateWithFlags(&done[1], cudaEventDisableTiming) == cudaSuccess;
+    if (!ok) (void)cudaGetLastError();
+  }
+  ~SideStream() {
+    if (ok && cudaEventRecord(ready, sv) == cudaSuccess) (void)cudaStreamWaitEvent(owner, ready, 0);
+    if (done[1]) cudaEventDestroy(done[1]);
+    if (done[0]) cudaEventDestroy(done[0]);
+    if (ready) cudaEventDestroy(ready);
+    if (sv) cudaStreamDestroy(sv);
+  }
+};
+
+// Whether the V updates of the Jacobi sweeps (FP32 and FP64) may run on a
+// side stream (environment MPJ_JACOBI_OVERLAP=0 keeps them on the caller's).
+bool mpj_v_overlap_enabled();
+
 // Counts every device (or pinned host) allocation the library makes
 // (diagnostic, mpj_device_allocations).
 void mpj_count_alloc();

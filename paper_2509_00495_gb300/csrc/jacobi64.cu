@@ -721,32 +721,6 @@ size_t mpj_jacobi64_scratch_bytes_ordering(int n, int ordering) {
 }
 
 namespace {
-// Side stream and events for overlapping the V updates with the rotation
-// rounds; released when the solve returns.  On every exit (also an early
-// error return) the owner stream is first made to wait for the side stream,
-// so stream-ordered reuse or freeing of the scratch stays after the last V
-// update.
-struct SideStream {
-  cudaStream_t owner = nullptr;
-  cudaStream_t sv = nullptr;
-  cudaEvent_t ready = nullptr, done[2] = {nullptr, nullptr};
-  bool ok = false;
-  explicit SideStream(cudaStream_t s) : owner(s) {
-    ok = cudaStreamCreateWithFlags(&sv, cudaStreamNonBlocking) == cudaSuccess &&
-         cudaEventCreateWithFlags(&ready, cudaEventDisableTiming) == cudaSuccess &&
-         cudaEventCreateWithFlags(&done[0], cudaEventDisableTiming) == cudaSuccess &&
-         cudaEventCreateWithFlags(&done[1], cudaEventDisableTiming) == cudaSuccess;
-    if (!ok) (void)cudaGetLastError();
-  }
-  ~SideStream() {
-    if (ok && cudaEventRecord(ready, sv) == cudaSuccess) (void)cudaStreamWaitEvent(owner, ready, 0);
-    if (done[1]) cudaEventDestroy(done[1]);
-    if (done[0]) cudaEventDestroy(done[0]);
-    if (ready) cudaEventDestroy(ready);
-    if (sv) cudaStreamDestroy(sv);
-  }
-};
-
 // rr_step64 with programmatic stream serialization, so that consecutive
 // rounds overlap their launch and ramp-up (the kernel waits in
 // griddepcontrol.wait before touching memory).
@@ -769,15 +743,17 @@ cudaError_t launch_rr_step64(int grid, cudaStream_t s, double* A, int lda, int n
   return e;
 }
 
-bool overlap_enabled(int n) {
+bool overlap_enabled(int n) { return mpj_v_overlap_enabled() && n >= 256; }
+}  // namespace
+
+bool mpj_v_overlap_enabled() {
   static int env = -1;
   if (env < 0) {
     const char* e = getenv("MPJ_JACOBI_OVERLAP");
     env = (e && e[0] == '0') ? 0 : 1;
   }
-  return env == 1 && n >= 256;
+  return env == 1;
 }
-}  // namespace
 
 int mpj_jacobi64_run(int n, double* A, int lda, double* V, int ldv, double tol, int ordering, int max_sweeps,
                      int* sweeps_out, double* off_out, double* off_initial, void* scratch, size_t scratch_bytes,

@@ -19,6 +19,7 @@
 // each restricted to the tiles the next step needs, so that A32 and V32 are
 // touched once or twice per round instead of once per pair step.  off(A32) is
 // reduced after each sweep; stop at off(A32) <= tol32 or the sweep cap.
+#include <memory>
 #include <cuda_fp16.h>
 #include <stdlib.h>
 
@@ -94,7 +95,8 @@ MPJ_DEV void rec32(int x, int y, float dxx, float dyy, float axy, float skip, Ro
 
 // One CTA per block pair of outer round R: inner round-robin sweep on the
 // 32 x 32 subproblem; writes the rotated subproblem S and the accumulated U.
-__global__ void __launch_bounds__(256) solve32(const float* __restrict__ A32, int N, int nb, int R,
+constexpr int S32_THREADS = 512;
+__global__ void __launch_bounds__(S32_THREADS) solve32(const float* __restrict__ A32, int N, int nb, int R,
                                                float* __restrict__ Sbuf, float* __restrict__ Ubuf, bool hq) {
   __shared__ float S[W2][LD];
   __shared__ float U[W2][LD];
@@ -105,8 +107,8 @@ __global__ void __launch_bounds__(256) solve32(const float* __restrict__ A32, in
   const int tid = threadIdx.x;
   pdl_wait();
   #pragma unroll
-  for (int it = 0; it < W2 * W2 / 256; ++it) {
-    const int e = tid + it * 256;
+  for (int it = 0; it < W2 * W2 / S32_THREADS; ++it) {
+    const int e = tid + it * S32_THREADS;
     int li = e % W2, lj = e / W2;
     S[li][lj] = A32[(size_t)gidx(I, J, lj) * N + gidx(I, J, li)];
     U[li][lj] = (li == lj) ? 1.0f : 0.0f;
@@ -130,7 +132,7 @@ __global__ void __launch_bounds__(256) solve32(const float* __restrict__ A32, in
     __syncthreads();
     {
       int a = tid % 16, b = tid / 16;
-      if (a >= b) {
+      if (b < 16 && a >= b) {
         int xa, ya, xb, yb;
         rr_slot(W2, rho, a, xa, ya);
         rr_slot(W2, rho, b, xb, yb);
@@ -168,7 +170,7 @@ __global__ void __launch_bounds__(256) solve32(const float* __restrict__ A32, in
         }
       }
       // U <- U J: rows of U are independent; columns x_b, y_b
-      for (int e = tid; e < W2 * (W2 / 2); e += 256) {
+      for (int e = tid; e < W2 * (W2 / 2); e += S32_THREADS) {
         int row = e % W2, sb = e / W2;
         RotRec<float> rb = rec[sb];
         if (!rec_rotated(rb.cm1, rb.sig)) continue;
@@ -185,8 +187,8 @@ __global__ void __launch_bounds__(256) solve32(const float* __restrict__ A32, in
   float* So = Sbuf + (size_t)slot * W2 * W2;
   float* Uo = Ubuf + (size_t)slot * W2 * W2;
   #pragma unroll
-  for (int it = 0; it < W2 * W2 / 256; ++it) {
-    const int e = tid + it * 256;
+  for (int it = 0; it < W2 * W2 / S32_THREADS; ++it) {
+    const int e = tid + it * S32_THREADS;
     int li = e % W2, lj = e / W2;
     So[e] = S[li][lj];
     Uo[e] = U[li][lj];
@@ -349,14 +351,14 @@ __global__ void __launch_bounds__(RT) rmul32(const float* X, float* Y, int N, in
 
 int mpj_stage1_padded(int n) { return ((n + W2 - 1) / W2) * W2; }
 
-// A32, V32, the per-pair S and U, a flag word after them (the tensor-core
+// A32, V32, two sets of the per-pair S and U (alternate rounds), a flag word after them (the tensor-core
 // update also keeps the transposed intermediate B^T there).
 static int stage1_tensor_cores();
 
 size_t mpj_stage1_bytes(int n) {
   size_t N = (size_t)mpj_stage1_padded(n);
   size_t nb = N / BS;
-  return 3 * N * N * sizeof(float) + 2 * (nb / 2) * W2 * W2 * sizeof(float) + 4096;
+  return 3 * N * N * sizeof(float) + 4 * (nb / 2) * W2 * W2 * sizeof(float) + 4096;
 }
 
 // MPJ_STAGE1_TC=1 runs the A update of each block round on the tcgen05
@@ -382,9 +384,10 @@ int mpj_stage1_run(int n, const double* A, int lda, double* Ql, int ldq, double 
   const int nb = N / BS;
   float* A32 = (float*)work;
   float* V32 = A32 + (size_t)N * N;
-  float* Sbuf = V32 + (size_t)N * N;
-  float* Ubuf = Sbuf + (size_t)(nb / 2) * W2 * W2;
-  float* Bt = Ubuf + (size_t)(nb / 2) * W2 * W2;
+  const size_t pset = (size_t)(nb / 2) * W2 * W2;
+  float* Sb[2] = {V32 + (size_t)N * N, V32 + (size_t)N * N + pset};
+  float* Ub[2] = {Sb[1] + pset, Sb[1] + 2 * pset};
+  float* Bt = Ub[1] + pset;
   unsigned* tflag = (unsigned*)(Bt + (size_t)N * N);
   MPJ_CUDA_TRY(cudaMemsetAsync(tflag, 0, sizeof(unsigned), s));
   const int tc = stage1_tensor_cores() && !half;
@@ -398,27 +401,47 @@ int mpj_stage1_run(int n, const double* A, int lda, double* Ql, int ldq, double 
   double off = sqrt(off2);
   int sweeps = 0, status = MPJ_OK;
   const int npairs = nb / 2;
+  const dim3 g32((npairs + 3) / 4, npairs);
+  // V <- V U~ of round R runs on a side stream, overlapping round R + 1's
+  // subproblems; the S/U sets alternate between rounds, and round R + 2's
+  // subproblems wait for round R's V update before overwriting its set.
+  // The side stream is joined before V is read (and on every return).
+  std::unique_ptr<SideStream> side;
+  if (mpj_v_overlap_enabled() && npairs >= 8) {
+    side.reset(new SideStream(s));
+    if (!side->ok) side.reset();
+  }
+  bool vpending[2] = {false, false};
   while (off > tol32) {
     if (sweeps >= max_sweeps) {
       status = MPJ_NOT_CONVERGED;
       break;
     }
     for (int R = 0; R < nb - 1; ++R) {
-      MPJ_CUDA_TRY(mpj_launch_pdl(solve32, dim3(npairs), dim3(256), 0, s, A32, N, nb, R, Sbuf, Ubuf, half));
+      const int par = R & 1;
+      float* Sbuf = Sb[par];
+      float* Ubuf = Ub[par];
+      if (side && vpending[par]) MPJ_CUDA_TRY(cudaStreamWaitEvent(s, side->done[par], 0));
+      MPJ_CUDA_TRY(mpj_launch_pdl(solve32, dim3(npairs), dim3(S32_THREADS), 0, s, A32, N, nb, R, Sbuf, Ubuf, half));
+      // V <- V U~
+      if (side) {
+        MPJ_CUDA_TRY(cudaEventRecord(side->ready, s));
+        MPJ_CUDA_TRY(cudaStreamWaitEvent(side->sv, side->ready, 0));
+        MPJ_CUDA_TRY(mpj_launch_pdl(rmul32, g32, dim3(RT), 0, side->sv, (const float*)V32, V32, N, nb, R,
+                                    (const float*)Sbuf, (const float*)Ubuf, (int)R32_ALL, half));
+        MPJ_CUDA_TRY(cudaEventRecord(side->done[par], side->sv));
+        vpending[par] = true;
+      } else {
+        MPJ_CUDA_TRY(mpj_launch_pdl(rmul32, g32, dim3(RT), 0, s, (const float*)V32, V32, N, nb, R,
+                                    (const float*)Sbuf, (const float*)Ubuf, (int)R32_ALL, half));
+      }
       if (tc == 1) {
         // A' = U^T A U = (A U)^T U (A symmetric): B^T = (A U)^T, then
         // A' = (B^T)(:, I_q) U_q on the tensor cores; V U on the FP32 pipe
         MPJ_CUDA_TRY(mpj_tc_panel(N, nb, R, Ubuf, A32, Bt, 1, nullptr, nullptr, tflag, s));
         MPJ_CUDA_TRY(mpj_tc_panel(N, nb, R, Ubuf, Bt, A32, 0, nullptr, nullptr, tflag, s));
-        rmul32<<<dim3((npairs + 3) / 4, npairs), RT, 0, s>>>(V32, V32, N, nb, R, Sbuf, Ubuf, R32_ALL,
-                                                              false);
-        mpj_count_launch();
       } else {
-        // V <- V U~, B = A U~ (tiles a < Q, stored transposed), A = B^T U~ (tiles a > Q, mirrored; S on
-        // the diagonal)
-        const dim3 g32((npairs + 3) / 4, npairs);
-        MPJ_CUDA_TRY(mpj_launch_pdl(rmul32, g32, dim3(RT), 0, s, (const float*)V32, V32, N, nb, R,
-                                    (const float*)Sbuf, (const float*)Ubuf, (int)R32_ALL, half));
+        // B = A U~ (tiles a < Q, stored transposed), A = B^T U~ (tiles a > Q, mirrored; S on the diagonal)
         MPJ_CUDA_TRY(mpj_launch_pdl(rmul32, g32, dim3(RT), 0, s, (const float*)A32, Bt, N, nb, R,
                                     (const float*)Sbuf, (const float*)Ubuf, (int)R32_FIRST, half));
         MPJ_CUDA_TRY(mpj_launch_pdl(rmul32, g32, dim3(RT), 0, s, (const float*)Bt, A32, N, nb, R,
@@ -434,6 +457,10 @@ int mpj_stage1_run(int n, const double* A, int lda, double* Ql, int ldq, double 
     MPJ_CUDA_TRY(cudaStreamSynchronize(s));
     if (tf & MPJ_FLAG_TIMEOUT) return MPJ_ETIMEOUT;
     off = sqrt(off2);
+  }
+  if (side) {
+    for (int par = 0; par < 2; ++par)
+      if (vpending[par]) MPJ_CUDA_TRY(cudaStreamWaitEvent(s, side->done[par], 0));
   }
   widen<<<1024, 256, 0, s>>>(V32, N, n, Ql, ldq);
   mpj_count_launch();

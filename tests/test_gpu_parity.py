@@ -525,9 +525,10 @@ np.save(sys.argv[2], np.concatenate([r.W.cpu().numpy()[None, :], r.Q.cpu().numpy
 
 @pytest.mark.gpu
 def test_side_stream_overlap_is_bitwise_neutral(tmp_path):
-    """The batched V updates give the same bits on the private side stream as
-    on the caller's stream (n = 300 >= 256 turns the overlap on); a difference
-    would flag a race between the rotation rounds and the V updates."""
+    """The V updates of stage 1 and of the FP64 sweeps give the same bits on
+    the private side stream as on the caller's stream (n = 300 >= 256 turns
+    the overlap on in both); a difference would flag a race between the
+    rotation rounds and the V updates."""
     import os
     import subprocess
     import sys as _sys
