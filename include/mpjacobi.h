@@ -36,6 +36,9 @@
  *                         of the FP64 sweeps on `stream` (by default they
  *                         run on a private side stream joined back into
  *                         `stream`);
+ *   MPJ_STAGE1_GRAPH=0    enqueue the stage-1 sweeps kernel by kernel (by
+ *                         default one sweep is captured once per workspace
+ *                         as a CUDA graph and replayed);
  *   MPJ_STAGE1_TC=1       run the stage-1 A update on the tcgen05 tensor
  *                         cores (3xTF32; slower on GB300, off by default);
  *   MPJ_GEMM_TC=0         run the Newton-Schulz and Q_d^T A Q_d products on

@@ -175,8 +175,11 @@ MPJ_DEV float ld_cg(const float* p) { return __ldcg(p); }
 
 // Host-side helpers implemented in syev.cu
 void mpj_set_cuda_error(cudaError_t e, const char* what, int line);
-// Counts every kernel this library enqueues (diagnostic, mpj_kernel_launches).
+// Counts every kernel this library enqueues (diagnostic, mpj_kernel_launches);
+// mpj_count_launches adds k at once (a graph replay; negative for kernels
+// that were only captured).
 void mpj_count_launch();
+void mpj_count_launches(long long k);
 
 // Programmatic dependent launch.  A kernel launched by mpj_launch_pdl may have
 // its CTAs scheduled while the previous kernel in the stream drains (once all
@@ -210,7 +213,7 @@ cudaError_t mpj_launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size
 // rounds; released when the solve returns.  On every exit (also an early
 // error return) the owner stream is first made to wait for the side stream,
 // so stream-ordered reuse or freeing of the scratch stays after the last V
-// update.
+// update (owner = null: the caller has joined it, e.g. inside a captured graph).
 struct SideStream {
   cudaStream_t owner = nullptr;
   cudaStream_t sv = nullptr;
@@ -224,7 +227,7 @@ struct SideStream {
     if (!ok) (void)cudaGetLastError();
   }
   ~SideStream() {
-    if (ok && cudaEventRecord(ready, sv) == cudaSuccess) (void)cudaStreamWaitEvent(owner, ready, 0);
+    if (ok && owner && cudaEventRecord(ready, sv) == cudaSuccess) (void)cudaStreamWaitEvent(owner, ready, 0);
     if (done[1]) cudaEventDestroy(done[1]);
     if (done[0]) cudaEventDestroy(done[0]);
     if (ready) cudaEventDestroy(ready);

@@ -20,6 +20,8 @@
 // touched once or twice per round instead of once per pair step.  off(A32) is
 // reduced after each sweep; stop at off(A32) <= tol32 or the sweep cap.
 #include <memory>
+#include <mutex>
+#include <vector>
 #include <cuda_fp16.h>
 #include <stdlib.h>
 
@@ -220,10 +222,11 @@ MPJ_DEV void fma2(unsigned long long& d, unsigned long long a, unsigned long lon
 // each of the block pairs a = 4 gx .. 4 gx + 3.  In exact arithmetic this is
 // A <- U~^T A U~ (the second step reads B only in tiles (Q, a), Q < a, the
 // ones the first formed).  128 threads: the tile's 128 x 32 values of X_Q and
-// U_Q in shared memory, then thread t forms the 4 x 8 block of tile rows
-// 4 (t mod 32) .. +3 and columns 8 (t / 32) .. +7: per k one float4 of X (four
-// shared-memory wavefronts per warp) and two broadcast float4 of U_Q feed 32
-// FMAs, so the FP32 pipe, not shared memory, sets the pace.
+// U_Q in shared memory, then warp w forms the 32 x 32 block of tile rows
+// 32 w .. +31 (block pair a0 + w) and lane (g, h) = (t mod 8, t / 8 mod 4) the
+// 4 x 8 block of rows 32 w + 4 g .. +3 and columns 8 h .. +7: per k one float4
+// of X (8 distinct in a warp: one shared-memory wavefront) and two float4 of
+// U_Q (4 distinct: one wavefront each) feed 32 FMAs.
 enum { R32_ALL = 0, R32_FIRST = 1, R32_SECOND = 2 };
 constexpr int RT = 128;
 constexpr int XLD = 132;  // padded row length of the X tile (k-major), 16-byte aligned rows
@@ -270,8 +273,8 @@ __global__ void __launch_bounds__(RT) rmul32(const float* X, float* Y, int N, in
     }
   }
   __syncthreads();
-  const int r0 = 4 * (tid & 31), c0 = 8 * (tid >> 5);
-  const int a = a0 + (r0 >> 5);  // the pair of this thread's four rows
+  const int r0 = 32 * (tid >> 5) + 4 * (tid & 7), c0 = 8 * ((tid >> 3) & 3);
+  const int a = a0 + (r0 >> 5);  // the pair of this thread's four rows (one per warp)
   if (a >= npairs) return;
   if (tri == R32_FIRST && a >= Q) return;
   if (tri == R32_SECOND && a < Q) return;
@@ -376,21 +379,172 @@ static int stage1_tensor_cores() {
   return env;
 }
 
+
 cudaError_t mpj_sumsq32(const float* A, int lda, int n, double* partial, double* out, cudaStream_t s);
+
+
+namespace {
+// One stage-1 sweep (nb - 1 block rounds) enqueued on stream s.  V <- V U~ of
+// round R runs on the side stream (when given), overlapping round R + 1's
+// subproblems; the S/U sets alternate between rounds, round R + 2's
+// subproblems wait for round R's V update before overwriting its set, and
+// the side stream is joined into s at the end of the sweep.
+struct Stage1Bufs {
+  int N, nb;
+  float *A32, *V32, *Sb[2], *Ub[2], *Bt;
+  unsigned* tflag;
+  bool half;
+  int tc;
+};
+
+cudaError_t stage1_sweep(const Stage1Bufs& b, cudaStream_t s, SideStream* side) {
+  const int N = b.N, nb = b.nb, npairs = nb / 2;
+  const dim3 g32((npairs + 3) / 4, npairs);
+  bool vpending[2] = {false, false};
+  cudaError_t e = cudaSuccess;
+#define S1_TRY(x)                    \
+  do {                               \
+    e = (x);                         \
+    if (e != cudaSuccess) return e;  \
+  } while (0)
+  for (int R = 0; R < nb - 1; ++R) {
+    const int par = R & 1;
+    float* Sbuf = b.Sb[par];
+    float* Ubuf = b.Ub[par];
+    if (side && vpending[par]) S1_TRY(cudaStreamWaitEvent(s, side->done[par], 0));
+    S1_TRY(mpj_launch_pdl(solve32, dim3(npairs), dim3(S32_THREADS), 0, s, (const float*)b.A32, N, nb, R, Sbuf, Ubuf,
+                          b.half));
+    // V <- V U~
+    if (side) {
+      S1_TRY(cudaEventRecord(side->ready, s));
+      S1_TRY(cudaStreamWaitEvent(side->sv, side->ready, 0));
+      S1_TRY(mpj_launch_pdl(rmul32, g32, dim3(RT), 0, side->sv, (const float*)b.V32, b.V32, N, nb, R,
+                            (const float*)Sbuf, (const float*)Ubuf, (int)R32_ALL, b.half));
+      S1_TRY(cudaEventRecord(side->done[par], side->sv));
+      vpending[par] = true;
+    } else {
+      S1_TRY(mpj_launch_pdl(rmul32, g32, dim3(RT), 0, s, (const float*)b.V32, b.V32, N, nb, R, (const float*)Sbuf,
+                            (const float*)Ubuf, (int)R32_ALL, b.half));
+    }
+    if (b.tc == 1) {
+      // A' = U^T A U = (A U)^T U (A symmetric): B^T = (A U)^T, then
+      // A' = (B^T)(:, I_q) U_q on the tensor cores; V U on the FP32 pipe
+      S1_TRY(mpj_tc_panel(N, nb, R, Ubuf, b.A32, b.Bt, 1, nullptr, nullptr, b.tflag, s));
+      S1_TRY(mpj_tc_panel(N, nb, R, Ubuf, b.Bt, b.A32, 0, nullptr, nullptr, b.tflag, s));
+    } else {
+      // B = A U~ (tiles a < Q, stored transposed), A = B^T U~ (tiles a > Q, mirrored; S on the diagonal)
+      S1_TRY(mpj_launch_pdl(rmul32, g32, dim3(RT), 0, s, (const float*)b.A32, b.Bt, N, nb, R, (const float*)Sbuf,
+                            (const float*)Ubuf, (int)R32_FIRST, b.half));
+      S1_TRY(mpj_launch_pdl(rmul32, g32, dim3(RT), 0, s, (const float*)b.Bt, b.A32, N, nb, R, (const float*)Sbuf,
+                            (const float*)Ubuf, (int)R32_SECOND, b.half));
+    }
+  }
+  if (side)
+    for (int par = 0; par < 2; ++par)
+      if (vpending[par]) S1_TRY(cudaStreamWaitEvent(s, side->done[par], 0));
+#undef S1_TRY
+  return cudaGetLastError();
+}
+
+// A sweep captured once as a CUDA graph (the fork to the side stream and the
+// dependent launches become graph edges) and replayed for every sweep.  The
+// kernels' arguments are the workspace addresses, so an executable graph is
+// kept per (device, workspace, N, precision, update engine) and reused by
+// later calls with the same workspace.
+struct SweepGraph {
+  int dev, N, tc;
+  bool half, side;
+  void* work;
+  cudaGraphExec_t exec;
+  long long launches;  // kernels in one sweep
+};
+std::mutex g_sweep_mu;
+std::vector<SweepGraph> g_sweeps;
+constexpr size_t kMaxSweepGraphs = 4;
+
+bool sweep_graphs_enabled() {
+  static int env = -1;
+  if (env < 0) {
+    const char* e = getenv("MPJ_STAGE1_GRAPH");
+    env = (e && e[0] == '0') ? 0 : 1;
+  }
+  return env == 1;
+}
+
+// The executable graph of one sweep for these buffers (captured on first use),
+// or null if capture is not possible (the sweep is then enqueued directly).
+const SweepGraph* sweep_graph(const Stage1Bufs& b, void* work, bool use_side) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return nullptr;
+  }
+  std::lock_guard<std::mutex> lock(g_sweep_mu);
+  for (const SweepGraph& g : g_sweeps)
+    if (g.dev == dev && g.work == work && g.N == b.N && g.half == b.half && g.tc == b.tc && g.side == use_side)
+      return &g;
+  cudaStream_t cap = nullptr;
+  if (cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return nullptr;
+  }
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  cudaError_t e = cudaSuccess;
+  const long long before = mpj_kernel_launches();
+  {
+    std::unique_ptr<SideStream> side;
+    if (use_side) {
+      side.reset(new SideStream(cap));
+      if (!side->ok) e = cudaErrorUnknown;
+      side->owner = nullptr;  // joined inside the captured sweep
+    }
+    if (e == cudaSuccess) e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+      const cudaError_t eq = stage1_sweep(b, cap, side.get());
+      e = cudaStreamEndCapture(cap, &graph);
+      if (eq != cudaSuccess) e = eq;
+    }
+  }
+  const long long per = mpj_kernel_launches() - before;
+  mpj_count_launches(-per);  // captured, not launched
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
+  if (graph) cudaGraphDestroy(graph);
+  cudaStreamDestroy(cap);
+  if (e != cudaSuccess) {
+    (void)cudaGetLastError();
+    if (exec) cudaGraphExecDestroy(exec);
+    return nullptr;
+  }
+  if (g_sweeps.size() >= kMaxSweepGraphs) {
+    cudaGraphExecDestroy(g_sweeps.front().exec);
+    g_sweeps.erase(g_sweeps.begin());
+  }
+  g_sweeps.push_back(SweepGraph{dev, b.N, b.tc, b.half, use_side, work, exec, per});
+  return &g_sweeps.back();
+}
+}  // namespace
 
 int mpj_stage1_run(int n, const double* A, int lda, double* Ql, int ldq, double tol32, int max_sweeps, int* sweeps_out,
                    double* off_out, void* work, double* partial, double* dscal, cudaStream_t s, bool half) {
-  const int N = mpj_stage1_padded(n);
-  const int nb = N / BS;
-  float* A32 = (float*)work;
-  float* V32 = A32 + (size_t)N * N;
+  Stage1Bufs b;
+  b.N = mpj_stage1_padded(n);
+  b.nb = b.N / BS;
+  const int N = b.N, nb = b.nb;
+  b.A32 = (float*)work;
+  b.V32 = b.A32 + (size_t)N * N;
   const size_t pset = (size_t)(nb / 2) * W2 * W2;
-  float* Sb[2] = {V32 + (size_t)N * N, V32 + (size_t)N * N + pset};
-  float* Ub[2] = {Sb[1] + pset, Sb[1] + 2 * pset};
-  float* Bt = Ub[1] + pset;
-  unsigned* tflag = (unsigned*)(Bt + (size_t)N * N);
-  MPJ_CUDA_TRY(cudaMemsetAsync(tflag, 0, sizeof(unsigned), s));
-  const int tc = stage1_tensor_cores() && !half;
+  b.Sb[0] = b.V32 + (size_t)N * N;
+  b.Sb[1] = b.Sb[0] + pset;
+  b.Ub[0] = b.Sb[1] + pset;
+  b.Ub[1] = b.Ub[0] + pset;
+  b.Bt = b.Ub[1] + pset;
+  b.tflag = (unsigned*)(b.Bt + (size_t)N * N);
+  b.half = half;
+  b.tc = stage1_tensor_cores() && !half;
+  float* A32 = b.A32;
+  float* V32 = b.V32;
+  MPJ_CUDA_TRY(cudaMemsetAsync(b.tflag, 0, sizeof(unsigned), s));
   init32<<<1024, 256, 0, s>>>(A, lda, n, N, A32, V32, half);
   mpj_count_launch();
   MPJ_CUDA_TRY(cudaGetLastError());
@@ -400,67 +554,33 @@ int mpj_stage1_run(int n, const double* A, int lda, double* Ql, int ldq, double 
   MPJ_CUDA_TRY(cudaStreamSynchronize(s));
   double off = sqrt(off2);
   int sweeps = 0, status = MPJ_OK;
-  const int npairs = nb / 2;
-  const dim3 g32((npairs + 3) / 4, npairs);
-  // V <- V U~ of round R runs on a side stream, overlapping round R + 1's
-  // subproblems; the S/U sets alternate between rounds, and round R + 2's
-  // subproblems wait for round R's V update before overwriting its set.
-  // The side stream is joined before V is read (and on every return).
+  const bool use_side = mpj_v_overlap_enabled() && nb / 2 >= 8;
+  const SweepGraph* graph = nullptr;
   std::unique_ptr<SideStream> side;
-  if (mpj_v_overlap_enabled() && npairs >= 8) {
-    side.reset(new SideStream(s));
-    if (!side->ok) side.reset();
-  }
-  bool vpending[2] = {false, false};
   while (off > tol32) {
     if (sweeps >= max_sweeps) {
       status = MPJ_NOT_CONVERGED;
       break;
     }
-    for (int R = 0; R < nb - 1; ++R) {
-      const int par = R & 1;
-      float* Sbuf = Sb[par];
-      float* Ubuf = Ub[par];
-      if (side && vpending[par]) MPJ_CUDA_TRY(cudaStreamWaitEvent(s, side->done[par], 0));
-      MPJ_CUDA_TRY(mpj_launch_pdl(solve32, dim3(npairs), dim3(S32_THREADS), 0, s, A32, N, nb, R, Sbuf, Ubuf, half));
-      // V <- V U~
-      if (side) {
-        MPJ_CUDA_TRY(cudaEventRecord(side->ready, s));
-        MPJ_CUDA_TRY(cudaStreamWaitEvent(side->sv, side->ready, 0));
-        MPJ_CUDA_TRY(mpj_launch_pdl(rmul32, g32, dim3(RT), 0, side->sv, (const float*)V32, V32, N, nb, R,
-                                    (const float*)Sbuf, (const float*)Ubuf, (int)R32_ALL, half));
-        MPJ_CUDA_TRY(cudaEventRecord(side->done[par], side->sv));
-        vpending[par] = true;
-      } else {
-        MPJ_CUDA_TRY(mpj_launch_pdl(rmul32, g32, dim3(RT), 0, s, (const float*)V32, V32, N, nb, R,
-                                    (const float*)Sbuf, (const float*)Ubuf, (int)R32_ALL, half));
+    if (sweeps == 0 && sweep_graphs_enabled()) graph = sweep_graph(b, work, use_side);
+    if (graph) {
+      MPJ_CUDA_TRY(cudaGraphLaunch(graph->exec, s));
+      mpj_count_launches(graph->launches);
+    } else {
+      if (use_side && !side) {
+        side.reset(new SideStream(s));
+        if (!side->ok) side.reset();
       }
-      if (tc == 1) {
-        // A' = U^T A U = (A U)^T U (A symmetric): B^T = (A U)^T, then
-        // A' = (B^T)(:, I_q) U_q on the tensor cores; V U on the FP32 pipe
-        MPJ_CUDA_TRY(mpj_tc_panel(N, nb, R, Ubuf, A32, Bt, 1, nullptr, nullptr, tflag, s));
-        MPJ_CUDA_TRY(mpj_tc_panel(N, nb, R, Ubuf, Bt, A32, 0, nullptr, nullptr, tflag, s));
-      } else {
-        // B = A U~ (tiles a < Q, stored transposed), A = B^T U~ (tiles a > Q, mirrored; S on the diagonal)
-        MPJ_CUDA_TRY(mpj_launch_pdl(rmul32, g32, dim3(RT), 0, s, (const float*)A32, Bt, N, nb, R,
-                                    (const float*)Sbuf, (const float*)Ubuf, (int)R32_FIRST, half));
-        MPJ_CUDA_TRY(mpj_launch_pdl(rmul32, g32, dim3(RT), 0, s, (const float*)Bt, A32, N, nb, R,
-                                    (const float*)Sbuf, (const float*)Ubuf, (int)R32_SECOND, half));
-      }
+      MPJ_CUDA_TRY(stage1_sweep(b, s, side.get()));
     }
-    MPJ_CUDA_TRY(cudaGetLastError());
     ++sweeps;
     MPJ_CUDA_TRY(mpj_sumsq32(A32, N, N, partial, dscal, s));
     unsigned tf = 0;
     MPJ_CUDA_TRY(cudaMemcpyAsync(&off2, dscal, sizeof(double), cudaMemcpyDeviceToHost, s));
-    MPJ_CUDA_TRY(cudaMemcpyAsync(&tf, tflag, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+    MPJ_CUDA_TRY(cudaMemcpyAsync(&tf, b.tflag, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
     MPJ_CUDA_TRY(cudaStreamSynchronize(s));
     if (tf & MPJ_FLAG_TIMEOUT) return MPJ_ETIMEOUT;
     off = sqrt(off2);
-  }
-  if (side) {
-    for (int par = 0; par < 2; ++par)
-      if (vpending[par]) MPJ_CUDA_TRY(cudaStreamWaitEvent(s, side->done[par], 0));
   }
   widen<<<1024, 256, 0, s>>>(V32, N, n, Ql, ldq);
   mpj_count_launch();

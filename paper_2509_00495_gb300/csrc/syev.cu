@@ -33,6 +33,7 @@ static std::atomic<long long> g_launches{0};
 static std::atomic<long long> g_allocs{0};
 
 void mpj_count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+void mpj_count_launches(long long k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
 void mpj_count_alloc() { g_allocs.fetch_add(1, std::memory_order_relaxed); }
 
 void mpj_set_cuda_error(cudaError_t e, const char* what, int line) {
