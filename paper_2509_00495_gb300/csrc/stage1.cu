@@ -14,11 +14,11 @@
 // sets, so applying them to the rest of the matrix afterwards as products
 //   A[P,Q] <- U_P^T A[P,Q] U_Q,   V[:,Q] <- V[:,Q] U_Q
 // (P, Q = index sets of block pairs) gives the same iterates as applying them
-// one by one.  Each round is the subproblem solves and three block-diagonal
-// right multiplications (FP32 FMA, rmul32): V U~, B = A U~ and A = B^T U~,
-// each restricted to the tiles the next step needs, so that A32 and V32 are
-// touched once or twice per round instead of once per pair step.  off(A32) is
-// reduced after each sweep; stop at off(A32) <= tol32 or the sweep cap.
+// one by one.  Each round is the subproblem solves and two block products
+// (FP32 FMA, rmul32): V <- V U~ and A <- U~^T A U~ (the lower tiles, each
+// formed once and mirrored), so that A32 and V32 are touched once per round
+// instead of once per pair step.  off(A32) is reduced after each sweep; stop
+// at off(A32) <= tol32 or the sweep cap.
 #include <memory>
 #include <mutex>
 #include <vector>
@@ -213,55 +213,96 @@ MPJ_DEV void fma2(unsigned long long& d, unsigned long long a, unsigned long lon
 }
 
 // ---------------------------------------------------------------- block update
-// The round's rotations applied to the rest of A32 and to V32 as three
-// block-diagonal right multiplications Y[:, g_Q(c)] = X_Q U_Q (FP32 FMA, K = 32):
-//   V <- V U~ (every tile),  B = A U~ (tiles a < Q, B stored transposed),
-//   A = B^T U~ (tiles a > Q, read as columns of the stored B^T, written to
-//   both triangles; the diagonal tiles a = Q are the solved subproblems S),
-// over tiles (a, Q): block pair Q and the 128 rows that are the 32 indices of
-// each of the block pairs a = 4 gx .. 4 gx + 3.  In exact arithmetic this is
-// A <- U~^T A U~ (the second step reads B only in tiles (Q, a), Q < a, the
-// ones the first formed).  128 threads: the tile's 128 x 32 values of X_Q and
-// U_Q in shared memory, then warp w forms the 32 x 32 block of tile rows
-// 32 w .. +31 (block pair a0 + w) and lane (g, h) = (t mod 8, t / 8 mod 4) the
-// 4 x 8 block of rows 32 w + 4 g .. +3 and columns 8 h .. +7: per k one float4
-// of X (8 distinct in a warp: one shared-memory wavefront) and two float4 of
-// U_Q (4 distinct: one wavefront each) feed 32 FMAs.
-enum { R32_ALL = 0, R32_FIRST = 1, R32_SECOND = 2 };
+enum { R32_ALL = 0, R32_BOTH = 1 };
 constexpr int RT = 128;
 constexpr int XLD = 132;  // padded row length of the X tile (k-major), 16-byte aligned rows
 constexpr int ULD = 40;   // padded row length of U_Q, 16-byte aligned rows
 
-__global__ void __launch_bounds__(RT) rmul32(const float* X, float* Y, int N, int nb, int R,
-                                             const float* __restrict__ Sbuf, const float* __restrict__ Ubuf, int tri,
-                                             bool hq) {
-  __shared__ __align__(16) float Xs[W2][XLD];  // Xs[k][r] = X_Q(r, k)
-  __shared__ __align__(16) float Us[W2][ULD];  // Us[k][c] = U_Q(k, c)
-  const int tid = threadIdx.x;
-  const int Q = blockIdx.y, gx = blockIdx.x, npairs = nb / 2;
-  const int a0 = 4 * gx, a1 = min(4 * gx + 3, npairs - 1);
-  pdl_wait();
-  if ((tri == R32_FIRST && a0 >= Q) || (tri == R32_SECOND && a1 < Q)) return;
-  int IQ, JQ;
-  block_pair(nb, R, Q, IQ, JQ);
-  const float* Uq = Ubuf + (size_t)Q * W2 * W2;  // column-major 32 x 32: U(k, c) at Uq[k + 32 c]
+// The 32 x 32 product of one warp: acc(4 g + i, 8 h + j) = sum_k L(k, 4 g + i) R(k, 8 h + j)
+// for lane (g, h) = (lane mod 8, lane / 8), L and R k-major in shared memory
+// (row stride LDL, LDR floats); packed FP32 pairs, each half rounded as fmaf.
+template <int LDL, int LDR>
+MPJ_DEV void warp_mm32(const float* L, const float* R, int g, int h, float acc[4][8]) {
+  unsigned long long acc2[4][4];
 #pragma unroll
-  for (int it = 0; it < W2 * W2 / (4 * RT); ++it) {
-    const int e = 4 * (tid + it * RT), k = e % W2, c = e / W2;
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int jp = 0; jp < 4; ++jp) acc2[i][jp] = 0ULL;
+#pragma unroll 4
+  for (int k = 0; k < W2; ++k) {
+    const float4 x = *reinterpret_cast<const float4*>(L + k * LDL + 4 * g);
+    const float4 u0 = *reinterpret_cast<const float4*>(R + k * LDR + 8 * h);
+    const float4 u1 = *reinterpret_cast<const float4*>(R + k * LDR + 8 * h + 4);
+    const float xa[4] = {x.x, x.y, x.z, x.w};
+    const unsigned long long up[4] = {pk2(u0.x, u0.y), pk2(u0.z, u0.w), pk2(u1.x, u1.y), pk2(u1.z, u1.w)};
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const unsigned long long xx = pk2(xa[i], xa[i]);
+#pragma unroll
+      for (int jp = 0; jp < 4; ++jp) fma2(acc2[i][jp], xx, up[jp]);
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int jp = 0; jp < 4; ++jp) unpk2(acc2[i][jp], acc[i][2 * jp], acc[i][2 * jp + 1]);
+}
+
+// U(k, c) of block pair P (column-major 32 x 32 in Ubuf) into Us[k][c]
+MPJ_DEV void load_u(const float* __restrict__ Ubuf, int P, float (*Us)[ULD], int t, int nt) {
+  const float* Uq = Ubuf + (size_t)P * W2 * W2;
+  for (int e = 4 * t; e < W2 * W2; e += 4 * nt) {
+    const int k = e % W2, c = e / W2;
     const float4 v = *reinterpret_cast<const float4*>(Uq + e);
     Us[k][c] = v.x;
     Us[k + 1][c] = v.y;
     Us[k + 2][c] = v.z;
     Us[k + 3][c] = v.w;
   }
+}
+
+// The round's rotations applied to the rest of A32 and to V32 as block-diagonal
+// right multiplications Y[:, g_Q(c)] = X_Q U_Q (FP32 FMA, K = 32) over tiles
+// (a, Q): block pair Q and the 128 rows that are the 32 indices of each of
+// the block pairs a = 4 gx .. 4 gx + 3.  Modes:
+//   R32_ALL    V <- V U~ (every tile, in place);
+//   R32_BOTH   A <- U~^T A U~ in one pass, in place: tile (a, Q), a > Q, gets
+//              U_a^T (A[P_a, Q] U_Q) (the second product on the first one's
+//              result in shared memory), written to both triangles; the
+//              diagonal tiles a = Q are the solved subproblems S.  The tiles
+//              read (a > Q) are only those their own CTA writes, the mirrors
+//              (Q, a) are read by no CTA.
+// 128 threads: the tile's 128 x 32 values of X_Q and U_Q in shared memory,
+// then warp w forms the 32 x 32 block of tile rows 32 w .. +31 (block pair
+// a0 + w) and lane (g, h) = (t mod 8, t / 8 mod 4) the 4 x 8 block of rows
+// 32 w + 4 g .. +3 and columns 8 h .. +7: per k one float4 of X (8 distinct
+// in a warp: one shared-memory wavefront) and two float4 of U_Q (4 distinct:
+// one wavefront each) feed 32 FMAs.
+template <int TRI>
+__global__ void __launch_bounds__(RT) rmul32(const float* X, float* Y, int N, int nb, int R,
+                                             const float* __restrict__ Sbuf, const float* __restrict__ Ubuf, bool hq) {
+  __shared__ __align__(16) float Xs[W2][XLD];  // Xs[k][r] = X_Q(r, k); R32_BOTH: then T = X_Q U_Q per warp
+  __shared__ __align__(16) float Us[W2][ULD];  // Us[k][c] = U_Q(k, c)
+  __shared__ __align__(16) float Ua[TRI == R32_BOTH ? 4 : 1][W2][ULD];  // U_a of each warp's pair
+  const int tid = threadIdx.x;
+  const int Q = blockIdx.y, gx = blockIdx.x, npairs = nb / 2;
+  const int a0 = 4 * gx, a1 = min(4 * gx + 3, npairs - 1);
+  pdl_wait();
+  if (TRI == R32_BOTH && a1 < Q) return;
+  int IQ, JQ;
+  block_pair(nb, R, Q, IQ, JQ);
+  load_u(Ubuf, Q, Us, tid, RT);
+  const int warp = tid >> 5, lane = tid & 31;
+  const int a = a0 + warp;  // this warp's block pair
+  if (TRI == R32_BOTH && a < npairs && a > Q) load_u(Ubuf, a, Ua[warp], lane, 32);
   {
     // X_Q(r, k) = X[g_Q(k) N + row(r)]; thread t: tile rows 4 (t mod 32) .. +3
     // (consecutive rows of one block), contraction indices k = t / 32 + 4 i
-    const int rq = tid & 31, a = a0 + (rq >> 3);
+    const int rq = tid & 31, ar = a0 + (rq >> 3);
     int row = -1;
-    if (a < npairs) {
+    if (ar < npairs && (TRI != R32_BOTH || ar > Q)) {
       int I, J;
-      block_pair(nb, R, a, I, J);
+      block_pair(nb, R, ar, I, J);
       row = gidx(I, J, (4 * rq) & 31);
     }
 #pragma unroll
@@ -273,73 +314,49 @@ __global__ void __launch_bounds__(RT) rmul32(const float* X, float* Y, int N, in
     }
   }
   __syncthreads();
-  const int r0 = 32 * (tid >> 5) + 4 * (tid & 7), c0 = 8 * ((tid >> 3) & 3);
-  const int a = a0 + (r0 >> 5);  // the pair of this thread's four rows (one per warp)
+  const int g = lane & 7, h = lane >> 3;
+  const int c0 = 8 * h;
   if (a >= npairs) return;
-  if (tri == R32_FIRST && a >= Q) return;
-  if (tri == R32_SECOND && a < Q) return;
+  if (TRI == R32_BOTH && a < Q) return;
   int I, J;
   block_pair(nb, R, a, I, J);
-  const int row0 = gidx(I, J, r0 & 31);  // rows row0 .. row0 + 3 (one block)
-  const int col0 = gidx(IQ, JQ, c0);     // columns col0 .. col0 + 7 (one block)
-  if (tri == R32_SECOND && a == Q) {
+  const int row0 = gidx(I, J, 4 * g);  // rows row0 .. row0 + 3 (one block)
+  const int col0 = gidx(IQ, JQ, c0);   // columns col0 .. col0 + 7 (one block)
+  if (TRI == R32_BOTH && a == Q) {
     // the diagonal tile: the solved subproblem
     const float* Sq = Sbuf + (size_t)Q * W2 * W2;
 #pragma unroll
     for (int cc = 0; cc < 8; ++cc) {
-      const float4 o = *reinterpret_cast<const float4*>(Sq + (r0 & 31) + W2 * (c0 + cc));
+      const float4 o = *reinterpret_cast<const float4*>(Sq + 4 * g + W2 * (c0 + cc));
       *reinterpret_cast<float4*>(Y + (size_t)(col0 + cc) * N + row0) = o;
     }
     return;
   }
-  // packed FP32 pairs: one fma.rn.f32x2 forms two of the thread's FMAs
-  // (columns 2jp, 2jp + 1 of row i), each rounded as fmaf would
-  unsigned long long acc2[4][4];
-#pragma unroll
-  for (int i = 0; i < 4; ++i)
-#pragma unroll
-    for (int jp = 0; jp < 4; ++jp) acc2[i][jp] = 0ULL;
-#pragma unroll 4
-  for (int k = 0; k < W2; ++k) {
-    const float4 x = *reinterpret_cast<const float4*>(&Xs[k][r0]);
-    const float4 u0 = *reinterpret_cast<const float4*>(&Us[k][c0]);
-    const float4 u1 = *reinterpret_cast<const float4*>(&Us[k][c0 + 4]);
-    const float xa[4] = {x.x, x.y, x.z, x.w};
-    const unsigned long long up[4] = {pk2(u0.x, u0.y), pk2(u0.z, u0.w), pk2(u1.x, u1.y), pk2(u1.z, u1.w)};
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const unsigned long long xx = pk2(xa[i], xa[i]);
-#pragma unroll
-      for (int jp = 0; jp < 4; ++jp) fma2(acc2[i][jp], xx, up[jp]);
-    }
-  }
   float acc[4][8];
-#pragma unroll
-  for (int i = 0; i < 4; ++i)
-#pragma unroll
-    for (int jp = 0; jp < 4; ++jp) unpk2(acc2[i][jp], acc[i][2 * jp], acc[i][2 * jp + 1]);
-  const bool rq = hq && tri != R32_FIRST;
-#pragma unroll
-  for (int i = 0; i < 4; ++i)
-#pragma unroll
-    for (int j = 0; j < 8; ++j) acc[i][j] = qh(acc[i][j], rq);
-  if (tri == R32_FIRST) {
-    // B is stored transposed (B(r, c) at Y[r N + c]), so that the second
-    // product reads its rows of B^T as contiguous columns
+  warp_mm32<XLD, ULD>(&Xs[0][32 * warp], &Us[0][0], g, h, acc);
+  if (TRI == R32_BOTH) {
+    // T = X_Q U_Q over this warp's 32 x 32 block of Xs (T(i, c) at Xs[i][32 w + c]),
+    // then U_a^T T
+    __syncwarp();
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
-      *reinterpret_cast<float4*>(Y + (size_t)(row0 + i) * N + col0) =
+      *reinterpret_cast<float4*>(&Xs[4 * g + i][32 * warp + c0]) =
           make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
-      *reinterpret_cast<float4*>(Y + (size_t)(row0 + i) * N + col0 + 4) =
+      *reinterpret_cast<float4*>(&Xs[4 * g + i][32 * warp + c0 + 4]) =
           make_float4(acc[i][4], acc[i][5], acc[i][6], acc[i][7]);
     }
-    return;
+    __syncwarp();
+    warp_mm32<ULD, XLD>(&Ua[warp][0][0], &Xs[0][32 * warp], g, h, acc);
   }
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 8; ++j) acc[i][j] = qh(acc[i][j], hq);
 #pragma unroll
   for (int j = 0; j < 8; ++j)
     *reinterpret_cast<float4*>(Y + (size_t)(col0 + j) * N + row0) =
         make_float4(acc[0][j], acc[1][j], acc[2][j], acc[3][j]);
-  if (tri == R32_SECOND) {  // the mirror: rows col0 .. +7 of columns row0 .. +3
+  if (TRI == R32_BOTH) {  // the mirror: rows col0 .. +7 of columns row0 .. +3
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
       *reinterpret_cast<float4*>(Y + (size_t)(row0 + i) * N + col0) =
@@ -418,13 +435,13 @@ cudaError_t stage1_sweep(const Stage1Bufs& b, cudaStream_t s, SideStream* side) 
     if (side) {
       S1_TRY(cudaEventRecord(side->ready, s));
       S1_TRY(cudaStreamWaitEvent(side->sv, side->ready, 0));
-      S1_TRY(mpj_launch_pdl(rmul32, g32, dim3(RT), 0, side->sv, (const float*)b.V32, b.V32, N, nb, R,
-                            (const float*)Sbuf, (const float*)Ubuf, (int)R32_ALL, b.half));
+      S1_TRY(mpj_launch_pdl(rmul32<R32_ALL>, g32, dim3(RT), 0, side->sv, (const float*)b.V32, b.V32, N, nb, R,
+                            (const float*)Sbuf, (const float*)Ubuf, b.half));
       S1_TRY(cudaEventRecord(side->done[par], side->sv));
       vpending[par] = true;
     } else {
-      S1_TRY(mpj_launch_pdl(rmul32, g32, dim3(RT), 0, s, (const float*)b.V32, b.V32, N, nb, R, (const float*)Sbuf,
-                            (const float*)Ubuf, (int)R32_ALL, b.half));
+      S1_TRY(mpj_launch_pdl(rmul32<R32_ALL>, g32, dim3(RT), 0, s, (const float*)b.V32, b.V32, N, nb, R,
+                            (const float*)Sbuf, (const float*)Ubuf, b.half));
     }
     if (b.tc == 1) {
       // A' = U^T A U = (A U)^T U (A symmetric): B^T = (A U)^T, then
@@ -432,11 +449,9 @@ cudaError_t stage1_sweep(const Stage1Bufs& b, cudaStream_t s, SideStream* side) 
       S1_TRY(mpj_tc_panel(N, nb, R, Ubuf, b.A32, b.Bt, 1, nullptr, nullptr, b.tflag, s));
       S1_TRY(mpj_tc_panel(N, nb, R, Ubuf, b.Bt, b.A32, 0, nullptr, nullptr, b.tflag, s));
     } else {
-      // B = A U~ (tiles a < Q, stored transposed), A = B^T U~ (tiles a > Q, mirrored; S on the diagonal)
-      S1_TRY(mpj_launch_pdl(rmul32, g32, dim3(RT), 0, s, (const float*)b.A32, b.Bt, N, nb, R, (const float*)Sbuf,
-                            (const float*)Ubuf, (int)R32_FIRST, b.half));
-      S1_TRY(mpj_launch_pdl(rmul32, g32, dim3(RT), 0, s, (const float*)b.Bt, b.A32, N, nb, R, (const float*)Sbuf,
-                            (const float*)Ubuf, (int)R32_SECOND, b.half));
+      // A <- U~^T A U~ in one pass (tiles a > Q, mirrored; S on the diagonal)
+      S1_TRY(mpj_launch_pdl(rmul32<R32_BOTH>, g32, dim3(RT), 0, s, (const float*)b.A32, b.A32, N, nb, R,
+                            (const float*)Sbuf, (const float*)Ubuf, b.half));
     }
   }
   if (side)
