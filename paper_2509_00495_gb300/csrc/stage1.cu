@@ -96,10 +96,13 @@ MPJ_DEV void rec32(int x, int y, float dxx, float dyy, float axy, float skip, Ro
 }
 
 // One CTA per block pair of outer round R: inner round-robin sweep on the
-// 32 x 32 subproblem; writes the rotated subproblem S and the accumulated U.
+// 32 x 32 subproblem; writes the rotated subproblem S (column-major) and the
+// accumulated U (row-major for the FP32 products, column-major, urow false,
+// for the tensor-core panel).
 constexpr int S32_THREADS = 512;
 __global__ void __launch_bounds__(S32_THREADS) solve32(const float* __restrict__ A32, int N, int nb, int R,
-                                               float* __restrict__ Sbuf, float* __restrict__ Ubuf, bool hq) {
+                                               float* __restrict__ Sbuf, float* __restrict__ Ubuf, bool hq,
+                                               bool urow) {
   __shared__ float S[W2][LD];
   __shared__ float U[W2][LD];
   __shared__ RotRec<float> rec[W2 / 2];
@@ -193,7 +196,7 @@ __global__ void __launch_bounds__(S32_THREADS) solve32(const float* __restrict__
     const int e = tid + it * S32_THREADS;
     int li = e % W2, lj = e / W2;
     So[e] = S[li][lj];
-    Uo[e] = U[li][lj];
+    Uo[e] = urow ? U[lj][li] : U[li][lj];
   }
 }
 
@@ -248,16 +251,21 @@ MPJ_DEV void warp_mm32(const float* L, const float* R, int g, int h, float acc[4
     for (int jp = 0; jp < 4; ++jp) unpk2(acc2[i][jp], acc[i][2 * jp], acc[i][2 * jp + 1]);
 }
 
-// U(k, c) of block pair P (column-major 32 x 32 in Ubuf) into Us[k][c]
-MPJ_DEV void load_u(const float* __restrict__ Ubuf, int P, float (*Us)[ULD], int t, int nt) {
+// U(k, c) of block pair P (32 x 32 in Ubuf, row-major, or column-major when
+// ucol) into Us[k][c]
+MPJ_DEV void load_u(const float* __restrict__ Ubuf, int P, float (*Us)[ULD], int t, int nt, bool ucol) {
   const float* Uq = Ubuf + (size_t)P * W2 * W2;
   for (int e = 4 * t; e < W2 * W2; e += 4 * nt) {
-    const int k = e % W2, c = e / W2;
     const float4 v = *reinterpret_cast<const float4*>(Uq + e);
-    Us[k][c] = v.x;
-    Us[k + 1][c] = v.y;
-    Us[k + 2][c] = v.z;
-    Us[k + 3][c] = v.w;
+    if (!ucol) {
+      *reinterpret_cast<float4*>(&Us[e / W2][e % W2]) = v;
+    } else {
+      const int k = e % W2, c = e / W2;
+      Us[k][c] = v.x;
+      Us[k + 1][c] = v.y;
+      Us[k + 2][c] = v.z;
+      Us[k + 3][c] = v.w;
+    }
   }
 }
 
@@ -280,7 +288,8 @@ MPJ_DEV void load_u(const float* __restrict__ Ubuf, int P, float (*Us)[ULD], int
 // one wavefront each) feed 32 FMAs.
 template <int TRI>
 __global__ void __launch_bounds__(RT) rmul32(const float* X, float* Y, int N, int nb, int R,
-                                             const float* __restrict__ Sbuf, const float* __restrict__ Ubuf, bool hq) {
+                                             const float* __restrict__ Sbuf, const float* __restrict__ Ubuf, bool hq,
+                                             bool ucol) {
   __shared__ __align__(16) float Xs[W2][XLD];  // Xs[k][r] = X_Q(r, k); R32_BOTH: then T = X_Q U_Q per warp
   __shared__ __align__(16) float Us[W2][ULD];  // Us[k][c] = U_Q(k, c)
   __shared__ __align__(16) float Ua[TRI == R32_BOTH ? 4 : 1][W2][ULD];  // U_a of each warp's pair
@@ -291,10 +300,10 @@ __global__ void __launch_bounds__(RT) rmul32(const float* X, float* Y, int N, in
   if (TRI == R32_BOTH && a1 < Q) return;
   int IQ, JQ;
   block_pair(nb, R, Q, IQ, JQ);
-  load_u(Ubuf, Q, Us, tid, RT);
+  load_u(Ubuf, Q, Us, tid, RT, ucol);
   const int warp = tid >> 5, lane = tid & 31;
   const int a = a0 + warp;  // this warp's block pair
-  if (TRI == R32_BOTH && a < npairs && a > Q) load_u(Ubuf, a, Ua[warp], lane, 32);
+  if (TRI == R32_BOTH && a < npairs && a > Q) load_u(Ubuf, a, Ua[warp], lane, 32, ucol);
   {
     // X_Q(r, k) = X[g_Q(k) N + row(r)]; thread t: tile rows 4 (t mod 32) .. +3
     // (consecutive rows of one block), contraction indices k = t / 32 + 4 i
@@ -430,18 +439,18 @@ cudaError_t stage1_sweep(const Stage1Bufs& b, cudaStream_t s, SideStream* side) 
     float* Ubuf = b.Ub[par];
     if (side && vpending[par]) S1_TRY(cudaStreamWaitEvent(s, side->done[par], 0));
     S1_TRY(mpj_launch_pdl(solve32, dim3(npairs), dim3(S32_THREADS), 0, s, (const float*)b.A32, N, nb, R, Sbuf, Ubuf,
-                          b.half));
+                          b.half, b.tc != 1));
     // V <- V U~
     if (side) {
       S1_TRY(cudaEventRecord(side->ready, s));
       S1_TRY(cudaStreamWaitEvent(side->sv, side->ready, 0));
       S1_TRY(mpj_launch_pdl(rmul32<R32_ALL>, g32, dim3(RT), 0, side->sv, (const float*)b.V32, b.V32, N, nb, R,
-                            (const float*)Sbuf, (const float*)Ubuf, b.half));
+                            (const float*)Sbuf, (const float*)Ubuf, b.half, b.tc == 1));
       S1_TRY(cudaEventRecord(side->done[par], side->sv));
       vpending[par] = true;
     } else {
       S1_TRY(mpj_launch_pdl(rmul32<R32_ALL>, g32, dim3(RT), 0, s, (const float*)b.V32, b.V32, N, nb, R,
-                            (const float*)Sbuf, (const float*)Ubuf, b.half));
+                            (const float*)Sbuf, (const float*)Ubuf, b.half, b.tc == 1));
     }
     if (b.tc == 1) {
       // A' = U^T A U = (A U)^T U (A symmetric): B^T = (A U)^T, then
@@ -451,7 +460,7 @@ cudaError_t stage1_sweep(const Stage1Bufs& b, cudaStream_t s, SideStream* side) 
     } else {
       // A <- U~^T A U~ in one pass (tiles a > Q, mirrored; S on the diagonal)
       S1_TRY(mpj_launch_pdl(rmul32<R32_BOTH>, g32, dim3(RT), 0, s, (const float*)b.A32, b.A32, N, nb, R,
-                            (const float*)Sbuf, (const float*)Ubuf, b.half));
+                            (const float*)Sbuf, (const float*)Ubuf, b.half, false));
     }
   }
   if (side)

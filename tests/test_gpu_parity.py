@@ -544,6 +544,46 @@ def test_side_stream_overlap_is_bitwise_neutral(tmp_path):
     assert np.array_equal(outs[0], outs[1])
 
 
+_STAGE1_TC_SCRIPT = r"""
+import sys, numpy as np, torch
+sys.path.insert(0, sys.argv[1])
+from paper_2509_00495_gb300 import inputs, mpj
+A, lam = inputs.geo_matrix(300, 1e4, seed=17)
+r = mpj.syev_ex(torch.from_numpy(A).cuda())
+torch.cuda.synchronize()
+np.save(sys.argv[2], np.concatenate([r.W.cpu().numpy()[None, :], r.Q.cpu().numpy()]))
+print(r.status, r.info["sweeps32"], r.info["sweeps64"])
+"""
+
+
+@pytest.mark.gpu
+def test_stage1_tensor_core_option_solve(tmp_path):
+    """The whole mixed solve with the stage-1 A update on the tcgen05 panel
+    (MPJ_STAGE1_TC=1: U column-major for the panel, the V update on the FP32
+    pipe reading the same layout) reaches the FP64 accuracy bounds and the
+    known spectrum, like the default FP32-pipe stage."""
+    import os
+    import subprocess
+    import sys as _sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    script = tmp_path / "run.py"
+    script.write_text(_STAGE1_TC_SCRIPT)
+    out = tmp_path / "wq.npy"
+    env = dict(os.environ, MPJ_STAGE1_TC="1")
+    res = subprocess.run([_sys.executable, str(script), root, str(out)], check=True, env=env, timeout=300,
+                         capture_output=True, text=True)
+    status, sw32, sw64 = (int(x) for x in res.stdout.split()[-3:])
+    assert status == 0 and sw32 >= 1
+    WQ = np.load(out)
+    W, Q = WQ[0], WQ[1:]
+    A, lam = inputs.geo_matrix(300, 1e4, seed=17)
+    nA = np.linalg.norm(A, 2)
+    assert np.abs(W - np.sort(lam)).max() <= 1e-12 * nA
+    be, orF = triple(A, W, Q)
+    assert be <= 4 and orF <= 8, (be, orF)
+    assert sw64 < 10
+
+
 @pytest.mark.gpu
 @pytest.mark.parametrize("m,n,k,ta,tb", [(64, 64, 64, "N", "N"), (130, 70, 300, "N", "N"), (200, 129, 513, "T", "N"),
                                          (96, 200, 256, "N", "T"), (257, 65, 1000, "T", "T")])
