@@ -173,6 +173,59 @@ MPJ_DEV void oz_drain(uint32_t mbar, uint32_t parity) {
       : "r"(taddr))
 
 // ---- slicing ----------------------------------------------------------------
+// The slicing uses integer and FP32 instructions only (an FP64 instruction
+// costs 64 FP32 ones on this GPU).
+
+// |x| as the bit pattern of a non-negative double (ordered like the value)
+MPJ_DEV unsigned long long oz_absbits(double x) {
+  return (unsigned long long)__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFULL;
+}
+
+// The smallest e with max|x| < 2^e from the bit pattern of max|x| (0 for
+// zero): the exponent frexp returns.
+MPJ_DEV int oz_exp_of(unsigned long long b) {
+  if (b == 0) return 0;
+  const int ex = (int)(b >> 52);
+  if (ex > 0) return ex - 1022;
+  return (64 - __clzll((long long)b)) - 1074;  // subnormal
+}
+
+// The 8 slices of x on the grid 2^e (|x| < 2^e) as FP32 bit patterns of
+// small integers (their top 16 bits are the bf16): x = sum_i q_i 2^(e - 7 i) + r
+// with |q_1| <= 128, |q_i| <= 64 (i > 1), |r| <= 2^(e - 57).  Y = |x| 2^(56 - e)
+// rounded to an integer (half up; Y < 2^56), then balanced base-128 digits:
+// adding 64 to each of Y's seven low 7-bit groups (one 64-bit add, carries
+// included) makes group j equal d + 64 for a digit d in [-64, 63] of weight
+// 128^j, and the part above bit 49 the top digit in [0, 128].  A group g
+// becomes a float through the bit pattern of 2^23 + g; one FMA gives
+// sign(x) (g - 64).
+MPJ_DEV void oz_digits(double x, int e, uint32_t q[OZ_S]) {
+  const unsigned long long bits = (unsigned long long)__double_as_longlong(x);
+  const int ex = (int)((bits >> 52) & 0x7FF);
+  const unsigned long long mant = bits & 0xFFFFFFFFFFFFFULL;
+  const unsigned long long M = ex ? (mant | (1ULL << 52)) : mant;
+  const int sh = (ex ? ex : 1) - 1019 - e;  // |x| 2^(56 - e) = M 2^sh, sh <= 3
+  unsigned long long Y;
+  if (sh >= 0)
+    Y = M << sh;
+  else if (sh > -62)
+    Y = (M + (1ULL << (-sh - 1))) >> (-sh);
+  else
+    Y = 0;
+  const unsigned long long T = Y + 0x0001020408102040ULL;  // 64 * (1 + 128 + ... + 128^6)
+  const float sg = (bits >> 63) ? -1.0f : 1.0f;
+  const float c64 = -8388672.0f * sg;  // -(2^23 + 64) sign(x)
+#pragma unroll
+  for (int j = 0; j < 7; ++j) {
+    const uint32_t g = (uint32_t)(T >> (7 * j)) & 127u;
+    q[OZ_S - 1 - j] = __float_as_uint(fmaf(__uint_as_float(0x4B000000u | g), sg, c64));
+  }
+  q[0] = __float_as_uint(fmaf(__uint_as_float(0x4B000000u | (uint32_t)(T >> 49)), sg, -8388608.0f * sg));
+}
+
+// Two FP32 digit patterns packed as two bf16 (a in the low half).
+MPJ_DEV uint32_t oz_pack2(uint32_t a, uint32_t b) { return __byte_perm(a, b, 0x7632); }
+
 // Largest |x(r, k)| per row as the bit pattern of a non-negative double
 // (ordered like the value), combined with atomicMax.  Rows of a column-major
 // matrix (rs == 1): one thread per row over a strip of k, coalesced across rows.
@@ -181,9 +234,9 @@ __global__ void oz_rowmax_cols(const double* __restrict__ X, long long ks, int R
   const int r = blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= R) return;
   const int k0 = blockIdx.y * kstrip, k1 = min(K, k0 + kstrip);
-  double m = 0.0;
-  for (int k = k0; k < k1; ++k) m = fmax(m, fabs(X[r + (long long)k * ks]));
-  if (m > 0.0) atomicMax(mx + r, (unsigned long long)__double_as_longlong(m));
+  unsigned long long m = 0;  // max of the magnitudes' bit patterns (integer compares, no FP64)
+  for (int k = k0; k < k1; ++k) m = max(m, oz_absbits(X[r + (long long)k * ks]));
+  if (m) atomicMax(mx + r, m);
 }
 
 // Rows stored contiguously (or any other stride): one warp per row.
@@ -191,10 +244,10 @@ __global__ void oz_rowmax_warp(const double* __restrict__ X, long long rs, long 
                                unsigned long long* __restrict__ mx) {
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
   if (warp >= R) return;
-  double m = 0.0;
-  for (int k = lane; k < K; k += 32) m = fmax(m, fabs(X[(long long)warp * rs + (long long)k * ks]));
-  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
-  if (lane == 0) mx[warp] = (unsigned long long)__double_as_longlong(m);
+  unsigned long long m = 0;
+  for (int k = lane; k < K; k += 32) m = max(m, oz_absbits(X[(long long)warp * rs + (long long)k * ks]));
+  for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if (lane == 0) mx[warp] = m;
 }
 
 // The 8 slices of 8 consecutive k values of one row per thread, written as
@@ -216,32 +269,25 @@ __global__ void oz_slice(const double* __restrict__ X, long long rs, long long k
       r = (int)(idx / (Kp / 8));
     }
     const int k0 = g * 8;
-    int e = 0;
-    if (r < R) {
-      const double m = __longlong_as_double((long long)mx[r]);
-      if (m > 0.0) frexp(m, &e);  // m = f 2^e, f in [0.5, 1): every |x(r, k)| < 2^e
-    }
+    const int e = r < R ? oz_exp_of(mx[r]) : 0;  // every |x(r, k)| < 2^e
     if (g == 0) exps[r] = e;
-    double y[8];
+    uint32_t d[8][OZ_S];
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
       const int k = k0 + j;
       const double x = (r < R && k < K) ? X[(long long)r * rs + (long long)k * ks] : 0.0;
-      y[j] = ldexp(x, -e);  // |y| < 1, exact
+      oz_digits(x, e, d[j]);
     }
     const long long tile = (long long)(k0 / OZ_KS) * (Rp / 64) + r / 64;
     const long long off = tile * OZ_TILE64 + (kmaj16(r & 63, k0 & 31) >> 1);
 #pragma unroll
     for (int s = 0; s < OZ_S; ++s) {
-      __align__(16) __nv_bfloat16 q8[8];
-#pragma unroll
-      for (int j = 0; j < 8; ++j) {
-        y[j] *= 128.0;
-        const double q = rint(y[j]);
-        y[j] -= q;                           // exact: y and q share the grid of y's last bit
-        q8[j] = __double2bfloat16(q);        // |q| <= 128: exact
-      }
-      *reinterpret_cast<uint4*>(S + s * slice_elems + off) = *reinterpret_cast<const uint4*>(q8);
+      uint4 q;
+      q.x = oz_pack2(d[0][s], d[1][s]);
+      q.y = oz_pack2(d[2][s], d[3][s]);
+      q.z = oz_pack2(d[4][s], d[5][s]);
+      q.w = oz_pack2(d[6][s], d[7][s]);
+      *reinterpret_cast<uint4*>(S + s * slice_elems + off) = q;
     }
   }
 }
