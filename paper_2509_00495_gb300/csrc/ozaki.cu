@@ -305,7 +305,7 @@ __global__ void __maxnreg__(168)
     oz_gemm_kernel(const __nv_bfloat16* __restrict__ SA, const int* __restrict__ ea, int Rpa,
                    const __nv_bfloat16* __restrict__ SB, const int* __restrict__ eb, int Rpb, int Kp, int sub0,
                    int nsub, int m, int n, double alpha, double beta, const double* Cin, int ldcin, double* C,
-                   int ldc, unsigned* gflags) {
+                   int ldc, unsigned* gflags, int lower) {
   extern __shared__ __align__(1024) unsigned char dsm_raw[];
   OzSmem& sm = *reinterpret_cast<OzSmem*>(dsm_raw + ((1024 - (smem_u32(dsm_raw) & 1023)) & 1023));
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -317,6 +317,8 @@ __global__ void __maxnreg__(168)
   const int gsz = min(ntm - first_m, OZ_GROUP_M);
   const int local = id % (OZ_GROUP_M * ntn);
   const int mt = first_m + local % gsz, nt = local / gsz;
+  // lower: only tiles that meet the lower triangle (row >= column) are formed
+  if (lower && mt * OZ_TM + OZ_TM - 1 < nt * OZ_TN) return;
 
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&sm.tmem)),
@@ -526,7 +528,8 @@ cudaError_t mpj_oz_prepare(const double* X, long long rs, long long ks, int R, i
 }
 
 cudaError_t mpj_oz_gemm(const OzOperand& a, const OzOperand& b, int m, int n, double alpha, double beta,
-                        const double* Cin, int ldcin, double* C, int ldc, unsigned* flags, cudaStream_t s) {
+                        const double* Cin, int ldcin, double* C, int ldc, unsigned* flags, cudaStream_t s,
+                        bool lower) {
   if (a.Kp != b.Kp || m > a.R || n > b.R || m < 1 || n < 1) return cudaErrorInvalidValue;
   const size_t smem = sizeof(OzSmem) + 1024;
   cudaError_t e = cudaFuncSetAttribute(oz_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -538,7 +541,7 @@ cudaError_t mpj_oz_gemm(const OzOperand& a, const OzOperand& b, int m, int n, do
     const bool first = sub0 == 0;
     oz_gemm_kernel<<<ntm * ntn, OZ_THREADS, smem, s>>>(a.slices, a.exps, a.Rp, b.slices, b.exps, b.Rp, a.Kp, sub0, ns,
                                                         m, n, alpha, first ? beta : 1.0, first ? Cin : C,
-                                                        first ? ldcin : ldc, C, ldc, flags);
+                                                        first ? ldcin : ldc, C, ldc, flags, lower ? 1 : 0);
     mpj_count_launch();
     e = cudaGetLastError();
     if (e != cudaSuccess) {

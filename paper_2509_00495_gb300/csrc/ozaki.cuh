@@ -29,9 +29,13 @@ cudaError_t mpj_oz_prepare(const double* X, long long rs, long long ks, int R, i
 // C(0:m, 0:n) = alpha op(A) op(B) + beta Cin, op(A) rows from `a` (a.R >= m),
 // op(B) columns from `b` (b.R >= n), a.K == b.K.  Cin may alias C (ignored
 // when beta == 0).  A tensor-core completion wait that runs out sets
-// MPJ_FLAG_TIMEOUT in *flags (device word, may be null).
+// MPJ_FLAG_TIMEOUT in *flags (device word, may be null).  lower: only the
+// 128 x 64 output tiles that meet the lower triangle (row >= column) are
+// formed, the others are left untouched (for a symmetric result whose upper
+// triangle the caller mirrors from the lower one).
 cudaError_t mpj_oz_gemm(const OzOperand& a, const OzOperand& b, int m, int n, double alpha, double beta,
-                        const double* Cin, int ldcin, double* C, int ldc, unsigned* flags, cudaStream_t s);
+                        const double* Cin, int ldcin, double* C, int ldc, unsigned* flags, cudaStream_t s,
+                        bool lower = false);
 
 // Whether the FP64 products of the solver and of the adjoint run on this
 // engine (default) or on the FP64 DMMA kernel (environment MPJ_GEMM_TC=0).

@@ -347,9 +347,12 @@ int ns_steps_run(int n, double** X, double* M, double** Y, int steps, void* fp32
   for (int k = 0; k < steps; ++k) {
     if (tc) {
       OzOperand ox;
+      // X^T X is symmetric: the tiles of its lower triangle, mirrored
       cudaError_t e = mpj_oz_prepare(*X, n, 1, n, n, w.b0, &ox, s);  // column j of X = row j of X^T
-      if (e == cudaSuccess) e = mpj_oz_gemm(ox, ox, n, n, 1.0, 0.0, nullptr, n, M, n, w.flags, s);
+      if (e == cudaSuccess) e = mpj_oz_gemm(ox, ox, n, n, 1.0, 0.0, nullptr, n, M, n, w.flags, s, true);
       if (e != cudaSuccess) return oz_fail(e, "Newton-Schulz X^T X", __LINE__);
+      mirror_lower<<<blocks_for((size_t)n * n), 256, 0, s>>>(M, n, n);
+      mpj_count_launch();
     } else {
       MPJ_CUDA_TRY(mpj_gemm64(true, false, n, n, n, 1.0, *X, n, *X, n, 0.0, nullptr, n, M, n, 1, s));
     }
@@ -390,7 +393,7 @@ int transform_run(int n, const double* A, int lda, const double* Qd, int ldq, do
     if (e == cudaSuccess) e = mpj_oz_prepare(Qd, ldq, 1, n, n, w.b1, &oq, s);      // columns of Qd
     if (e == cudaSuccess) e = mpj_oz_gemm(oa, oq, n, n, 1.0, 0.0, nullptr, n, Y, n, w.flags, s);
     if (e == cudaSuccess) e = mpj_oz_prepare(Y, n, 1, n, n, w.b0, &oy, s);         // columns of A Qd
-    if (e == cudaSuccess) e = mpj_oz_gemm(oq, oy, n, n, 1.0, 0.0, nullptr, n, Ac, ldc, w.flags, s);
+    if (e == cudaSuccess) e = mpj_oz_gemm(oq, oy, n, n, 1.0, 0.0, nullptr, n, Ac, ldc, w.flags, s, true);
     if (e != cudaSuccess) return oz_fail(e, "transform", __LINE__);
     mirror_lower<<<blocks_for((size_t)n * n), 256, 0, s>>>(Ac, ldc, n);
     mpj_count_launch();
