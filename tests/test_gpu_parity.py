@@ -544,6 +544,48 @@ def test_side_stream_overlap_is_bitwise_neutral(tmp_path):
     assert np.array_equal(outs[0], outs[1])
 
 
+_GRAPH_SCRIPT = r"""
+import sys, numpy as np, torch
+sys.path.insert(0, sys.argv[1])
+from paper_2509_00495_gb300 import inputs, mpj
+outs, wss = [], {}
+# sizes and workspaces in turn (each workspace kept alive, so each has its own
+# address): cache hits, misses, and more keys than the cache holds
+# (evictions); the same size again with another workspace
+for n, ws_id in ((300, 0), (520, 1), (300, 0), (300, 2), (700, 3), (420, 4), (520, 1), (300, 0)):
+    A, lam = inputs.geo_matrix(n, 1e4, seed=n + ws_id)
+    if ws_id not in wss:
+        wss[ws_id] = torch.empty(mpj.syev_workspace(n), dtype=torch.uint8, device="cuda")
+    ws = wss[ws_id]
+    r = mpj.syev_ex(torch.from_numpy(A).cuda(), workspace=ws)
+    torch.cuda.synchronize()
+    assert r.status == 0
+    outs.append(np.concatenate([r.W.cpu().numpy(), r.Q.cpu().numpy().ravel()]))
+np.save(sys.argv[2], np.concatenate(outs))
+"""
+
+
+@pytest.mark.gpu
+def test_stage1_sweep_graphs_are_bitwise_neutral(tmp_path):
+    """Stage-1 sweeps replayed from the per-workspace CUDA-graph cache give the
+    same bits as the same sweeps enqueued kernel by kernel
+    (MPJ_STAGE1_GRAPH=0), over a sequence of sizes and workspaces that hits,
+    misses and evicts cache entries."""
+    import os
+    import subprocess
+    import sys as _sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    script = tmp_path / "run.py"
+    script.write_text(_GRAPH_SCRIPT)
+    outs = []
+    for flag in ("1", "0"):
+        out = tmp_path / f"g{flag}.npy"
+        env = dict(os.environ, MPJ_STAGE1_GRAPH=flag)
+        subprocess.run([_sys.executable, str(script), root, str(out)], check=True, env=env, timeout=300)
+        outs.append(np.load(out))
+    assert np.array_equal(outs[0], outs[1])
+
+
 _STAGE1_TC_SCRIPT = r"""
 import sys, numpy as np, torch
 sys.path.insert(0, sys.argv[1])
