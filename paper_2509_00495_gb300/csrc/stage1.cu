@@ -481,9 +481,18 @@ struct SweepGraph {
   void* work;
   cudaGraphExec_t exec;
   long long launches;  // kernels in one sweep
+  ~SweepGraph() {
+    if (exec) cudaGraphExecDestroy(exec);
+  }
 };
+// Shared ownership: an entry evicted by one thread stays valid for a solve
+// that is replaying it on another.  The registry itself is never destroyed
+// (no CUDA calls during static destruction at process exit).
 std::mutex g_sweep_mu;
-std::vector<SweepGraph> g_sweeps;
+std::vector<std::shared_ptr<SweepGraph>>& sweep_registry() {
+  static auto* r = new std::vector<std::shared_ptr<SweepGraph>>();
+  return *r;
+}
 constexpr size_t kMaxSweepGraphs = 4;
 
 bool sweep_graphs_enabled() {
@@ -497,16 +506,17 @@ bool sweep_graphs_enabled() {
 
 // The executable graph of one sweep for these buffers (captured on first use),
 // or null if capture is not possible (the sweep is then enqueued directly).
-const SweepGraph* sweep_graph(const Stage1Bufs& b, void* work, bool use_side) {
+std::shared_ptr<SweepGraph> sweep_graph(const Stage1Bufs& b, void* work, bool use_side) {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) {
     (void)cudaGetLastError();
     return nullptr;
   }
   std::lock_guard<std::mutex> lock(g_sweep_mu);
-  for (const SweepGraph& g : g_sweeps)
-    if (g.dev == dev && g.work == work && g.N == b.N && g.half == b.half && g.tc == b.tc && g.side == use_side)
-      return &g;
+  auto& reg = sweep_registry();
+  for (const auto& g : reg)
+    if (g->dev == dev && g->work == work && g->N == b.N && g->half == b.half && g->tc == b.tc && g->side == use_side)
+      return g;
   cudaStream_t cap = nullptr;
   if (cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking) != cudaSuccess) {
     (void)cudaGetLastError();
@@ -515,7 +525,9 @@ const SweepGraph* sweep_graph(const Stage1Bufs& b, void* work, bool use_side) {
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   cudaError_t e = cudaSuccess;
-  const long long before = mpj_kernel_launches();
+  // kernels of one sweep: per round the subproblems, V U~ and the A update
+  // (one launch, or two tensor-core panels)
+  const long long per = (long long)(b.nb - 1) * (b.tc == 1 ? 4 : 3);
   {
     std::unique_ptr<SideStream> side;
     if (use_side) {
@@ -530,8 +542,7 @@ const SweepGraph* sweep_graph(const Stage1Bufs& b, void* work, bool use_side) {
       if (eq != cudaSuccess) e = eq;
     }
   }
-  const long long per = mpj_kernel_launches() - before;
-  mpj_count_launches(-per);  // captured, not launched
+  if (e == cudaSuccess) mpj_count_launches(-per);  // captured, not launched
   if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
   if (graph) cudaGraphDestroy(graph);
   cudaStreamDestroy(cap);
@@ -540,12 +551,18 @@ const SweepGraph* sweep_graph(const Stage1Bufs& b, void* work, bool use_side) {
     if (exec) cudaGraphExecDestroy(exec);
     return nullptr;
   }
-  if (g_sweeps.size() >= kMaxSweepGraphs) {
-    cudaGraphExecDestroy(g_sweeps.front().exec);
-    g_sweeps.erase(g_sweeps.begin());
-  }
-  g_sweeps.push_back(SweepGraph{dev, b.N, b.tc, b.half, use_side, work, exec, per});
-  return &g_sweeps.back();
+  if (reg.size() >= kMaxSweepGraphs) reg.erase(reg.begin());
+  auto g = std::make_shared<SweepGraph>();
+  g->dev = dev;
+  g->N = b.N;
+  g->tc = b.tc;
+  g->half = b.half;
+  g->side = use_side;
+  g->work = work;
+  g->exec = exec;
+  g->launches = per;
+  reg.push_back(g);
+  return g;
 }
 }  // namespace
 
@@ -579,7 +596,7 @@ int mpj_stage1_run(int n, const double* A, int lda, double* Ql, int ldq, double 
   double off = sqrt(off2);
   int sweeps = 0, status = MPJ_OK;
   const bool use_side = mpj_v_overlap_enabled() && nb / 2 >= 8;
-  const SweepGraph* graph = nullptr;
+  std::shared_ptr<SweepGraph> graph;
   std::unique_ptr<SideStream> side;
   while (off > tol32) {
     if (sweeps >= max_sweeps) {
