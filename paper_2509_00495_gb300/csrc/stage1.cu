@@ -96,13 +96,14 @@ MPJ_DEV void rec32(int x, int y, float dxx, float dyy, float axy, float skip, Ro
 }
 
 // One CTA per block pair of outer round R: inner round-robin sweep on the
-// 32 x 32 subproblem; writes the rotated subproblem S (column-major) and the
+// 32 x 32 subproblem; writes the rotated subproblem S (column-major), the
 // accumulated U (row-major for the FP32 products, column-major, urow false,
-// for the tensor-core panel).
+// for the tensor-core panel) and the set T of its indices that rotated
+// (Mbuf, bit l for local index l): U is the identity outside T x T.
 constexpr int S32_THREADS = 512;
 __global__ void __launch_bounds__(S32_THREADS) solve32(const float* __restrict__ A32, int N, int nb, int R,
                                                float* __restrict__ Sbuf, float* __restrict__ Ubuf, bool hq,
-                                               bool urow) {
+                                               bool urow, unsigned* __restrict__ Mbuf) {
   __shared__ float S[W2][LD];
   __shared__ float U[W2][LD];
   __shared__ RotRec<float> rec[W2 / 2];
@@ -120,6 +121,7 @@ __global__ void __launch_bounds__(S32_THREADS) solve32(const float* __restrict__
   }
   __syncthreads();
   const float skip = hq ? 0x1p-11f : 0x1p-24f;
+  unsigned tmask = 0u;  // thread 0: the indices that rotated so far
   for (int rho = 0; rho < W2 - 1; ++rho) {
     if (tid < W2 / 2) {
       int x, y;
@@ -133,6 +135,8 @@ __global__ void __launch_bounds__(S32_THREADS) solve32(const float* __restrict__
         rr.dy = qh(rr.dy, true);
       }
       rec[tid] = rr;
+      const unsigned bits = rec_rotated(rr.cm1, rr.sig) ? ((1u << x) | (1u << y)) : 0u;
+      tmask |= __reduce_or_sync(0x0000FFFFu, bits);  // the 16 record lanes of warp 0
     }
     __syncthreads();
     {
@@ -198,6 +202,7 @@ __global__ void __launch_bounds__(S32_THREADS) solve32(const float* __restrict__
     So[e] = S[li][lj];
     Uo[e] = urow ? U[lj][li] : U[li][lj];
   }
+  if (tid == 0) Mbuf[slot] = tmask;
 }
 
 
@@ -233,6 +238,36 @@ MPJ_DEV void warp_mm32(const float* L, const float* R, int g, int h, float acc[4
     for (int jp = 0; jp < 4; ++jp) acc2[i][jp] = 0ULL;
 #pragma unroll 4
   for (int k = 0; k < W2; ++k) {
+    const float4 x = *reinterpret_cast<const float4*>(L + k * LDL + 4 * g);
+    const float4 u0 = *reinterpret_cast<const float4*>(R + k * LDR + 8 * h);
+    const float4 u1 = *reinterpret_cast<const float4*>(R + k * LDR + 8 * h + 4);
+    const float xa[4] = {x.x, x.y, x.z, x.w};
+    const unsigned long long up[4] = {pk2(u0.x, u0.y), pk2(u0.z, u0.w), pk2(u1.x, u1.y), pk2(u1.z, u1.w)};
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const unsigned long long xx = pk2(xa[i], xa[i]);
+#pragma unroll
+      for (int jp = 0; jp < 4; ++jp) fma2(acc2[i][jp], xx, up[jp]);
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int jp = 0; jp < 4; ++jp) unpk2(acc2[i][jp], acc[i][2 * jp], acc[i][2 * jp + 1]);
+}
+
+// warp_mm32 with the contraction restricted to the indices k in `mask` (in
+// increasing order: the terms it leaves out are exact zeros, so the sums
+// are those of the full contraction).
+template <int LDL, int LDR>
+MPJ_DEV void warp_mm32_masked(const float* L, const float* R, int g, int h, unsigned mask, float acc[4][8]) {
+  unsigned long long acc2[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int jp = 0; jp < 4; ++jp) acc2[i][jp] = 0ULL;
+  for (unsigned m = mask; m; m &= m - 1) {
+    const int k = __ffs(m) - 1;
     const float4 x = *reinterpret_cast<const float4*>(L + k * LDL + 4 * g);
     const float4 u0 = *reinterpret_cast<const float4*>(R + k * LDR + 8 * h);
     const float4 u1 = *reinterpret_cast<const float4*>(R + k * LDR + 8 * h + 4);
@@ -289,7 +324,7 @@ MPJ_DEV void load_u(const float* __restrict__ Ubuf, int P, float (*Us)[ULD], int
 template <int TRI>
 __global__ void __launch_bounds__(RT) rmul32(const float* X, float* Y, int N, int nb, int R,
                                              const float* __restrict__ Sbuf, const float* __restrict__ Ubuf, bool hq,
-                                             bool ucol) {
+                                             bool ucol, const unsigned* __restrict__ Mbuf) {
   __shared__ __align__(16) float Xs[W2][XLD];  // Xs[k][r] = X_Q(r, k); R32_BOTH: then T = X_Q U_Q per warp
   __shared__ __align__(16) float Us[W2][ULD];  // Us[k][c] = U_Q(k, c)
   __shared__ __align__(16) float Ua[TRI == R32_BOTH ? 4 : 1][W2][ULD];  // U_a of each warp's pair
@@ -298,6 +333,9 @@ __global__ void __launch_bounds__(RT) rmul32(const float* X, float* Y, int N, in
   const int a0 = 4 * gx, a1 = min(4 * gx + 3, npairs - 1);
   pdl_wait();
   if (TRI == R32_BOTH && a1 < Q) return;
+  // the indices of block pair Q that rotated: U_Q is the identity outside them
+  const unsigned mQ = Mbuf[Q];
+  if (TRI == R32_ALL && mQ == 0u) return;  // V U~ leaves these columns as they are
   int IQ, JQ;
   block_pair(nb, R, Q, IQ, JQ);
   load_u(Ubuf, Q, Us, tid, RT, ucol);
@@ -317,6 +355,7 @@ __global__ void __launch_bounds__(RT) rmul32(const float* X, float* Y, int N, in
 #pragma unroll
     for (int i = 0; i < W2 / 4; ++i) {
       const int k = (tid >> 5) + 4 * i;
+      if (TRI == R32_ALL && !((mQ >> k) & 1u)) continue;  // column not read (V U~ contracts over T_Q only)
       const float4 v = row >= 0 ? *reinterpret_cast<const float4*>(X + (size_t)gidx(IQ, JQ, k) * N + row)
                                 : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
       *reinterpret_cast<float4*>(&Xs[k][4 * rq]) = v;
@@ -341,11 +380,26 @@ __global__ void __launch_bounds__(RT) rmul32(const float* X, float* Y, int N, in
     }
     return;
   }
+  const unsigned ma = TRI == R32_BOTH ? Mbuf[a] : 0u;
+  if (TRI == R32_BOTH && mQ == 0u && ma == 0u) return;  // U_a^T A U_Q = A on this tile
+  // a column c outside T_Q: (X U_Q)(:, c) = X(:, c); else the contraction over T_Q
   float acc[4][8];
-  warp_mm32<XLD, ULD>(&Xs[0][32 * warp], &Us[0][0], g, h, acc);
+  if (mQ == 0xFFFFFFFFu) {
+    warp_mm32<XLD, ULD>(&Xs[0][32 * warp], &Us[0][0], g, h, acc);
+  } else {
+    warp_mm32_masked<XLD, ULD>(&Xs[0][32 * warp], &Us[0][0], g, h, mQ, acc);
+    if (TRI == R32_BOTH) {
+#pragma unroll
+      for (int j = 0; j < 8; ++j)
+        if (!((mQ >> (c0 + j)) & 1u)) {
+#pragma unroll
+          for (int i = 0; i < 4; ++i) acc[i][j] = Xs[c0 + j][32 * warp + 4 * g + i];
+        }
+    }
+  }
   if (TRI == R32_BOTH) {
     // T = X_Q U_Q over this warp's 32 x 32 block of Xs (T(i, c) at Xs[i][32 w + c]),
-    // then U_a^T T
+    // then U_a^T T (a row r outside T_a: (U_a^T T)(r, :) = T(r, :))
     __syncwarp();
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
@@ -355,7 +409,17 @@ __global__ void __launch_bounds__(RT) rmul32(const float* X, float* Y, int N, in
           make_float4(acc[i][4], acc[i][5], acc[i][6], acc[i][7]);
     }
     __syncwarp();
-    warp_mm32<ULD, XLD>(&Ua[warp][0][0], &Xs[0][32 * warp], g, h, acc);
+    if (ma == 0xFFFFFFFFu) {
+      warp_mm32<ULD, XLD>(&Ua[warp][0][0], &Xs[0][32 * warp], g, h, acc);
+    } else {
+      warp_mm32_masked<ULD, XLD>(&Ua[warp][0][0], &Xs[0][32 * warp], g, h, ma, acc);
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+        if (!((ma >> (4 * g + i)) & 1u)) {
+#pragma unroll
+          for (int j = 0; j < 8; ++j) acc[i][j] = Xs[4 * g + i][32 * warp + c0 + j];
+        }
+    }
   }
 #pragma unroll
   for (int i = 0; i < 4; ++i)
@@ -363,8 +427,9 @@ __global__ void __launch_bounds__(RT) rmul32(const float* X, float* Y, int N, in
     for (int j = 0; j < 8; ++j) acc[i][j] = qh(acc[i][j], hq);
 #pragma unroll
   for (int j = 0; j < 8; ++j)
-    *reinterpret_cast<float4*>(Y + (size_t)(col0 + j) * N + row0) =
-        make_float4(acc[0][j], acc[1][j], acc[2][j], acc[3][j]);
+    if (TRI == R32_BOTH || ((mQ >> (c0 + j)) & 1u))  // V: only the columns in T_Q change
+      *reinterpret_cast<float4*>(Y + (size_t)(col0 + j) * N + row0) =
+          make_float4(acc[0][j], acc[1][j], acc[2][j], acc[3][j]);
   if (TRI == R32_BOTH) {  // the mirror: rows col0 .. +7 of columns row0 .. +3
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
@@ -380,14 +445,15 @@ __global__ void __launch_bounds__(RT) rmul32(const float* X, float* Y, int N, in
 
 int mpj_stage1_padded(int n) { return ((n + W2 - 1) / W2) * W2; }
 
-// A32, V32, two sets of the per-pair S and U (alternate rounds), a flag word after them (the tensor-core
-// update also keeps the transposed intermediate B^T there).
+// A32, V32, two sets of the per-pair S and U (alternate rounds), the
+// tensor-core update's transposed intermediate B^T, a flag word and two sets
+// of the per-pair rotated-index masks.
 static int stage1_tensor_cores();
 
 size_t mpj_stage1_bytes(int n) {
   size_t N = (size_t)mpj_stage1_padded(n);
   size_t nb = N / BS;
-  return 3 * N * N * sizeof(float) + 4 * (nb / 2) * W2 * W2 * sizeof(float) + 4096;
+  return 3 * N * N * sizeof(float) + 4 * (nb / 2) * W2 * W2 * sizeof(float) + 4096 + 2 * (nb / 2) * sizeof(unsigned);
 }
 
 // MPJ_STAGE1_TC=1 runs the A update of each block round on the tcgen05
@@ -419,6 +485,7 @@ struct Stage1Bufs {
   int N, nb;
   float *A32, *V32, *Sb[2], *Ub[2], *Bt;
   unsigned* tflag;
+  unsigned* Mb[2];  // per-pair rotated-index masks, by round parity
   bool half;
   int tc;
 };
@@ -438,19 +505,20 @@ cudaError_t stage1_sweep(const Stage1Bufs& b, cudaStream_t s, SideStream* side) 
     float* Sbuf = b.Sb[par];
     float* Ubuf = b.Ub[par];
     if (side && vpending[par]) S1_TRY(cudaStreamWaitEvent(s, side->done[par], 0));
+    unsigned* Mbuf = b.Mb[par];
     S1_TRY(mpj_launch_pdl(solve32, dim3(npairs), dim3(S32_THREADS), 0, s, (const float*)b.A32, N, nb, R, Sbuf, Ubuf,
-                          b.half, b.tc != 1));
+                          b.half, b.tc != 1, Mbuf));
     // V <- V U~
     if (side) {
       S1_TRY(cudaEventRecord(side->ready, s));
       S1_TRY(cudaStreamWaitEvent(side->sv, side->ready, 0));
       S1_TRY(mpj_launch_pdl(rmul32<R32_ALL>, g32, dim3(RT), 0, side->sv, (const float*)b.V32, b.V32, N, nb, R,
-                            (const float*)Sbuf, (const float*)Ubuf, b.half, b.tc == 1));
+                            (const float*)Sbuf, (const float*)Ubuf, b.half, b.tc == 1, (const unsigned*)Mbuf));
       S1_TRY(cudaEventRecord(side->done[par], side->sv));
       vpending[par] = true;
     } else {
       S1_TRY(mpj_launch_pdl(rmul32<R32_ALL>, g32, dim3(RT), 0, s, (const float*)b.V32, b.V32, N, nb, R,
-                            (const float*)Sbuf, (const float*)Ubuf, b.half, b.tc == 1));
+                            (const float*)Sbuf, (const float*)Ubuf, b.half, b.tc == 1, (const unsigned*)Mbuf));
     }
     if (b.tc == 1) {
       // A' = U^T A U = (A U)^T U (A symmetric): B^T = (A U)^T, then
@@ -460,7 +528,7 @@ cudaError_t stage1_sweep(const Stage1Bufs& b, cudaStream_t s, SideStream* side) 
     } else {
       // A <- U~^T A U~ in one pass (tiles a > Q, mirrored; S on the diagonal)
       S1_TRY(mpj_launch_pdl(rmul32<R32_BOTH>, g32, dim3(RT), 0, s, (const float*)b.A32, b.A32, N, nb, R,
-                            (const float*)Sbuf, (const float*)Ubuf, b.half, false));
+                            (const float*)Sbuf, (const float*)Ubuf, b.half, false, (const unsigned*)Mbuf));
     }
   }
   if (side)
@@ -581,6 +649,8 @@ int mpj_stage1_run(int n, const double* A, int lda, double* Ql, int ldq, double 
   b.Ub[1] = b.Ub[0] + pset;
   b.Bt = b.Ub[1] + pset;
   b.tflag = (unsigned*)(b.Bt + (size_t)N * N);
+  b.Mb[0] = b.tflag + 64;
+  b.Mb[1] = b.Mb[0] + nb / 2;
   b.half = half;
   b.tc = stage1_tensor_cores() && !half;
   float* A32 = b.A32;
