@@ -99,7 +99,8 @@ MPJ_DEV void rec32(int x, int y, float dxx, float dyy, float axy, float skip, Ro
 // 32 x 32 subproblem; writes the rotated subproblem S (column-major), the
 // accumulated U (row-major for the FP32 products, column-major, urow false,
 // for the tensor-core panel) and the set T of its indices that rotated
-// (Mbuf, bit l for local index l): U is the identity outside T x T.
+// (Mbuf, bit l for local index l, if not null): U is the identity outside
+// T x T.
 constexpr int S32_THREADS = 512;
 __global__ void __launch_bounds__(S32_THREADS) solve32(const float* __restrict__ A32, int N, int nb, int R,
                                                float* __restrict__ Sbuf, float* __restrict__ Ubuf, bool hq,
@@ -135,8 +136,10 @@ __global__ void __launch_bounds__(S32_THREADS) solve32(const float* __restrict__
         rr.dy = qh(rr.dy, true);
       }
       rec[tid] = rr;
-      const unsigned bits = rec_rotated(rr.cm1, rr.sig) ? ((1u << x) | (1u << y)) : 0u;
-      tmask |= __reduce_or_sync(0x0000FFFFu, bits);  // the 16 record lanes of warp 0
+      if (Mbuf) {
+        const unsigned bits = rec_rotated(rr.cm1, rr.sig) ? ((1u << x) | (1u << y)) : 0u;
+        tmask |= __reduce_or_sync(0x0000FFFFu, bits);  // the 16 record lanes of warp 0
+      }
     }
     __syncthreads();
     {
@@ -202,7 +205,7 @@ __global__ void __launch_bounds__(S32_THREADS) solve32(const float* __restrict__
     So[e] = S[li][lj];
     Uo[e] = urow ? U[lj][li] : U[li][lj];
   }
-  if (tid == 0) Mbuf[slot] = tmask;
+  if (tid == 0 && Mbuf) Mbuf[slot] = tmask;
 }
 
 
@@ -321,7 +324,7 @@ MPJ_DEV void load_u(const float* __restrict__ Ubuf, int P, float (*Us)[ULD], int
 // 32 w + 4 g .. +3 and columns 8 h .. +7: per k one float4 of X (8 distinct
 // in a warp: one shared-memory wavefront) and two float4 of U_Q (4 distinct:
 // one wavefront each) feed 32 FMAs.
-template <int TRI>
+template <int TRI, bool MASKED>
 __global__ void __launch_bounds__(RT) rmul32(const float* X, float* Y, int N, int nb, int R,
                                              const float* __restrict__ Sbuf, const float* __restrict__ Ubuf, bool hq,
                                              bool ucol, const unsigned* __restrict__ Mbuf) {
@@ -333,15 +336,17 @@ __global__ void __launch_bounds__(RT) rmul32(const float* X, float* Y, int N, in
   const int a0 = 4 * gx, a1 = min(4 * gx + 3, npairs - 1);
   pdl_wait();
   if (TRI == R32_BOTH && a1 < Q) return;
-  // the indices of block pair Q that rotated: U_Q is the identity outside them
-  const unsigned mQ = Mbuf[Q];
-  if (TRI == R32_ALL && mQ == 0u) return;  // V U~ leaves these columns as they are
+  const int warp = tid >> 5, lane = tid & 31;
+  const int a = a0 + warp;  // this warp's block pair
+  // the indices of block pairs Q and a that rotated (U is the identity
+  // outside them); loaded together with the U blocks, used after them
+  const unsigned mQ = MASKED ? Mbuf[Q] : 0xFFFFFFFFu;
+  const unsigned ma = !MASKED ? 0xFFFFFFFFu : (TRI == R32_BOTH && a < npairs) ? Mbuf[a] : 0u;
   int IQ, JQ;
   block_pair(nb, R, Q, IQ, JQ);
   load_u(Ubuf, Q, Us, tid, RT, ucol);
-  const int warp = tid >> 5, lane = tid & 31;
-  const int a = a0 + warp;  // this warp's block pair
   if (TRI == R32_BOTH && a < npairs && a > Q) load_u(Ubuf, a, Ua[warp], lane, 32, ucol);
+  if (TRI == R32_ALL && mQ == 0u) return;  // V U~ leaves these columns as they are
   {
     // X_Q(r, k) = X[g_Q(k) N + row(r)]; thread t: tile rows 4 (t mod 32) .. +3
     // (consecutive rows of one block), contraction indices k = t / 32 + 4 i
@@ -380,7 +385,6 @@ __global__ void __launch_bounds__(RT) rmul32(const float* X, float* Y, int N, in
     }
     return;
   }
-  const unsigned ma = TRI == R32_BOTH ? Mbuf[a] : 0u;
   if (TRI == R32_BOTH && mQ == 0u && ma == 0u) return;  // U_a^T A U_Q = A on this tile
   // a column c outside T_Q: (X U_Q)(:, c) = X(:, c); else the contraction over T_Q
   float acc[4][8];
@@ -487,6 +491,7 @@ struct Stage1Bufs {
   unsigned* tflag;
   unsigned* Mb[2];  // per-pair rotated-index masks, by round parity
   bool half;
+  bool sparse;  // products over the rotated indices only (masked kernels)
   int tc;
 };
 
@@ -505,20 +510,21 @@ cudaError_t stage1_sweep(const Stage1Bufs& b, cudaStream_t s, SideStream* side) 
     float* Sbuf = b.Sb[par];
     float* Ubuf = b.Ub[par];
     if (side && vpending[par]) S1_TRY(cudaStreamWaitEvent(s, side->done[par], 0));
-    unsigned* Mbuf = b.Mb[par];
+    unsigned* Mbuf = b.sparse ? b.Mb[par] : nullptr;
     S1_TRY(mpj_launch_pdl(solve32, dim3(npairs), dim3(S32_THREADS), 0, s, (const float*)b.A32, N, nb, R, Sbuf, Ubuf,
                           b.half, b.tc != 1, Mbuf));
+    auto vmul = b.sparse ? rmul32<R32_ALL, true> : rmul32<R32_ALL, false>;
     // V <- V U~
     if (side) {
       S1_TRY(cudaEventRecord(side->ready, s));
       S1_TRY(cudaStreamWaitEvent(side->sv, side->ready, 0));
-      S1_TRY(mpj_launch_pdl(rmul32<R32_ALL>, g32, dim3(RT), 0, side->sv, (const float*)b.V32, b.V32, N, nb, R,
-                            (const float*)Sbuf, (const float*)Ubuf, b.half, b.tc == 1, (const unsigned*)Mbuf));
+      S1_TRY(mpj_launch_pdl(vmul, g32, dim3(RT), 0, side->sv, (const float*)b.V32, b.V32, N, nb, R, (const float*)Sbuf,
+                            (const float*)Ubuf, b.half, b.tc == 1, (const unsigned*)Mbuf));
       S1_TRY(cudaEventRecord(side->done[par], side->sv));
       vpending[par] = true;
     } else {
-      S1_TRY(mpj_launch_pdl(rmul32<R32_ALL>, g32, dim3(RT), 0, s, (const float*)b.V32, b.V32, N, nb, R,
-                            (const float*)Sbuf, (const float*)Ubuf, b.half, b.tc == 1, (const unsigned*)Mbuf));
+      S1_TRY(mpj_launch_pdl(vmul, g32, dim3(RT), 0, s, (const float*)b.V32, b.V32, N, nb, R, (const float*)Sbuf,
+                            (const float*)Ubuf, b.half, b.tc == 1, (const unsigned*)Mbuf));
     }
     if (b.tc == 1) {
       // A' = U^T A U = (A U)^T U (A symmetric): B^T = (A U)^T, then
@@ -527,8 +533,9 @@ cudaError_t stage1_sweep(const Stage1Bufs& b, cudaStream_t s, SideStream* side) 
       S1_TRY(mpj_tc_panel(N, nb, R, Ubuf, b.Bt, b.A32, 0, nullptr, nullptr, b.tflag, s));
     } else {
       // A <- U~^T A U~ in one pass (tiles a > Q, mirrored; S on the diagonal)
-      S1_TRY(mpj_launch_pdl(rmul32<R32_BOTH>, g32, dim3(RT), 0, s, (const float*)b.A32, b.A32, N, nb, R,
-                            (const float*)Sbuf, (const float*)Ubuf, b.half, false, (const unsigned*)Mbuf));
+      auto amul = b.sparse ? rmul32<R32_BOTH, true> : rmul32<R32_BOTH, false>;
+      S1_TRY(mpj_launch_pdl(amul, g32, dim3(RT), 0, s, (const float*)b.A32, b.A32, N, nb, R, (const float*)Sbuf,
+                            (const float*)Ubuf, b.half, false, (const unsigned*)Mbuf));
     }
   }
   if (side)
@@ -545,7 +552,7 @@ cudaError_t stage1_sweep(const Stage1Bufs& b, cudaStream_t s, SideStream* side) 
 // later calls with the same workspace.
 struct SweepGraph {
   int dev, N, tc;
-  bool half, side;
+  bool half, side, sparse;
   void* work;
   cudaGraphExec_t exec;
   long long launches;  // kernels in one sweep
@@ -583,7 +590,8 @@ std::shared_ptr<SweepGraph> sweep_graph(const Stage1Bufs& b, void* work, bool us
   std::lock_guard<std::mutex> lock(g_sweep_mu);
   auto& reg = sweep_registry();
   for (const auto& g : reg)
-    if (g->dev == dev && g->work == work && g->N == b.N && g->half == b.half && g->tc == b.tc && g->side == use_side)
+    if (g->dev == dev && g->work == work && g->N == b.N && g->half == b.half && g->tc == b.tc && g->side == use_side &&
+        g->sparse == b.sparse)
       return g;
   cudaStream_t cap = nullptr;
   if (cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking) != cudaSuccess) {
@@ -626,6 +634,7 @@ std::shared_ptr<SweepGraph> sweep_graph(const Stage1Bufs& b, void* work, bool us
   g->tc = b.tc;
   g->half = b.half;
   g->side = use_side;
+  g->sparse = b.sparse;
   g->work = work;
   g->exec = exec;
   g->launches = per;
@@ -635,7 +644,8 @@ std::shared_ptr<SweepGraph> sweep_graph(const Stage1Bufs& b, void* work, bool us
 }  // namespace
 
 int mpj_stage1_run(int n, const double* A, int lda, double* Ql, int ldq, double tol32, int max_sweeps, int* sweeps_out,
-                   double* off_out, void* work, double* partial, double* dscal, cudaStream_t s, bool half) {
+                   double* off_out, void* work, double* partial, double* dscal, cudaStream_t s, bool half,
+                   bool sparse) {
   Stage1Bufs b;
   b.N = mpj_stage1_padded(n);
   b.nb = b.N / BS;
@@ -652,6 +662,7 @@ int mpj_stage1_run(int n, const double* A, int lda, double* Ql, int ldq, double 
   b.Mb[0] = b.tflag + 64;
   b.Mb[1] = b.Mb[0] + nb / 2;
   b.half = half;
+  b.sparse = sparse;
   b.tc = stage1_tensor_cores() && !half;
   float* A32 = b.A32;
   float* V32 = b.V32;

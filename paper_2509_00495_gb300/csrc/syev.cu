@@ -566,7 +566,8 @@ int mpj_syev_ex(int n, const double* A, int lda, double* W, double* Q, int ldq, 
         // about one, up to the point where two FP64 sweeps remain (nine sweeps
         // at n = 4096), hence the cap
         int cap2 = o.max_sweeps32_pass2 > 0 ? o.max_sweeps32_pass2 : (o.max_sweeps32 < 9 ? o.max_sweeps32 : 9);
-        int r1b = mpj_stage1_run(n, M, n, Ql2, n, tol32b, cap2, &sweeps32b, nullptr, S1, sm.partial, sm.dscal, s);
+        int r1b = mpj_stage1_run(n, M, n, Ql2, n, tol32b, cap2, &sweeps32b, nullptr, S1, sm.partial, sm.dscal, s,
+                                 false, true);
         if (r1b < 0) {
           st = r1b;
           goto done;
